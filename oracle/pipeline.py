@@ -1,0 +1,64 @@
+"""End-to-end oracle set-up for one workload: mesh, assembly, decomposition,
+coarse space (variants of Sec. 4: none / NK / SNK, with or without GenEO),
+preconditioner and PCG."""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+from .mesh import build_mesh
+from .fem import assemble_A, assemble_rhs, local_element_A
+from .dd import decompose
+from .coarse import (snk_columns, nk_columns, geneo_columns, assemble_Z, tau_paper,
+                     independent_geneo)
+from .solver import build_preconditioner, pcg
+
+
+@dataclass
+class OracleProblem:
+    w: object
+    mesh: object
+    A: object
+    AT: np.ndarray
+    b: np.ndarray             # [nrhs, n]
+    dec: object
+    snk: list
+    geneo: list
+    gevps: list
+    Z: object
+    M: object
+    tau_p: float
+    info: dict = field(default_factory=dict)
+
+
+def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
+                  pou="boolean"):
+    mesh = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    A = assemble_A(mesh, w)
+    AT = local_element_A(mesh, w)
+    b = assemble_rhs(mesh, w)
+    dec = decompose(mesh, w.parts, w.overlap, pou=pou)
+    n = A.shape[0]
+    if coarse == "snk":
+        cols = snk_columns(mesh, dec)
+    elif coarse == "nk":
+        cols = nk_columns(mesh)
+    elif coarse == "none":
+        cols = []
+    else:
+        raise ValueError(coarse)
+    tp = tau_paper(w.tau, tau_convention)
+    gcols, gevps = ([], None)
+    if geneo:
+        gcols, gevps = geneo_columns(mesh, A, AT, dec, tp)
+        if gcols:
+            Zg = assemble_Z(n, cols) if cols else None
+            keep = independent_geneo(A, Zg, assemble_Z(n, gcols))
+            gcols = [gcols[k] for k in keep.tolist()]
+    Z = assemble_Z(n, cols + gcols) if (cols or gcols) else None
+    M = build_preconditioner(A, dec, Z)
+    return OracleProblem(w, mesh, A, AT, b, dec, cols, gcols, gevps, Z, M, tp)
+
+
+def solve(prob, tol=1e-8, maxit=1000, rhs=0):
+    return pcg(prob.A, prob.b[rhs], prob.M.apply, tol=tol, maxit=maxit)

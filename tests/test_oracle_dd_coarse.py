@@ -1,0 +1,260 @@
+"""Pins of the oracle's decomposition, coarse space, preconditioner and PCG
+against the paper's identities and condition-number statements (no GPU)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import workloads as W
+from oracle.mesh import build_mesh, gradient_dofs
+from oracle.fem import assemble_A, local_element_A, assemble_rhs
+from oracle.dd import decompose, k0, k1, restriction, local_dirichlet, local_neumann
+from oracle.coarse import (snk_columns, assemble_Z, local_gradient, xi_projector,
+                           local_gevp, geneo_columns)
+from oracle.solver import build_preconditioner, pcg, direct_solve
+from oracle.pipeline import build_problem, solve
+
+
+def small(n=(6, 5, 4), parts=(2, 2, 1), overlap=1, gamma=1e-2, holes=(), seed=0, mu=None,
+          tau=0.1):
+    rng = np.random.default_rng(seed)
+    nc = n[0] * n[1] * n[2]
+    mu_inv = mu if mu is not None else 10.0 ** rng.uniform(0, 2, nc)
+    return W.box(*n, parts=parts, overlap=overlap, gamma=gamma, mu_inv=mu_inv,
+                 eps=10.0 ** rng.uniform(-0.5, 0.5, nc), holes=holes, f='random',
+                 seed=seed, tau=tau)
+
+
+def setup(w, pou="boolean"):
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    A = assemble_A(m, w)
+    AT = local_element_A(m, w)
+    dec = decompose(m, w.parts, w.overlap, pou=pou)
+    return m, A, AT, dec
+
+
+@pytest.mark.parametrize("pou", ["boolean", "core"])
+def test_partition_of_unity(pou):
+    """sum_i R_i^T D_i R_i = I (Sec. 2, eq. "PoU"), D_i >= 0."""
+    w = small(holes=[((2, 4), (2, 3), (0, 4))])
+    m, A, AT, dec = setup(w, pou)
+    n = A.shape[0]
+    S = sum(restriction(dec, i, n).T @ sp.diags(dec.D[i]) @ restriction(dec, i, n)
+            for i in range(dec.nsub))
+    assert all((d >= 0).all() for d in dec.D)
+    assert np.abs(S.toarray() - np.eye(n)).max() <= 4 * np.finfo(float).eps
+
+
+def test_neumann_sum_and_lemma_k1():
+    """sum_i R_i^T A_i^Neu R_i = sum_T m_T A_T, which gives Lemma "Lemma_k1":
+    sum_i (R_i U)^T A_i^Neu (R_i U) <= k1 U^T A U."""
+    w = small(n=(6, 6, 3), parts=(3, 2, 1), overlap=1)
+    m, A, AT, dec = setup(w)
+    n = A.shape[0]
+    S = sum(restriction(dec, i, n).T @ sp.csr_matrix(local_neumann(m, AT, dec, i)) @
+            restriction(dec, i, n) for i in range(dec.nsub))
+    # multiplicity-weighted assembly
+    ntet = len(m.tets)
+    mult = dec.cell_mult[m.tet_cell]
+    from oracle.fem import assemble_edges, mirror_upper
+    Aw = mirror_upper(assemble_edges(m, AT * mult[:, None, None])[m.dof_edge][:, m.dof_edge])
+    assert np.abs((S - Aw).toarray()).max() <= 1e-12 * np.abs(Aw).max()
+    kk1 = k1(dec)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        U = rng.standard_normal(n)
+        lhs = sum(U[dec.N[i]] @ local_neumann(m, AT, dec, i) @ U[dec.N[i]] for i in range(dec.nsub))
+        assert lhs <= kk1 * (U @ (A @ U)) * (1 + 1e-12)
+    # A_i^Neu is SPD (gamma > 0) and A_i^Neu <= A_i in energy
+    for i in range(dec.nsub):
+        An = local_neumann(m, AT, dec, i)
+        assert np.linalg.eigvalsh(An)[0] > 0
+        Ai = local_dirichlet(A, dec, i)
+        assert np.linalg.eigvalsh(Ai - An)[0] >= -1e-10 * np.abs(Ai).max()
+
+
+def test_lemma_k0():
+    """Lemma "Lemma_k0" with Q_i = R_i^T: |sum_i R_i^T U_i|_A^2 <= k0 sum_i |U_i|_{A_i}^2."""
+    w = small(n=(6, 4, 4), parts=(3, 2, 1), overlap=1)
+    m, A, AT, dec = setup(w)
+    kk0 = k0(A, dec)
+    assert 1 <= kk0 <= dec.nsub
+    n = A.shape[0]
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        Us = [rng.standard_normal(len(Ni)) for Ni in dec.N]
+        v = np.zeros(n)
+        for Ni, U in zip(dec.N, Us):
+            v[Ni] += U
+        rhs = sum(U @ local_dirichlet(A, dec, i) @ U for i, U in enumerate(Us))
+        assert v @ (A @ v) <= kk0 * rhs * (1 + 1e-12)
+
+
+def test_snk_full_rank_boolean_and_contains_local_gradients():
+    """Z_G has full rank (Sec. 3.2 requires a full-rank Z) and spans
+    R_i^T D_i G_i for every i (Sec. 2, definition "near-kernelCS")."""
+    w = small(n=(6, 6, 4), parts=(2, 2, 2), overlap=1, holes=[((2, 4), (2, 4), (0, 4))])
+    m, A, AT, dec = setup(w)
+    Z = assemble_Z(A.shape[0], snk_columns(m, dec)).toarray()
+    s = np.linalg.svd(Z, compute_uv=False)
+    assert s[-1] > 1e-3 * s[0]
+    G = gradient_dofs(m).toarray()
+    for i in range(dec.nsub):
+        Ni = dec.N[i]
+        V = np.zeros((A.shape[0], G.shape[1]))
+        V[Ni] = dec.D[i][:, None] * G[Ni]
+        coef, *_ = np.linalg.lstsq(Z, V, rcond=None)
+        assert np.abs(Z @ coef - V).max() < 1e-10
+    # the global gradient is inside V_G (G in V_G, Sec. 2)
+    coef, *_ = np.linalg.lstsq(Z, G, rcond=None)
+    assert np.abs(Z @ coef - G).max() < 1e-10
+
+
+def test_core_pou_snk_is_rank_deficient():
+    """With the core-edge partition of unity the per-(i, v) columns are
+    linearly dependent across subdomains even after removing floating and
+    duplicate columns; this is why the Boolean partition of unity is used."""
+    w = W.unit_cube_8()
+    m, A, AT, dec = setup(w, "core")
+    Z = assemble_Z(A.shape[0], snk_columns(m, dec)).toarray()
+    s = np.linalg.svd(Z, compute_uv=False)
+    assert s[-1] < 1e-12 * s[0]
+
+
+def test_xi_projector_properties():
+    """xi_0i is the A_i-orthogonal projection on range(G_i) and
+    B^dagger = (I - xi) A_i^-1 inverts A_i on its A_i-orthogonal complement
+    (Sec. 2, eq. "inverseBw")."""
+    w = small(n=(6, 5, 4), parts=(2, 2, 1), overlap=1)
+    m, A, AT, dec = setup(w)
+    for i in range(dec.nsub):
+        Ai = local_dirichlet(A, dec, i)
+        Gi, kept = local_gradient(m, dec, i)
+        assert np.linalg.matrix_rank(Gi) == Gi.shape[1]
+        xi = xi_projector(Ai, Gi)
+        sc = np.abs(xi).max()
+        assert np.abs(xi @ xi - xi).max() < 1e-10 * sc
+        assert np.abs(Ai @ xi - xi.T @ Ai).max() < 1e-10 * np.abs(Ai).max() * sc
+        assert np.abs((np.eye(len(Ai)) - xi) @ Gi).max() < 1e-10
+        Bd = (np.eye(len(Ai)) - xi) @ np.linalg.inv(Ai)
+        rng = np.random.default_rng(i)
+        y = rng.standard_normal(len(Ai))
+        # y in the complement: b_i(y, G_i c) = 0  <=>  G_i^T A_i y = 0 ... here
+        # take y = A_i (I - xi) u, the image of the complement under A_i
+        y = Ai @ ((np.eye(len(Ai)) - xi) @ y)
+        u = Bd @ y
+        assert np.abs(Gi.T @ Ai @ u).max() < 1e-8 * np.abs(u).max() * np.abs(Ai).max()
+        assert np.abs(Ai @ u - y).max() < 1e-8 * np.abs(y).max()
+
+
+def test_gevp_count_by_inertia():
+    """#{lambda > tau} of eq. "eigAtildeBAS" equals the number of positive
+    eigenvalues of L - tau B (Sylvester), computed by an LDL^T inertia count
+    independent of the eigensolver."""
+    w = small(n=(6, 6, 4), parts=(2, 2, 1), overlap=1, gamma=1e-3)
+    m, A, AT, dec = setup(w)
+    for tau in (0.5, 2.0):
+        for j in range(dec.nsub):
+            g = local_gevp(m, A, AT, dec, j)
+            Lm = g.L - tau * g.Aneu
+            lu, d, perm = sla.ldl(0.5 * (Lm + Lm.T))
+            evd = np.concatenate([np.linalg.eigvalsh(d[k:k + 2, k:k + 2]) if (
+                k + 1 < len(d) and d[k + 1, k] != 0) else [d[k, k]] for k in _blocks(d)])
+            assert int((evd > 0).sum()) == int((g.lam > tau).sum())
+            # eigen-residual and B-orthonormality of the oracle's eigensolve
+            V, lam = g.V[:, :5], g.lam[:5]
+            R = g.L @ V - g.Aneu @ V * lam
+            assert np.abs(R).max() < 1e-8 * np.abs(g.L).max()
+            assert np.allclose(V.T @ g.Aneu @ V, np.eye(5), atol=1e-10)
+
+
+def _blocks(d):
+    k, out = 0, []
+    while k < len(d):
+        out.append(k)
+        k += 2 if (k + 1 < len(d) and d[k + 1, k] != 0) else 1
+    return out
+
+
+def _dense_precond(prob):
+    n = prob.A.shape[0]
+    return np.column_stack([prob.M.apply(e) for e in np.eye(n)])
+
+
+def test_preconditioner_identities():
+    """M^-1 symmetric (eq. "AS2"); (I - P0) Z = 0; (I - P0) sum_i R_i^T D_i
+    xi_0i R_i U = 0 (Sec. 3.1, proof of the stable decomposition)."""
+    w = small(n=(6, 5, 4), parts=(2, 2, 1), overlap=1, tau=3.0)
+    prob = build_problem(w, tau_convention="paper")
+    assert len(prob.geneo) > 0
+    A = prob.A.toarray()
+    Minv = _dense_precond(prob)
+    assert np.abs(Minv - Minv.T).max() < 1e-10 * np.abs(Minv).max()
+    Z = prob.Z.toarray()
+    E = Z.T @ A @ Z
+    P0 = Z @ np.linalg.solve(E, Z.T @ A)
+    assert np.abs((np.eye(len(A)) - P0) @ Z).max() < 1e-9
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal(len(A))
+    v = np.zeros(len(A))
+    for i in range(prob.dec.nsub):
+        Ai = local_dirichlet(prob.A, prob.dec, i)
+        Gi, _ = local_gradient(prob.mesh, prob.dec, i)
+        v[prob.dec.N[i]] += prob.dec.D[i] * (xi_projector(Ai, Gi) @ U[prob.dec.N[i]])
+    assert np.abs((np.eye(len(A)) - P0) @ v).max() < 1e-9 * np.abs(v).max()
+
+
+def test_exact_cases():
+    """Z = I gives M^-1 = A^-1; one subdomain covering Omega gives A^-1."""
+    w = small(n=(4, 4, 3), parts=(2, 1, 1), overlap=1)
+    m, A, AT, dec = setup(w)
+    n = A.shape[0]
+    M = build_preconditioner(A, dec, sp.identity(n, format='csc'))
+    r = np.random.default_rng(0).standard_normal(n)
+    x = direct_solve(A, r)
+    assert np.abs(M.apply(r) - x).max() < 1e-10 * np.abs(x).max()
+    w1 = small(n=(4, 4, 3), parts=(1, 1, 1), overlap=1)
+    p1 = build_problem(w1)
+    assert np.abs(p1.M.apply(r) - x).max() < 1e-10 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("tau_p", [2.0, 3.0])
+def test_condition_number_bound_geneo(tau_p):
+    """Theorem (Sec. 3.2): the eigenvalues of M^-1_AS,2 A lie in
+    [1/(1 + k1 tau), k0] (Lemma "surj_cont" gives the upper bound)."""
+    w = small(n=(6, 4, 4), parts=(2, 2, 1), overlap=1, gamma=1e-3, tau=tau_p, seed=5)
+    prob = build_problem(w, tau_convention="paper")
+    A = prob.A.toarray()
+    ev = np.sort(np.real(np.linalg.eigvals(_dense_precond(prob) @ A)))
+    kk0, kk1 = k0(prob.A, prob.dec), k1(prob.dec)
+    assert ev[-1] <= kk0 * (1 + 1e-8)
+    assert ev[0] >= 1.0 / (1.0 + kk1 * tau_p) * (1 - 1e-8)
+
+
+def test_condition_number_bound_snk_only():
+    """Theorem (Sec. 3.1): with the SNK space alone the eigenvalues lie in
+    [1/(1 + k1 tau0), k0] with tau0 of eq. "tauOneLevelAS"."""
+    w = small(n=(6, 4, 4), parts=(2, 2, 1), overlap=1, gamma=1e-3, seed=6)
+    prob = build_problem(w, geneo=False)
+    m, A, AT, dec = prob.mesh, prob.A, prob.AT, prob.dec
+    tau0 = max(local_gevp(m, A, AT, dec, j).lam[0] for j in range(dec.nsub))
+    ev = np.sort(np.real(np.linalg.eigvals(_dense_precond(prob) @ A.toarray())))
+    assert ev[-1] <= k0(A, dec) * (1 + 1e-8)
+    assert ev[0] >= 1.0 / (1.0 + k1(dec) * tau0) * (1 - 1e-8)
+
+
+def test_pcg_matches_direct_solve():
+    w = small(n=(6, 6, 4), parts=(2, 2, 2), overlap=1, gamma=1e-4,
+              holes=[((2, 4), (2, 4), (0, 4))])
+    prob = build_problem(w)
+    x = direct_solve(prob.A, prob.b[0])
+    r = solve(prob, tol=1e-12, maxit=500)
+    assert r.relres <= 1e-12
+    ev = np.linalg.eigvalsh(prob.A.toarray())
+    kappa = ev[-1] / ev[0]
+    # forward error <= kappa(A) * relative residual
+    assert np.linalg.norm(r.x - x) / np.linalg.norm(x) <= 2 * kappa * r.relres + 1e-12
+    # the one-level method needs more iterations than the two-level one
+    r1 = pcg(prob.A, prob.b[0], build_problem(w, coarse="none", geneo=False).M.apply, 1e-8)
+    r2 = solve(prob, tol=1e-8)
+    assert r2.iters <= r1.iters

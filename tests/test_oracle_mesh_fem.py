@@ -1,0 +1,189 @@
+"""Pins of the oracle's mesh, incidence, element matrices, assembly and load
+against what the paper and the mathematics fix (no GPU)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle.mesh import build_mesh, gradient_full, curl_full, gradient_dofs, LOCAL_EDGES
+from oracle.fem import (element_matrices, barycentric_gradients, assemble_A, assemble_K,
+                        assemble_rhs, edge_vectors)
+from oracle.dd import decompose
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "beam_sizes.txt")
+
+
+def golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(x) for x in line.split()])
+    return rows
+
+
+def box_edges_closed_form(nx, ny, nz):
+    """Axis edges + one diagonal per grid square + one body diagonal per cell."""
+    n = (nx, ny, nz)
+    axis = sum(n[a] * (n[(a + 1) % 3] + 1) * (n[(a + 2) % 3] + 1) for a in range(3))
+    faces = sum(n[a] * n[(a + 1) % 3] * (n[(a + 2) % 3] + 1) for a in range(3))
+    return axis + faces + nx * ny * nz
+
+
+def test_paper_dof_counts_exact():
+    """Sec. 4: the beam of N = 8 subdomains has 121,696 dofs (all edges)."""
+    rows = golden_rows()
+    r8 = [r for r in rows if r[0] == 8][0]
+    m = build_mesh(64, 16, 16, 1 / 16, np.ones(64 * 16 * 16, np.uint8))
+    assert len(m.edges) == r8[1] == 121696
+    # the closed form agrees with the mesh on several boxes ...
+    for dims in [(1, 1, 1), (3, 2, 5), (7, 4, 3), (64, 16, 16)]:
+        mm = build_mesh(*dims, 1.0, np.ones(np.prod(dims), np.uint8))
+        assert len(mm.edges) == box_edges_closed_form(*dims)
+    # ... and reproduces the N = 256 count of the paper
+    r256 = [r for r in rows if r[0] == 256][0]
+    assert box_edges_closed_form(2048, 16, 16) == r256[1] == 3869472
+
+
+def test_paper_table_sizes_rounded():
+    """Table "homogeneous_beam_both": #dofs, NK (= vertices) and SNK (= sum of
+    vertex counts of the overlapping subdomains, one layer) in thousands."""
+    for N, _, dofs_k, nk_k, snk_k in golden_rows():
+        nx = 8 * N
+        assert round(box_edges_closed_form(nx, 16, 16) / 1000) == dofs_k
+        assert round((nx + 1) * 17 * 17 / 1000) == nk_k
+        if N <= 16:
+            m = build_mesh(nx, 16, 16, 1 / 16, np.ones(nx * 256, np.uint8))
+            dec = decompose(m, (N, 1, 1), 1)
+            nverts = sum(len(np.unique(m.tets[dec.sub_tets[i]])) for i in range(N))
+            if N == 8:
+                assert nverts == 24854
+            assert round(nverts / 1000) == snk_k
+
+
+def test_curl_grad_zero_integer():
+    """curl(grad) = 0 on the integer incidence matrices (Sec. 1: the gradient
+    matrix spans the kernel of the discrete curl-curl operator)."""
+    w = W.box(3, 2, 2, holes=[((1, 2), (0, 1), (0, 1))])
+    m = build_mesh(w.nx, w.ny, w.nz, 1.0, w.active)
+    FG = curl_full(m) @ gradient_full(m)
+    assert FG.dtype.kind == 'i'
+    assert abs(FG).sum() == 0
+    # and the sign convention matters: flipping one edge breaks it
+    G = gradient_full(m).tolil()
+    G[0, :] = -G[0, :]
+    assert abs(curl_full(m) @ G.tocsr()).sum() > 0
+
+
+def _one_tet(scale=(1.0, 1.0, 1.0)):
+    P = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [1, 1, 1]], float) * np.array(scale)
+    P = P + np.array([0.3, -0.2, 0.1])
+    return P[None]
+
+
+def test_element_mass_constant_field():
+    """A constant field c is reproduced by the Whitney space with dofs
+    u_e = c . t_e, so u^T M_T u = eps |T| |c|^2."""
+    P = _one_tet((0.7, 1.3, 0.9))
+    eps = np.array([2.5])
+    _, M, vol = element_matrices(P, np.array([1.0]), eps)
+    c = np.array([0.4, -1.1, 0.7])
+    u = np.array([c @ (P[0, b] - P[0, a]) for a, b in LOCAL_EDGES])
+    assert np.isclose(u @ M[0] @ u, eps[0] * vol[0] * c @ c, rtol=1e-13)
+
+
+def test_element_curl_linear_field():
+    """u = a x x has curl 2a, so u^T K_T u = mu^-1 |T| 4|a|^2 (exact: the
+    field is in the Whitney space; dofs are line integrals, exact for
+    linear integrands at the edge midpoint)."""
+    P = _one_tet((1.2, 0.8, 1.1))
+    mu_inv = np.array([3.0])
+    K, _, vol = element_matrices(P, mu_inv, np.array([1.0]))
+    a = np.array([0.3, 0.5, -0.8])
+    u = np.array([np.cross(a, 0.5 * (P[0, a_] + P[0, b])) @ (P[0, b] - P[0, a_])
+                  for a_, b in LOCAL_EDGES])
+    assert np.isclose(u @ K[0] @ u, mu_inv[0] * vol[0] * 4 * a @ a, rtol=1e-12)
+
+
+def test_barycentric_partition():
+    P = _one_tet((0.5, 2.0, 1.0))
+    g, vol = barycentric_gradients(P)
+    assert np.allclose(g.sum(axis=1), 0, atol=1e-14)
+    # grad lambda_k . (p_l - p_0) = delta_kl - delta_0l
+    for k in range(4):
+        for l in range(1, 4):
+            assert np.isclose(g[0, k] @ (P[0, l] - P[0, 0]), float(k == l) - float(k == 0))
+    assert np.isclose(vol[0], 0.5 * 2.0 * 1.0 / 6)
+
+
+def test_kernel_of_curl_curl():
+    """K G = 0 (gradients are in the kernel of curl-curl, Sec. 1)."""
+    w = W.box(6, 5, 4, mu_inv=np.linspace(1, 5, 120), holes=[((2, 4), (2, 3), (0, 4))])
+    m = build_mesh(w.nx, w.ny, w.nz, (0.25, 0.3, 0.2), w.active)
+    K = assemble_K(m, w)
+    G = gradient_dofs(m)
+    assert G.shape[1] > 10
+    KG = K @ G
+    assert abs(KG).max() <= 1e-14 * abs(K).max() * 2
+
+
+def test_A_spd_and_symmetric():
+    w = W.box(3, 3, 2, gamma=1e-3, mu_inv=np.arange(1, 19, dtype=float))
+    m = build_mesh(w.nx, w.ny, w.nz, 1 / 3, w.active)
+    A = assemble_A(m, w)
+    assert (A != A.T).nnz == 0
+    ev = np.linalg.eigvalsh(A.toarray())
+    assert ev[0] > 0
+
+
+def test_load_constant_f_closed_form():
+    """For constant f: int_T f . W_ab = f . (|T|/4)(grad l_b - grad l_a)."""
+    w = W.box(2, 3, 2, f=(0.3, -0.7, 1.1))
+    m = build_mesh(w.nx, w.ny, w.nz, (0.5, 0.25, 0.4), w.active)
+    b = assemble_rhs(m, w)[0]
+    g, vol = barycentric_gradients(m.coords[m.tets])
+    f = np.array([0.3, -0.7, 1.1])
+    ref = np.zeros(len(m.edges))
+    for e, (a, bb) in enumerate(LOCAL_EDGES):
+        np.add.at(ref, m.tet_edges[:, e], (vol / 4) * ((g[:, bb] - g[:, a]) @ f))
+    assert np.allclose(b, ref[m.dof_edge], rtol=1e-13, atol=1e-16)
+
+
+def _manufactured_error(n, gamma=1.0):
+    """Relative discrete L2 error of the FE solution against the edge
+    interpolant of E* = (sin pi y sin pi z, sin pi z sin pi x, sin pi x sin pi y)
+    with f = (2 pi^2 + gamma) E* (div E* = 0, E* x n = 0 on the unit cube)."""
+    w = W.box(n, n, n, gamma=gamma)
+    m = build_mesh(n, n, n, 1.0 / n, w.active)
+    Es = lambda x: np.stack([np.sin(np.pi * x[:, 1]) * np.sin(np.pi * x[:, 2]),
+                             np.sin(np.pi * x[:, 2]) * np.sin(np.pi * x[:, 0]),
+                             np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1])], axis=1)
+    # source per edge slot, evaluated at the edge midpoints
+    from oracle.mesh import edge_slot
+    base, d = edge_slot(m)
+    mid = 0.5 * (m.coords[m.edges[:, 0]] + m.coords[m.edges[:, 1]])
+    f_slot = np.zeros((1, m.nverts, 7, 3))
+    f_slot[0, base, d] = (2 * np.pi ** 2 + gamma) * Es(mid)
+    w.f_slot = f_slot
+    A = assemble_A(m, w)
+    b = assemble_rhs(m, w)[0]
+    u = spla.spsolve(A.tocsc(), b)
+    # interpolant dof: line integral by 3-point Gauss on each edge
+    t = edge_vectors(m)
+    gp = [(0.5 - np.sqrt(15) / 10, 5 / 18), (0.5, 8 / 18), (0.5 + np.sqrt(15) / 10, 5 / 18)]
+    pi_u = sum(wq * np.einsum('ei,ei->e', Es(m.coords[m.edges[:, 0]] + s * t), t) for s, wq in gp)
+    pi_u = pi_u[m.dof_edge]
+    wM = W.box(n, n, n, gamma=1.0)
+    from oracle.fem import element_matrices as em, assemble_edges
+    _, M, _ = em(m.coords[m.tets], np.ones(len(m.tets)), np.ones(len(m.tets)))
+    Mf = assemble_edges(m, M)[m.dof_edge][:, m.dof_edge]
+    e = u - pi_u
+    return np.sqrt(e @ (Mf @ e) / (pi_u @ (Mf @ pi_u)))
+
+
+def test_manufactured_solution_rate():
+    errs = [_manufactured_error(n) for n in (4, 8, 16)]
+    rates = [np.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(r >= 0.9 for r in rates), (errs, rates)

@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs for the positive-Maxwell GenEO workloads.
+
+This module only draws inputs: grid shape, active-cell masks (holes), per-cell
+coefficients mu^-1 and eps, gamma, the box partition, the overlap width, the
+GenEO threshold and the source field.  It holds none of the method's
+arithmetic, so the CPU oracle and the CUDA library both consume it.
+
+Conventions (the library's C-ABI uses the same ones):
+
+* cells are numbered ``c = i + nx*(j + ny*k)``;
+* vertices are numbered ``v = i + (nx+1)*(j + (ny+1)*k)``;
+* the source field is given per *edge slot* ``(v, d)``: every edge of the
+  Kuhn-split structured mesh runs from its lower vertex ``v`` along one of the
+  seven positive directions ``DIRS[d]``.  ``f_slot`` has shape
+  ``[nrhs, nverts, 7, 3]`` (float64); slots that are not edges are ignored.
+
+The workloads follow the paper's test set-up (cubic cells split into six
+tetrahedra, beams of size (N/2)x1x1 with h=1/16, layered or hole-located
+coefficient jumps, gamma between 1e-6 and 1e2; Section 4) and the five
+configurations this library is benchmarked on.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+# positive edge directions of the Kuhn split (axis, face diagonal, body diagonal)
+DIRS = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1],
+                 [1, 1, 0], [1, 0, 1], [0, 1, 1], [1, 1, 1]], dtype=np.int64)
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    hx: float
+    hy: float
+    hz: float
+    active: np.ndarray          # uint8 [ncells]
+    mu_inv: np.ndarray          # float64 [ncells]
+    eps: np.ndarray             # float64 [ncells]
+    gamma: float
+    parts: tuple                # (px, py, pz) boxes
+    overlap: int                # layers of cells added around each box
+    tau: float                  # GenEO threshold (convention chosen by the solver)
+    f_slot: np.ndarray          # float64 [nrhs, nverts, 7, 3]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def ncells(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nverts(self):
+        return (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+
+    @property
+    def nrhs(self):
+        return self.f_slot.shape[0]
+
+
+def _cell_ijk(nx, ny, nz):
+    c = np.arange(nx * ny * nz)
+    return c % nx, (c // nx) % ny, c // (nx * ny)
+
+
+def _const_f(nverts, vec=(1.0, 1.0, 1.0), nrhs=1):
+    f = np.empty((nrhs, nverts, 7, 3), dtype=np.float64)
+    f[...] = np.asarray(vec, dtype=np.float64)
+    return f
+
+
+def _uniform_f(rng, nverts, nrhs=1):
+    return rng.uniform(-1.0, 1.0, size=(nrhs, nverts, 7, 3))
+
+
+def box(nx, ny, nz, *, h=None, parts=(2, 2, 2), overlap=1, gamma=1.0, tau=0.1,
+        mu_inv=1.0, eps=1.0, holes=(), f=(1.0, 1.0, 1.0), nrhs=1, seed=None,
+        name=None):
+    """Generic box of cells.  ``holes`` lists half-open cell ranges
+    ``((i0,i1),(j0,j1),(k0,k1))`` that are removed.  ``mu_inv``/``eps`` are
+    scalars or per-cell arrays.  ``f`` is a constant 3-vector or ``'random'``
+    (uniform in [-1,1]^3 per edge slot, seeded)."""
+    if h is None:
+        h = 1.0 / max(nx, ny, nz)
+    ncells = nx * ny * nz
+    ci, cj, ck = _cell_ijk(nx, ny, nz)
+    active = np.ones(ncells, dtype=np.uint8)
+    for (i0, i1), (j0, j1), (k0, k1) in holes:
+        m = (ci >= i0) & (ci < i1) & (cj >= j0) & (cj < j1) & (ck >= k0) & (ck < k1)
+        active[m] = 0
+    mu = np.broadcast_to(np.asarray(mu_inv, dtype=np.float64), (ncells,)).copy()
+    ep = np.broadcast_to(np.asarray(eps, dtype=np.float64), (ncells,)).copy()
+    nverts = (nx + 1) * (ny + 1) * (nz + 1)
+    if isinstance(f, str) and f == 'random':
+        fs = _uniform_f(np.random.default_rng(seed), nverts, nrhs)
+    else:
+        fs = _const_f(nverts, f, nrhs)
+    return Workload(name or f"box{nx}x{ny}x{nz}", nx, ny, nz, h, h, h, active, mu, ep,
+                    float(gamma), tuple(parts), int(overlap), float(tau), fs)
+
+
+def unit_cube_8():
+    """Plain method, FP64: 8^3 unit cube, mu=eps=1, gamma=1, f=(1,1,1),
+    2x2x2 boxes, one overlap layer, tau=0.1."""
+    return box(8, 8, 8, parts=(2, 2, 2), overlap=1, gamma=1.0, tau=0.1,
+               name="cube8_plain")
+
+
+def cube32_hole_channels(seed=2):
+    """32^3 unit cube with a through-hole (central 8x8x32 column removed);
+    mu^-1 log-uniform in [1,1e3] per cell inside 4 random 2x2-cell channels
+    running the full length of a random axis, 1 elsewhere; eps=1;
+    gamma=1e-4; f uniform in [-1,1]^3 per edge; 4x4x4 boxes, overlap 2."""
+    n = 32
+    rng = np.random.default_rng(seed)
+    ci, cj, ck = _cell_ijk(n, n, n)
+    ijk = np.stack([ci, cj, ck])
+    active = np.ones(n ** 3, dtype=np.uint8)
+    active[(ci >= 12) & (ci < 20) & (cj >= 12) & (cj < 20)] = 0
+    mu = np.ones(n ** 3)
+    chans = []
+    for _ in range(4):
+        axis = int(rng.integers(0, 3))
+        others = [a for a in range(3) if a != axis]
+        p = int(rng.integers(0, n - 1))
+        q = int(rng.integers(0, n - 1))
+        m = ((ijk[others[0]] >= p) & (ijk[others[0]] < p + 2) &
+             (ijk[others[1]] >= q) & (ijk[others[1]] < q + 2))
+        mu[m] = 10.0 ** rng.uniform(0.0, 3.0, size=int(m.sum()))
+        chans.append((axis, p, q))
+    f = _uniform_f(rng, (n + 1) ** 3, 1)
+    w = Workload("cube32_hole_channels", n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, active, mu,
+                 np.ones(n ** 3), 1e-4, (4, 4, 4), 2, 0.1, f, meta={"channels": chans})
+    return w
+
+
+def beam128_layered(seed=4, nrhs=16):
+    """128x16x16 cells (h=1/16), two 4x4-cell through-holes along x
+    (y in [3,7) and [9,13), z in [6,10)); mu^-1 alternating 1 and 1e6 every
+    8 cells in x; eps=1; gamma=1e-6; 16 seeded uniform right-hand sides;
+    32x4x4 boxes, overlap 1."""
+    nx, ny, nz = 128, 16, 16
+    rng = np.random.default_rng(seed)
+    ci, cj, ck = _cell_ijk(nx, ny, nz)
+    active = np.ones(nx * ny * nz, dtype=np.uint8)
+    for j0, j1 in ((3, 7), (9, 13)):
+        active[(cj >= j0) & (cj < j1) & (ck >= 6) & (ck < 10)] = 0
+    mu = np.where((ci // 8) % 2 == 0, 1.0, 1e6)
+    f = _uniform_f(rng, (nx + 1) * (ny + 1) * (nz + 1), nrhs)
+    return Workload("beam128_layered", nx, ny, nz, 1 / 16, 1 / 16, 1 / 16, active, mu,
+                    np.ones(nx * ny * nz), 1e-6, (32, 4, 4), 1, 0.1, f)
+
+
+def cube48_blocks(seed=5):
+    """48^3 unit cube, mu^-1 log-uniform in [1,1e6] on 3x3x3-cell blocks,
+    gamma=1e-3, 8x8x8 boxes, overlap 1, f=(1,1,1)."""
+    n = 48
+    rng = np.random.default_rng(seed)
+    ci, cj, ck = _cell_ijk(n, n, n)
+    blk = 10.0 ** rng.uniform(0.0, 6.0, size=(16, 16, 16))
+    mu = blk[ck // 3, cj // 3, ci // 3]
+    return Workload("cube48_blocks", n, n, n, 1 / n, 1 / n, 1 / n,
+                    np.ones(n ** 3, dtype=np.uint8), mu, np.ones(n ** 3), 1e-3,
+                    (8, 8, 8), 1, 0.1, _const_f((n + 1) ** 3))
+
+
+def paper_beam(nsub=8, *, gamma=1e-3, tau=0.1):
+    """The paper's weak-scaling beam (N/2)x1x1 with h=1/16 and N boxes along
+    the length, one overlap layer, mu=eps=1, f=(1,1,1) (Section 4)."""
+    nx = 8 * nsub
+    return box(nx, 16, 16, h=1 / 16, parts=(nsub, 1, 1), overlap=1, gamma=gamma,
+               tau=tau, name=f"paper_beam_N{nsub}")
+
+
+def many_problems(count=256, seed=3):
+    """Batch of independent problems: n^3 cubes, n uniform in {8..24}, 1-2
+    cubic holes of side U{2..ceil(n/4)} at least one cell from the boundary,
+    mu^-1 in {1,1e2,1e4} on 4^3-cell blocks, gamma log-uniform in [1e-6,1],
+    boxes (px,py,pz) in {2,3,4}^3 with product in [8,64], overlap 1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    choices = [(a, b, c) for a in (2, 3, 4) for b in (2, 3, 4) for c in (2, 3, 4)
+               if 8 <= a * b * c <= 64]
+    for p in range(count):
+        n = int(rng.integers(8, 25))
+        holes = []
+        for _ in range(int(rng.integers(1, 3))):
+            s = int(rng.integers(2, -(-n // 4) + 1))
+            lo = [int(rng.integers(1, n - s)) for _ in range(3)]
+            holes.append(tuple((l, l + s) for l in lo))
+        ci, cj, ck = _cell_ijk(n, n, n)
+        nb = -(-n // 4)
+        blk = rng.choice(np.array([1.0, 1e2, 1e4]), size=(nb, nb, nb))
+        mu = blk[ck // 4, cj // 4, ci // 4]
+        gamma = float(10.0 ** rng.uniform(-6.0, 0.0))
+        parts = choices[int(rng.integers(0, len(choices)))]
+        w = box(n, n, n, parts=parts, overlap=1, gamma=gamma, tau=0.1, mu_inv=mu,
+                holes=holes, name=f"batch{p}_n{n}")
+        out.append(w)
+    return out
