@@ -1,0 +1,197 @@
+/*
+ * geneo.h -- C-ABI of the GB300 (sm_103a) library for the two-level
+ * GenEO-type additive Schwarz preconditioner of positive Maxwell problems.
+ *
+ * Method: Bootland, Dolean, Nataf, Tournier, "A robust and adaptive
+ * GenEO-type domain decomposition preconditioner for H(curl) problems in
+ * three-dimensional general topologies" (arXiv 2311.18783).
+ *
+ *   problem   curl(mu^-1 curl E) + gamma eps E = f, E x n = 0
+ *             (Sec. 1, eq. "positivemaxwell"), discretised with lowest-order
+ *             Nedelec edge elements into A U = (K + gamma M) U = f
+ *             (Sec. 1, eq. "discretemaxwell"; Sec. 2, eq. "bilinearformposmax");
+ *   method    M^-1_AS,2 = Z E^-1 Z^T + (I - P0) sum_i R_i^T A_i^-1 R_i (I - P0^T)
+ *             (Sec. 2, eq. "AS2"; closed form at the end of Sec. 3.2), with
+ *             Z spanning the split near-kernel space (Sec. 2, definition
+ *             "near-kernelCS") plus the GenEO eigenvectors of the filtered
+ *             generalised eigenproblem (Sec. 3.2, GEVP "tauthresholdAS",
+ *             eq. "eigAtildeBAS") with eigenvalues above the threshold;
+ *   Krylov    preconditioned conjugate gradients (A is SPD, Sec. 2, and
+ *             M^-1_AS,2 is symmetric, eq. "AS2").
+ *
+ * Mesh: a structured grid of nx*ny*nz cubic cells, each split into six Kuhn
+ * tetrahedra; cells are numbered c = i + nx*(j + ny*k) and vertices
+ * v = i + (nx+1)*(j + (ny+1)*k).  Edges run from the lower to the higher
+ * vertex id along one of seven positive directions DIRS = {x, y, z, x+y,
+ * x+z, y+z, x+y+z} (in that order), so an edge is identified by its slot
+ * (v, d).  Unknowns are the edges that do not lie on the boundary (Dirichlet
+ * E x n = 0, eliminated), numbered in lexicographic (tail, head) order.
+ *
+ * Conventions of every entry point:
+ *  - "host" pointers are caller-owned CPU memory, only read (or written)
+ *    during the call; "device" pointers are caller-owned CUDA global memory
+ *    on the context's device, of float64 unless stated otherwise;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream); work is enqueued on it and the call returns without waiting,
+ *    except where a host result is produced (noted per call);
+ *  - the return value is GENEO_OK (0) on success, a positive warning, or a
+ *    negative error code; geneo_last_error() gives a message.  No exception
+ *    or abort crosses this interface.
+ *  - all memory the context needs is allocated in geneo_setup and released
+ *    by geneo_destroy.  A context is not thread safe; calls that use the
+ *    same context must not overlap.
+ */
+#ifndef GENEO_H
+#define GENEO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GENEO_OK 0
+#define GENEO_NOT_CONVERGED 1      /* warning: maxit reached, x holds the last iterate */
+#define GENEO_ERR_INVALID_ARG (-1)
+#define GENEO_ERR_CUDA (-2)
+#define GENEO_ERR_OOM (-3)
+#define GENEO_ERR_NOT_SPD (-4)     /* a pivot of a factorisation was not positive */
+#define GENEO_ERR_BREAKDOWN (-5)   /* PCG: p^T A p <= 0 or not finite */
+#define GENEO_ERR_TIMEOUT (-6)     /* a bounded device wait gave up */
+#define GENEO_ERR_STATE (-7)       /* call not valid in the context's state */
+
+#define GENEO_PREC_FP64 0          /* local factors stored and applied in float64 */
+#define GENEO_PREC_FP32 1          /* split factors: gradient part float64, rest float32 */
+
+#define GENEO_COARSE_NONE 0        /* one-level additive Schwarz (eq. "AS") */
+#define GENEO_COARSE_SNK 1         /* split near-kernel space (definition "near-kernelCS") */
+
+#define GENEO_TAU_RECIPROCAL 0     /* select lambda > 1/tau */
+#define GENEO_TAU_PAPER 1          /* select lambda > tau (GEVP "tauthresholdAS" literally) */
+
+/* Opaque context: owns every device allocation of one set-up problem. */
+typedef struct geneo_ctx geneo_ctx;
+
+/* Problem description; arrays are host memory, copied during geneo_setup. */
+typedef struct {
+  int32_t nx, ny, nz;        /* cells per axis, each >= 1 */
+  double hx, hy, hz;         /* cell edge lengths, > 0 */
+  const uint8_t *active;     /* [nx*ny*nz] 1 = cell present, 0 = hole */
+  const double *mu_inv;      /* [nx*ny*nz] mu^-1 per cell, > 0 */
+  const double *eps;         /* [nx*ny*nz] eps per cell, > 0 */
+  double gamma;              /* > 0 */
+  int32_t px, py, pz;        /* boxes per axis; cell (i,j,k) is in box (i*px/nx, j*py/ny, k*pz/nz) */
+  int32_t overlap;           /* layers of cells added around each box (vertex neighbours), >= 1 */
+  double tau;                /* GenEO threshold, > 0, read with options.tau_convention */
+} geneo_problem;
+
+typedef struct {
+  int32_t precision;         /* GENEO_PREC_* */
+  int32_t coarse;            /* GENEO_COARSE_* */
+  int32_t geneo;             /* 1: add GenEO eigenvectors to the coarse space */
+  int32_t tau_convention;    /* GENEO_TAU_* */
+  int32_t lobpcg_block;      /* block size of the batched LOBPCG (>= 1) */
+  int32_t lobpcg_maxit;      /* iterations per block before giving up */
+  double lobpcg_tol;         /* relative eigen-residual tolerance */
+  uint64_t seed;             /* initial LOBPCG blocks (counter-based hash) */
+} geneo_options;
+
+typedef struct {
+  int64_t nverts, ncells, ntets, nedges;
+  int64_t n;                 /* unknowns (interior edges) */
+  int64_t nnz;               /* nonzeros of A (CSR, both triangles) */
+  int32_t nsub;              /* subdomains */
+  int32_t k0, k1;            /* Sec. 2, eq. "k0", and the maximal cell multiplicity */
+  int64_t sum_ni;            /* sum of n_i */
+  int64_t max_ni;
+  int64_t n0;                /* coarse dimension */
+  int64_t n0_snk;            /* split near-kernel columns */
+  int64_t n0_geneo;          /* GenEO columns kept */
+  int64_t local_factor_bytes;  /* bytes of the stored local factors */
+  int64_t coarse_factor_bytes; /* bytes of the stored coarse factor */
+  double setup_seconds;      /* wall time of geneo_setup */
+} geneo_sizes;
+
+typedef struct {
+  int32_t iters;
+  double relres;             /* ||b - A x|| / ||b|| of the PCG recurrence at exit */
+  double seconds;            /* wall time of the solve, including the final synchronisation */
+} geneo_solve_info;
+
+/* Fills `opt` with the defaults: FP64, SNK coarse space, GenEO on,
+ * reciprocal tau, LOBPCG block 8, 200 iterations, tolerance 1e-8, seed 1. */
+void geneo_default_options(geneo_options *opt);
+
+/* Builds topology, decomposition, A, the local factors, the GenEO
+ * eigenvectors and the coarse factor on the current CUDA device (Sec. 2-3).
+ * Blocks until the set-up has finished.  On success *out owns all device
+ * memory of the problem.  Errors: INVALID_ARG (bad sizes, gamma <= 0,
+ * overlap < 1, empty mesh), OOM, CUDA, NOT_SPD. */
+int geneo_setup(const geneo_problem *prob, const geneo_options *opt, geneo_ctx **out);
+
+/* Releases every resource of the context (NULL is allowed). */
+void geneo_destroy(geneo_ctx *ctx);
+
+/* Host copy of the sizes. */
+int geneo_query(const geneo_ctx *ctx, geneo_sizes *out);
+
+/* b_dev[n] = load l(v) = int f . W_e (Sec. 2) of the source field given per
+ * edge slot: f_slot_host is [nverts][7][3] float64 host memory (slots that
+ * are not edges are ignored).  f is read as the Whitney interpolant with
+ * dofs f_e . (x_head - x_tail), so b = M_1 c (exact for constant f). */
+int geneo_assemble_rhs(geneo_ctx *ctx, const double *f_slot_host, double *b_dev, void *stream);
+
+/* y_dev[n] = A x_dev (Sec. 1, eq. "discretemaxwell"), CSR SpMV. */
+int geneo_spmv(geneo_ctx *ctx, const double *x_dev, double *y_dev, void *stream);
+
+/* w_dev[n] = sum_i R_i^T A_i^-1 R_i r_dev (Sec. 2, eq. "AS"). */
+int geneo_local_solve(geneo_ctx *ctx, const double *r_dev, double *w_dev, void *stream);
+
+/* y_dev[n] = Z E^-1 Z^T r_dev, E = Z^T A Z (Sec. 2); zero if there is no coarse space. */
+int geneo_coarse_solve(geneo_ctx *ctx, const double *r_dev, double *y_dev, void *stream);
+
+/* z_dev[n] = M^-1_AS,2 r_dev (Sec. 2, eq. "AS2"; closed form at the end of Sec. 3.2). */
+int geneo_apply_preconditioner(geneo_ctx *ctx, const double *r_dev, double *z_dev, void *stream);
+
+/* PCG on A x = b from x = 0 until ||r||/||b|| <= tol or maxit iterations;
+ * b_dev, x_dev device [n].  Synchronises `stream` once per iteration to test
+ * convergence; `info` (host, may be NULL) receives the iteration count,
+ * final relative residual and wall time.  Returns OK, NOT_CONVERGED or
+ * BREAKDOWN. */
+int geneo_solve(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol, int32_t maxit,
+                geneo_solve_info *info, void *stream);
+
+/* Same solve with host buffers: copies b_host[n] to the device, solves, and
+ * copies x back to x_host[n] before returning. */
+int geneo_solve_host(geneo_ctx *ctx, const double *b_host, double *x_host, double tol,
+                     int32_t maxit, geneo_solve_info *info, void *stream);
+
+/* Copies the internal array `name` into host memory dst (capacity bytes);
+ * *size receives the byte size (call with dst = NULL to query).  For parity
+ * tests of the integer and floating-point set-up data.  Names:
+ *  "edges"       int32 [nedges][2]  tail, head vertex ids
+ *  "dir_edge"    uint8 [nedges]     1 = Dirichlet edge
+ *  "dof_edge"    int32 [n]          edge id of each unknown
+ *  "dof_vert"    int32 [nvdofs]     interior vertices
+ *  "A_rowptr"    int32 [n+1], "A_col" int32 [nnz], "A_val" float64 [nnz]
+ *  "N_off"       int64 [nsub+1], "N_idx" int32 [sum n_i]  R_i index sets
+ *  "owner"       int32 [n]          subdomain owning each unknown (partition of unity)
+ *  "snk_sub", "snk_vert"  int32 [n0_snk]  subdomain and vertex of each SNK column
+ *  "geneo_sub"   int32 [n0_geneo], "geneo_lambda" float64 [n0_geneo]
+ *  "geneo_found" int32 [nsub]       eigenvalues above the threshold found per subdomain
+ *  "Zcol_ptr" int64 [n0+1], "Zcol_row" int32 [nnzZ], "Zcol_val" float64 [nnzZ]
+ *  "k0k1"        int32 [2]
+ * Returns INVALID_ARG for an unknown name or a too small buffer. */
+int geneo_export(const geneo_ctx *ctx, const char *name, void *dst, int64_t capacity,
+                 int64_t *size);
+
+/* Message of the last error of this thread. */
+const char *geneo_last_error(void);
+
+/* Static text of a status code. */
+const char *geneo_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENEO_H */

@@ -159,12 +159,29 @@ def xi_projector(Ai, Gi):
     return Gi @ sla.solve(S, Gi.T @ Ai, assume_a='pos')
 
 
-def local_gevp(mesh, A, AT, dec, j):
+def xi_projector_curl(mesh, w, dec, i, Gi):
+    """xi_0i with G_i^T A_i formed through the curl operator:
+    G_i^T A_i = (C R_i^T G_i)^T (C R_i^T) + gamma G_i^T M_i, which equals the
+    assembled product but keeps its small (order gamma) entries accurate."""
+    from .fem import curl_operator, assemble_mass
+    if Gi.shape[1] == 0:
+        return np.zeros((len(dec.N[i]), len(dec.N[i])))
+    Ni = dec.N[i]
+    Ci = curl_operator(mesh, w)[:, Ni]
+    Mi = assemble_mass(mesh, w)[Ni][:, Ni]
+    CG = Ci @ Gi
+    GtA = (Ci.T @ CG).T + w.gamma * (Mi @ Gi).T
+    S = GtA @ Gi
+    S = 0.5 * (S + S.T)
+    return Gi @ sla.solve(S, GtA, assume_a='pos')
+
+
+def local_gevp(mesh, w, A, AT, dec, j):
     """Dense solve of GEVP "tauthresholdAS" (eq. "eigAtildeBAS") on Omega_j."""
     Ai = local_dirichlet(A, dec, j)
     Aneu = local_neumann(mesh, AT, dec, j)
     Gi, _ = local_gradient(mesh, dec, j)
-    xi = xi_projector(Ai, Gi)
+    xi = xi_projector_curl(mesh, w, dec, j, Gi)
     Ixi = np.eye(len(Ai)) - xi
     Dj = dec.D[j]
     L = Ixi.T @ (Dj[:, None] * Ai * Dj[None, :]) @ Ixi
@@ -192,13 +209,13 @@ def tau_paper(tau, convention="reciprocal"):
     raise ValueError(convention)
 
 
-def geneo_columns(mesh, A, AT, dec, tau_p, gevps=None):
+def geneo_columns(mesh, w, A, AT, dec, tau_p, gevps=None):
     """Columns R_j^T D_j (I - xi_0j) V_jk for lambda_jk > tau_p, per subdomain
     in descending lambda order.  Returns (cols, gevps)."""
     cols = []
     out = []
     for j in range(dec.nsub):
-        g = gevps[j] if gevps is not None else local_gevp(mesh, A, AT, dec, j)
+        g = gevps[j] if gevps is not None else local_gevp(mesh, w, A, AT, dec, j)
         out.append(g)
         sel = np.nonzero(g.lam > tau_p)[0]
         Ixi = np.eye(len(g.Ai)) - g.xi
@@ -220,30 +237,45 @@ def assemble_Z(n, cols):
 DEP_TOL = 1e-8
 
 
-def independent_geneo(A, Zg, Zh):
-    """Indices of the GenEO columns kept by the ordered Cholesky of the Schur
-    complement of the GenEO block (pivot >= DEP_TOL * diagonal)."""
-    if Zh.shape[1] == 0:
+def galerkin(mesh, w, X, Y=None):
+    """X^T A Y summed element by element, K-part through the curl operator:
+    (C X)^T (C Y) + gamma X^T M Y.  Equal to X^T A Y; for gradient-like
+    columns it avoids the cancellation of K G = 0 inside assembled A."""
+    from .fem import curl_operator, assemble_mass
+    Y = X if Y is None else Y
+    Cm = curl_operator(mesh, w)
+    M = assemble_mass(mesh, w)
+    CX, CY = Cm @ X, Cm @ Y
+    out = CX.T @ CY + w.gamma * (X.T @ (M @ Y))
+    return out.toarray() if sp.issparse(out) else np.asarray(out)
+
+
+def coarse_matrix(mesh, w, Z):
+    """E = Z^T A Z (Sec. 2), element by element (see galerkin)."""
+    E = galerkin(mesh, w, Z)
+    return 0.5 * (E + E.T)
+
+
+def independent_geneo(E, n_snk):
+    """Indices (relative to the GenEO block) of the GenEO columns kept by
+    the ordered Cholesky of the Schur complement of the GenEO block of E
+    (pivot >= DEP_TOL * diagonal).  E covers [SNK | GenEO candidates]."""
+    m = E.shape[0] - n_snk
+    if m == 0:
         return np.zeros(0, np.int64)
-    AZh = A @ Zh
-    Ehh = (Zh.T @ AZh)
-    Ehh = Ehh.toarray() if sp.issparse(Ehh) else np.asarray(Ehh)
-    Ehh = 0.5 * (Ehh + Ehh.T)
+    Ehh = E[n_snk:, n_snk:]
     diag = np.diag(Ehh).copy()
-    if Zg is not None and Zg.shape[1] > 0:
-        Egg = (Zg.T @ (A @ Zg))
-        Egh = Zg.T @ AZh
-        Egh = Egh.toarray() if sp.issparse(Egh) else np.asarray(Egh)
-        if Egg.shape[0] <= 6000:
-            Egg = Egg.toarray() if sp.issparse(Egg) else Egg
-            S = Ehh - Egh.T @ sla.cho_solve(sla.cho_factor(0.5 * (Egg + Egg.T)), Egh)
+    if n_snk > 0:
+        Egg = E[:n_snk, :n_snk]
+        Egh = E[:n_snk, n_snk:]
+        if n_snk <= 6000:
+            S = Ehh - Egh.T @ sla.cho_solve(sla.cho_factor(Egg), Egh)
         else:
             import scipy.sparse.linalg as spla
             S = Ehh - Egh.T @ spla.splu(sp.csc_matrix(Egg)).solve(Egh)
     else:
         S = Ehh
     S = 0.5 * (S + S.T)
-    m = len(S)
     keep = []
     L = np.zeros((m, m))
     for k in range(m):
@@ -256,9 +288,3 @@ def independent_geneo(A, Zg, Zh):
         L[rest, k] = (S[rest, k] - L[np.ix_(rest, keep)] @ L[k, keep]) / d
         keep.append(k)
     return np.array(keep, dtype=np.int64)
-
-
-def coarse_matrix(A, Z):
-    """E = Z^T A Z (Sec. 2)."""
-    E = (Z.T @ (A @ Z)).toarray() if sp.issparse(Z) else Z.T @ (A @ Z)
-    return 0.5 * (E + E.T)

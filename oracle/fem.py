@@ -123,3 +123,35 @@ def assemble_rhs(mesh, w):
         c = np.einsum('ei,ei->e', fe, t)
         out.append((M1 @ c)[mesh.dof_edge])
     return np.array(out)
+
+
+def curl_operator(mesh, w, tet_subset=None):
+    """Sparse C (3 ntets x ndofs): row 3T+d holds sqrt(mu^-1_T |T|) times the
+    d-th component of curl W_e for the unknowns e of T, so that
+    K = C^T C (the curl-curl part of eq. "bilinearformposmax").  Products
+    C Z stay accurate for gradient columns: the curl of a gradient is a
+    rounding-size vector that enters K-energies squared."""
+    g, vol = barycentric_gradients(mesh.coords[mesh.tets])
+    mu, _ = tet_coefficients(mesh, w)
+    sc = np.sqrt(mu * vol)
+    nt = len(mesh.tets)
+    rows, cols, vals = [], [], []
+    for e, (a, b) in enumerate(LOCAL_EDGES):
+        cv = 2.0 * np.cross(g[:, a, :], g[:, b, :]) * sc[:, None]
+        dof = mesh.edge_dof[mesh.tet_edges[:, e]]
+        ok = dof >= 0
+        if tet_subset is not None:
+            ok &= tet_subset
+        for d in range(3):
+            rows.append(3 * np.nonzero(ok)[0] + d)
+            cols.append(dof[ok])
+            vals.append(cv[ok, d])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(3 * nt, mesh.ndofs))
+
+
+def assemble_mass(mesh, w):
+    """eps-weighted mass matrix over interior dofs (the M of A = K + gamma M)."""
+    mu, ep = tet_coefficients(mesh, w)
+    _, M, _ = element_matrices(mesh.coords[mesh.tets], mu, ep)
+    return mirror_upper(assemble_edges(mesh, M)[mesh.dof_edge][:, mesh.dof_edge])

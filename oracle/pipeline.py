@@ -10,7 +10,7 @@ from .mesh import build_mesh
 from .fem import assemble_A, assemble_rhs, local_element_A
 from .dd import decompose
 from .coarse import (snk_columns, nk_columns, geneo_columns, assemble_Z, tau_paper,
-                     independent_geneo)
+                     independent_geneo, coarse_matrix)
 from .solver import build_preconditioner, pcg
 
 
@@ -49,14 +49,19 @@ def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
         raise ValueError(coarse)
     tp = tau_paper(w.tau, tau_convention)
     gcols, gevps = ([], None)
+    E = None
     if geneo:
-        gcols, gevps = geneo_columns(mesh, A, AT, dec, tp)
+        gcols, gevps = geneo_columns(mesh, w, A, AT, dec, tp)
         if gcols:
-            Zg = assemble_Z(n, cols) if cols else None
-            keep = independent_geneo(A, Zg, assemble_Z(n, gcols))
+            E = coarse_matrix(mesh, w, assemble_Z(n, cols + gcols))
+            keep = independent_geneo(E, len(cols))
+            sel = np.concatenate([np.arange(len(cols)), len(cols) + keep])
+            E = E[np.ix_(sel, sel)]
             gcols = [gcols[k] for k in keep.tolist()]
     Z = assemble_Z(n, cols + gcols) if (cols or gcols) else None
-    M = build_preconditioner(A, dec, Z)
+    if Z is not None and E is None:
+        E = coarse_matrix(mesh, w, Z)
+    M = build_preconditioner(A, dec, Z, E=E)
     return OracleProblem(w, mesh, A, AT, b, dec, cols, gcols, gevps, Z, M, tp)
 
 

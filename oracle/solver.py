@@ -59,16 +59,19 @@ def factor_sparse(E):
     return lu.solve
 
 
-def build_preconditioner(A, dec, Z, local_mats=None):
+def build_preconditioner(A, dec, Z, local_mats=None, E=None):
+    """Local Cholesky factors of A_i and the factor of E = Z^T A Z (computed
+    from the assembled A unless given)."""
     Ainv = []
     for i in range(dec.nsub):
         Ai = A[dec.N[i]][:, dec.N[i]].toarray() if local_mats is None else local_mats[i]
         Ainv.append(sla.cho_factor(Ai, lower=True))
     if Z is None or Z.shape[1] == 0:
         return TwoLevel(A, dec.N, Ainv, None, None)
-    E = (Z.T @ (A @ Z))
-    E = E.toarray() if sp.issparse(E) else E
-    E = 0.5 * (E + E.T)
+    if E is None:
+        E = (Z.T @ (A @ Z))
+        E = E.toarray() if sp.issparse(E) else E
+        E = 0.5 * (E + E.T)
     fact = factor_dense(E) if E.shape[0] <= 6000 else factor_sparse(E)
     return TwoLevel(A, dec.N, Ainv, Z, fact)
 

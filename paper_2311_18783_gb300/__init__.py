@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) library for the GenEO-type two-level additive Schwarz
+preconditioner of positive Maxwell problems (arXiv 2311.18783).
+
+The computation lives in the C-ABI shared library ``libgeneo.so`` (see
+``include/geneo.h``); this package only marshals arguments.  Importing it
+loads the library and raises if it has not been built: there is no CPU
+fallback.
+"""
+from .api import (GeneoError, Options, Solver, load_library, PREC_FP64, PREC_FP32,
+                  COARSE_NONE, COARSE_SNK, TAU_RECIPROCAL, TAU_PAPER)
+
+__all__ = ["GeneoError", "Options", "Solver", "load_library", "PREC_FP64", "PREC_FP32",
+           "COARSE_NONE", "COARSE_SNK", "TAU_RECIPROCAL", "TAU_PAPER"]

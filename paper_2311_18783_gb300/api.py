@@ -1,0 +1,231 @@
+"""ctypes binding of include/geneo.h.  Device buffers are torch CUDA tensors
+(float64, contiguous); streams are torch streams.  Every entry point has the
+same name as its C function without the ``geneo_`` prefix."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgeneo.so")
+
+PREC_FP64, PREC_FP32 = 0, 1
+COARSE_NONE, COARSE_SNK = 0, 1
+TAU_RECIPROCAL, TAU_PAPER = 0, 1
+NOT_CONVERGED = 1
+
+
+class GeneoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"geneo status {status}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
+                ("active", C.POINTER(C.c_uint8)), ("mu_inv", C.POINTER(C.c_double)),
+                ("eps", C.POINTER(C.c_double)), ("gamma", C.c_double),
+                ("px", C.c_int32), ("py", C.c_int32), ("pz", C.c_int32),
+                ("overlap", C.c_int32), ("tau", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("coarse", C.c_int32), ("geneo", C.c_int32),
+                ("tau_convention", C.c_int32), ("lobpcg_block", C.c_int32),
+                ("lobpcg_maxit", C.c_int32), ("lobpcg_tol", C.c_double), ("seed", C.c_uint64)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("nverts", C.c_int64), ("ncells", C.c_int64), ("ntets", C.c_int64),
+                ("nedges", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("nsub", C.c_int32), ("k0", C.c_int32), ("k1", C.c_int32),
+                ("sum_ni", C.c_int64), ("max_ni", C.c_int64), ("n0", C.c_int64),
+                ("n0_snk", C.c_int64), ("n0_geneo", C.c_int64),
+                ("local_factor_bytes", C.c_int64), ("coarse_factor_bytes", C.c_int64),
+                ("setup_seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("relres", C.c_double), ("seconds", C.c_double)]
+
+
+_LIB = None
+
+# exported C functions and their argument types
+_SIGS = {
+    "geneo_default_options": (None, [C.POINTER(Options)]),
+    "geneo_setup": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+    "geneo_destroy": (None, [C.c_void_p]),
+    "geneo_query": (C.c_int, [C.c_void_p, C.POINTER(Sizes)]),
+    "geneo_assemble_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "geneo_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "geneo_local_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "geneo_coarse_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "geneo_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "geneo_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
+                              C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
+                                   C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_export": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64,
+                               C.POINTER(C.c_int64)]),
+    "geneo_last_error": (C.c_char_p, []),
+    "geneo_strerror": (C.c_char_p, [C.c_int]),
+}
+
+_EXPORT_DTYPES = {
+    "edges": np.int32, "dir_edge": np.uint8, "dof_edge": np.int32, "dof_vert": np.int32,
+    "A_rowptr": np.int32, "A_col": np.int32, "A_val": np.float64, "N_off": np.int64,
+    "N_idx": np.int32, "owner": np.int32, "snk_sub": np.int32, "snk_vert": np.int32,
+    "geneo_sub": np.int32, "geneo_lambda": np.float64, "geneo_found": np.int32,
+    "Zcol_ptr": np.int64, "Zcol_row": np.int32, "Zcol_val": np.float64, "k0k1": np.int32,
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load libgeneo.so; raises OSError if it is missing (build it with
+    ``__graft_entry__.build()`` or ``python paper_2311_18783_gb300/build.py``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: the CUDA library must be built first")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status):
+    if status < 0:
+        msg = _LIB.geneo_last_error().decode()
+        raise GeneoError(status, msg)
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def default_options(**kw):
+    lib = load_library()
+    o = Options()
+    lib.geneo_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One set-up problem on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, h, active, mu_inv, eps, gamma, parts, overlap, tau,
+                 options=None, **opt_kw):
+        lib = load_library()
+        self._keep = [np.ascontiguousarray(active, dtype=np.uint8),
+                      np.ascontiguousarray(mu_inv, dtype=np.float64),
+                      np.ascontiguousarray(eps, dtype=np.float64)]
+        hx, hy, hz = (h, h, h) if np.isscalar(h) else h
+        p = Problem(nx, ny, nz, hx, hy, hz,
+                    self._keep[0].ctypes.data_as(C.POINTER(C.c_uint8)),
+                    self._keep[1].ctypes.data_as(C.POINTER(C.c_double)),
+                    self._keep[2].ctypes.data_as(C.POINTER(C.c_double)),
+                    gamma, parts[0], parts[1], parts[2], overlap, tau)
+        o = options if options is not None else default_options(**opt_kw)
+        ctx = C.c_void_p()
+        _check(lib.geneo_setup(C.byref(p), C.byref(o), C.byref(ctx)))
+        self._ctx = ctx
+        self.options = o
+        self.sizes = self.query()
+        self.n = self.sizes["n"]
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active, w.mu_inv, w.eps, w.gamma,
+                   w.parts, w.overlap, w.tau, **kw)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            _LIB.geneo_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self):
+        s = Sizes()
+        _check(_LIB.geneo_query(self._ctx, C.byref(s)))
+        return s.as_dict()
+
+    def assemble_rhs(self, f_slot, b, stream=None):
+        """f_slot: host float64 [nverts, 7, 3]; b: CUDA tensor [n]."""
+        f = np.ascontiguousarray(f_slot, dtype=np.float64)
+        _check(_LIB.geneo_assemble_rhs(self._ctx, f.ctypes.data_as(C.c_void_p), _ptr(b),
+                                       _stream(stream)))
+        return b
+
+    def spmv(self, x, y, stream=None):
+        _check(_LIB.geneo_spmv(self._ctx, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def local_solve(self, r, w, stream=None):
+        _check(_LIB.geneo_local_solve(self._ctx, _ptr(r), _ptr(w), _stream(stream)))
+        return w
+
+    def coarse_solve(self, r, y, stream=None):
+        _check(_LIB.geneo_coarse_solve(self._ctx, _ptr(r), _ptr(y), _stream(stream)))
+        return y
+
+    def apply_preconditioner(self, r, z, stream=None):
+        _check(_LIB.geneo_apply_preconditioner(self._ctx, _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
+    def solve(self, b, x, tol=1e-8, maxit=1000, stream=None):
+        info = SolveInfo()
+        st = _check(_LIB.geneo_solve(self._ctx, _ptr(b), _ptr(x), tol, maxit, C.byref(info),
+                                     _stream(stream)))
+        return {"status": st, "iters": info.iters, "relres": info.relres,
+                "seconds": info.seconds}
+
+    def solve_host(self, b, tol=1e-8, maxit=1000, stream=None, out=None):
+        """b: host float64 array [n] (pinned tensors are fastest).  Returns x."""
+        import torch
+        bh = b if isinstance(b, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(b))
+        xh = out if out is not None else torch.empty_like(bh)
+        info = SolveInfo()
+        st = _check(_LIB.geneo_solve_host(self._ctx, C.c_void_p(bh.data_ptr()),
+                                          C.c_void_p(xh.data_ptr()), tol, maxit, C.byref(info),
+                                          _stream(stream)))
+        return xh, {"status": st, "iters": info.iters, "relres": info.relres,
+                    "seconds": info.seconds}
+
+    def export(self, name):
+        size = C.c_int64(0)
+        _check(_LIB.geneo_export(self._ctx, name.encode(), None, 0, C.byref(size)))
+        dt = np.dtype(_EXPORT_DTYPES[name])
+        out = np.empty(size.value // dt.itemsize, dtype=dt)
+        _check(_LIB.geneo_export(self._ctx, name.encode(), out.ctypes.data_as(C.c_void_p),
+                                 size.value, C.byref(size)))
+        return out

@@ -1,0 +1,264 @@
+// C-ABI entry points (include/geneo.h): argument checks, status codes and
+// the thread-local error message.  No exception crosses this boundary.
+#include <cstring>
+#include <string>
+
+#include "setup.hpp"
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string &msg) {
+  g_last_error = msg;
+  return status;
+}
+
+template <class F>
+int guarded(F &&f) {
+  try {
+    return f();
+  } catch (const geneo::Error &e) {
+    return fail(e.status, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(GENEO_ERR_OOM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(GENEO_ERR_CUDA, e.what());
+  } catch (...) {
+    return fail(GENEO_ERR_CUDA, "unknown failure");
+  }
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+}  // namespace
+
+geneo_ctx::~geneo_ctx() {
+  if (h_scal) cudaFreeHost(h_scal);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+extern "C" {
+
+void geneo_default_options(geneo_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = GENEO_PREC_FP64;
+  o->coarse = GENEO_COARSE_SNK;
+  o->geneo = 1;
+  o->tau_convention = GENEO_TAU_RECIPROCAL;
+  o->lobpcg_block = 8;
+  o->lobpcg_maxit = 200;
+  o->lobpcg_tol = 1e-8;
+  o->seed = 1;
+}
+
+int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **out) {
+  if (!p || !out) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->hx > 0) || !(p->hy > 0) || !(p->hz > 0))
+    return fail(GENEO_ERR_INVALID_ARG, "grid sizes must be positive");
+  if (!p->active || !p->mu_inv || !p->eps) return fail(GENEO_ERR_INVALID_ARG, "null array");
+  if (!(p->gamma > 0)) return fail(GENEO_ERR_INVALID_ARG, "gamma must be > 0");
+  if (p->overlap < 1) return fail(GENEO_ERR_INVALID_ARG, "overlap must be >= 1");
+  if (p->px < 1 || p->py < 1 || p->pz < 1 || p->px > p->nx || p->py > p->ny || p->pz > p->nz)
+    return fail(GENEO_ERR_INVALID_ARG, "box counts must lie in [1, cells per axis]");
+  if (!(p->tau > 0)) return fail(GENEO_ERR_INVALID_ARG, "tau must be > 0");
+  const int64_t nc = (int64_t)p->nx * p->ny * p->nz;
+  if (nc > (int64_t)1 << 28) return fail(GENEO_ERR_INVALID_ARG, "mesh too large for int32 indices");
+  for (int64_t c = 0; c < nc; ++c)
+    if (p->active[c] && (!(p->mu_inv[c] > 0) || !(p->eps[c] > 0)))
+      return fail(GENEO_ERR_INVALID_ARG, "mu^-1 and eps must be > 0 on active cells");
+  geneo_options o;
+  geneo_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32)
+    return fail(GENEO_ERR_INVALID_ARG, "unknown precision");
+  if (o.coarse != GENEO_COARSE_NONE && o.coarse != GENEO_COARSE_SNK)
+    return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
+  if (o.lobpcg_block < 1 || o.lobpcg_block > 32 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
+    return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");
+  return guarded([&]() {
+    auto c = new geneo_ctx();
+    try {
+      c->nx = p->nx;
+      c->ny = p->ny;
+      c->nz = p->nz;
+      c->h[0] = p->hx;
+      c->h[1] = p->hy;
+      c->h[2] = p->hz;
+      c->gamma = p->gamma;
+      c->tau = p->tau;
+      c->tau_p = o.tau_convention == GENEO_TAU_PAPER ? p->tau : 1.0 / p->tau;
+      c->px = p->px;
+      c->py = p->py;
+      c->pz = p->pz;
+      c->overlap = p->overlap;
+      c->active.assign(p->active, p->active + nc);
+      c->mu_inv.assign(p->mu_inv, p->mu_inv + nc);
+      c->eps.assign(p->eps, p->eps + nc);
+      c->opt = o;
+      GENEO_CUDA(cudaGetDevice(&c->device));
+      c->sm_count = geneo::device_sm_count();
+      GENEO_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      geneo::setup_all(c);
+    } catch (...) {
+      delete c;
+      throw;
+    }
+    *out = c;
+    return GENEO_OK;
+  });
+}
+
+void geneo_destroy(geneo_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  delete c;
+}
+
+int geneo_query(const geneo_ctx *c, geneo_sizes *o) {
+  if (!c || !o) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  std::memset(o, 0, sizeof(*o));
+  o->nverts = c->topo.nverts;
+  o->ncells = c->topo.ncells;
+  o->ntets = c->topo.ntets();
+  o->nedges = c->topo.nedges();
+  o->n = c->topo.ndofs();
+  o->nnz = c->topo.nnz();
+  o->nsub = c->dec.nsub;
+  o->k0 = c->dec.k0;
+  o->k1 = c->dec.k1;
+  o->sum_ni = c->dec.N_off.empty() ? 0 : c->dec.N_off.back();
+  for (int i = 0; i < c->dec.nsub; ++i) o->max_ni = std::max<int64_t>(o->max_ni, c->dec.ni(i));
+  o->n0 = c->n0;
+  o->n0_snk = c->n0_snk;
+  o->n0_geneo = c->n0_geneo;
+  o->local_factor_bytes = c->loc_f64.bytes() + c->loc_f32.bytes();
+  o->coarse_factor_bytes = c->crs_f64.bytes();
+  o->setup_seconds = c->setup_seconds;
+  return GENEO_OK;
+}
+
+int geneo_assemble_rhs(geneo_ctx *c, const double *f, double *b, void *s) {
+  if (!c || !f || !b) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::assemble_rhs(c, f, b, as_stream(s));
+    return GENEO_OK;
+  });
+}
+
+int geneo_spmv(geneo_ctx *c, const double *x, double *y, void *s) {
+  if (!c || !x || !y) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::spmv(c, x, y, as_stream(s));
+    return GENEO_OK;
+  });
+}
+
+int geneo_local_solve(geneo_ctx *c, const double *r, double *w, void *s) {
+  if (!c || !r || !w) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::local_solve(c, r, w, as_stream(s));
+    return GENEO_OK;
+  });
+}
+
+int geneo_coarse_solve(geneo_ctx *c, const double *r, double *y, void *s) {
+  if (!c || !r || !y) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::coarse_solve(c, r, y, as_stream(s));
+    return GENEO_OK;
+  });
+}
+
+int geneo_apply_preconditioner(geneo_ctx *c, const double *r, double *z, void *s) {
+  if (!c || !r || !z) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::apply_preconditioner(c, r, z, as_stream(s));
+    return GENEO_OK;
+  });
+}
+
+int geneo_solve(geneo_ctx *c, const double *b, double *x, double tol, int32_t maxit,
+                geneo_solve_info *info, void *s) {
+  if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
+  return guarded([&]() { return geneo::pcg(c, b, x, tol, maxit, info, as_stream(s)); });
+}
+
+int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int32_t maxit,
+                     geneo_solve_info *info, void *s) {
+  if (!c || !bh || !xh) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
+  return guarded([&]() {
+    cudaStream_t st = as_stream(s);
+    const int64_t n = c->topo.ndofs();
+    // b and x live in two vectors the context reserves for this call
+    GENEO_CUDA(cudaMemcpyAsync(c->h_b.p, bh, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    const int rc = geneo::pcg(c, c->h_b.p, c->h_x.p, tol, maxit, info, st);
+    GENEO_CUDA(cudaMemcpyAsync(xh, c->h_x.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    GENEO_CUDA(cudaStreamSynchronize(st));
+    return rc;
+  });
+}
+
+int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, int64_t *size) {
+  if (!c || !name) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() -> int {
+    std::vector<unsigned char> buf;
+    auto put = [&](const void *p, size_t bytes) {
+      buf.assign((const unsigned char *)p, (const unsigned char *)p + bytes);
+    };
+    const std::string nm(name);
+    const geneo::Topology &t = c->topo;
+    if (nm == "edges") put(t.edges.data(), t.edges.size() * 4);
+    else if (nm == "dir_edge") put(t.dir_edge.data(), t.dir_edge.size());
+    else if (nm == "dof_edge") put(t.dof_edge.data(), t.dof_edge.size() * 4);
+    else if (nm == "dof_vert") put(t.dof_vert.data(), t.dof_vert.size() * 4);
+    else if (nm == "A_rowptr") put(t.rowptr.data(), t.rowptr.size() * 4);
+    else if (nm == "A_col") put(t.col.data(), t.col.size() * 4);
+    else if (nm == "A_val") {
+      auto v = c->d_val.download(c->stream);
+      put(v.data(), v.size() * 8);
+    } else if (nm == "N_off") put(c->dec.N_off.data(), c->dec.N_off.size() * 8);
+    else if (nm == "N_idx") put(c->dec.N_idx.data(), c->dec.N_idx.size() * 4);
+    else if (nm == "owner") put(c->dec.owner.data(), c->dec.owner.size() * 4);
+    else if (nm == "snk_sub") put(c->snk.sub.data(), c->snk.sub.size() * 4);
+    else if (nm == "snk_vert") put(c->snk.vert.data(), c->snk.vert.size() * 4);
+    else if (nm == "geneo_sub") put(c->geneo_sub.data(), c->geneo_sub.size() * 4);
+    else if (nm == "geneo_lambda") put(c->geneo_lambda.data(), c->geneo_lambda.size() * 8);
+    else if (nm == "geneo_found") put(c->geneo_found.data(), c->geneo_found.size() * 4);
+    else if (nm == "Zcol_ptr") put(c->zc_ptr.data(), c->zc_ptr.size() * 8);
+    else if (nm == "Zcol_row") put(c->zc_row.data(), c->zc_row.size() * 4);
+    else if (nm == "Zcol_val") put(c->zc_val.data(), c->zc_val.size() * 8);
+    else if (nm == "k0k1") {
+      int32_t k[2] = {c->dec.k0, c->dec.k1};
+      put(k, 8);
+    } else
+      return fail(GENEO_ERR_INVALID_ARG, "unknown export name: " + nm);
+    if (size) *size = (int64_t)buf.size();
+    if (dst) {
+      if (cap < (int64_t)buf.size()) return fail(GENEO_ERR_INVALID_ARG, "buffer too small");
+      if (!buf.empty()) std::memcpy(dst, buf.data(), buf.size());
+    }
+    return GENEO_OK;
+  });
+}
+
+const char *geneo_last_error(void) { return g_last_error.c_str(); }
+
+const char *geneo_strerror(int s) {
+  switch (s) {
+    case GENEO_OK: return "ok";
+    case GENEO_NOT_CONVERGED: return "not converged";
+    case GENEO_ERR_INVALID_ARG: return "invalid argument";
+    case GENEO_ERR_CUDA: return "CUDA error";
+    case GENEO_ERR_OOM: return "out of memory";
+    case GENEO_ERR_NOT_SPD: return "matrix not positive definite";
+    case GENEO_ERR_BREAKDOWN: return "Krylov breakdown";
+    case GENEO_ERR_TIMEOUT: return "device wait timed out";
+    case GENEO_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

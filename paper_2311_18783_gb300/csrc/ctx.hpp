@@ -1,0 +1,63 @@
+// The library context: host topology plus every device array of one problem.
+#pragma once
+#include "common.cuh"
+#include "dense.cuh"
+#include "topology.hpp"
+
+struct geneo_ctx {
+  // problem copy
+  int nx = 0, ny = 0, nz = 0;
+  double h[3] = {0, 0, 0};
+  double gamma = 0, tau = 0, tau_p = 0;
+  int px = 0, py = 0, pz = 0, overlap = 0;
+  std::vector<uint8_t> active;
+  std::vector<double> mu_inv, eps;
+  geneo_options opt{};
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;  // internal set-up stream
+  double setup_seconds = 0;
+
+  geneo::Topology topo;
+  geneo::Decomposition dec;
+  geneo::LocalStructure ls;
+  geneo::SNKColumns snk;
+
+  // mesh and global matrix
+  geneo::DevBuf<int32_t> d_tets, d_tet_cell, d_tet_edges, d_edge_tail, d_edge_dir;
+  geneo::DevBuf<double> d_mu, d_eps;
+  geneo::DevBuf<double> d_Ae;                 // [ntets][36] element A_T
+  geneo::DevBuf<int32_t> d_rowptr, d_col;
+  geneo::DevBuf<double> d_val;
+  geneo::DevBuf<int64_t> d_cptr, d_rptr;
+  geneo::DevBuf<int32_t> d_cidx, d_ridx;
+
+  // local factors (tile-packed inverses of A_i)
+  geneo::TileBatch loc;
+  geneo::DevBuf<double> loc_f64;
+  geneo::DevBuf<float> loc_f32;
+  geneo::DevBuf<int32_t> d_l2g;               // [loc.vlen] unknown or -1
+  geneo::DevBuf<int64_t> d_g2l_ptr, d_g2l;    // prolongation lists (padded slots)
+
+  // coarse space: Z in CSC and CSR, dense E^-1 (tile-packed single matrix)
+  int64_t n0 = 0, n0_snk = 0, n0_geneo = 0;
+  std::vector<int32_t> geneo_sub, geneo_found;
+  std::vector<double> geneo_lambda;
+  std::vector<int64_t> zc_ptr;
+  std::vector<int32_t> zc_row;
+  std::vector<double> zc_val;
+  geneo::DevBuf<int64_t> d_zc_ptr, d_zr_ptr;
+  geneo::DevBuf<int32_t> d_zc_row, d_zr_col;
+  geneo::DevBuf<double> d_zc_val, d_zr_val;
+  geneo::TileBatch crs;
+  geneo::DevBuf<double> crs_f64;
+
+  // work vectors
+  geneo::DevBuf<double> v_y0, v_s, v_w, v_t, v_c, loc_x, loc_y, crs_x, crs_y;
+  geneo::DevBuf<double> p_r, p_z, p_p, p_q, scal, partials;
+  geneo::DevBuf<double> h_b, h_x;  // device copies used by geneo_solve_host
+  geneo::DevBuf<int> d_err;
+  double *h_scal = nullptr;  // pinned host mirror of the PCG scalars
+
+  ~geneo_ctx();
+};

@@ -1,0 +1,648 @@
+// Batched tile-packed symmetric matrices: explicit inversion by a symmetric
+// Gauss-Jordan sweep (float64) and a streaming SYMV whose 64x64 tiles are
+// staged in shared memory by cp.async.bulk copies completed on mbarriers.
+//
+// The local solves A_i^-1 of Sec. 2, eq. "AS", are applied as explicit
+// inverses: every tile is read once per application and the work of all
+// subdomains is spread over all SMs.
+#include "dense.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <queue>
+
+namespace geneo {
+
+int device_sm_count() {
+  int dev = 0, n = 0;
+  GENEO_CUDA(cudaGetDevice(&dev));
+  GENEO_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  return n;
+}
+
+void TileBatch::layout(const std::vector<int64_t> &dims) {
+  nmat = (int)dims.size();
+  dim = dims;
+  nt.resize(nmat);
+  toff.resize(nmat + 1);
+  voff.resize(nmat + 1);
+  toff[0] = voff[0] = 0;
+  maxnt = 0;
+  for (int m = 0; m < nmat; ++m) {
+    nt[m] = (int32_t)((dims[m] + kTile - 1) / kTile);
+    maxnt = std::max(maxnt, nt[m]);
+    toff[m + 1] = toff[m] + (int64_t)nt[m] * (nt[m] + 1) / 2;
+    voff[m + 1] = voff[m] + (int64_t)nt[m] * kTile;
+  }
+  ntiles = toff[nmat];
+  vlen = voff[nmat];
+}
+
+void TileBatch::upload_meta(cudaStream_t s) {
+  d_nt.upload(nt, s);
+  d_toff.upload(toff, s);
+  d_voff.upload(voff, s);
+  std::vector<int32_t> vm, vi;
+  for (int m = 0; m < nmat; ++m)
+    for (int I = 0; I < nt[m]; ++I) {
+      vm.push_back(m);
+      vi.push_back(I);
+    }
+  d_vrow_m.upload(vm, s);
+  d_vrow_I.upload(vi, s);
+  rowpart.alloc(vlen);
+  colpart.alloc(ntiles * (int64_t)kTile);
+}
+
+// Longest-processing-time assignment of tile rows (strips) to persistent CTAs.
+void TileBatch::schedule(int nctas, cudaStream_t s) {
+  struct Strip { int32_t m, I; };
+  std::vector<Strip> strips;
+  for (int m = 0; m < nmat; ++m)
+    for (int I = 0; I < nt[m]; ++I) strips.push_back({m, I});
+  std::stable_sort(strips.begin(), strips.end(),
+                   [](const Strip &a, const Strip &b) { return a.I > b.I; });
+  nctas = std::max(1, std::min<int>(nctas, (int)strips.size()));
+  using Load = std::pair<int64_t, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+  for (int c = 0; c < nctas; ++c) pq.push({0, c});
+  std::vector<std::vector<Strip>> per(nctas);
+  for (const Strip &st : strips) {
+    Load l = pq.top();
+    pq.pop();
+    per[l.second].push_back(st);
+    pq.push({l.first + st.I + 1, l.second});
+  }
+  std::vector<int32_t> sm, si, off(1, 0);
+  for (int c = 0; c < nctas; ++c) {
+    for (const Strip &st : per[c]) {
+      sm.push_back(st.m);
+      si.push_back(st.I);
+    }
+    off.push_back((int32_t)sm.size());
+  }
+  sched_ctas = nctas;
+  d_strip_m.upload(sm, s);
+  d_strip_I.upload(si, s);
+  d_cta_off.upload(off, s);
+}
+
+// ---------------------------------------------------------------------------
+// tile helpers
+
+__device__ __forceinline__ void tile_I_J(int64_t q, int &I, int &J) {
+  int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
+  while ((int64_t)i * (i + 1) / 2 > q) --i;
+  I = i;
+  J = (int)(q - (int64_t)i * (i + 1) / 2);
+}
+
+__device__ __forceinline__ int64_t tidx(int64_t toff, int I, int J) {
+  return toff + (int64_t)I * (I + 1) / 2 + J;
+}
+
+constexpr int kLd = kTile + 1;  // padded shared-memory leading dimension
+
+// dst[r][c] = src[r][c] (transpose = false) or src[c][r] (transpose = true)
+__device__ __forceinline__ void load_tile_smem(double *dst, const double *__restrict__ src,
+                                               bool transpose) {
+  for (int q = threadIdx.x; q < kTileElems; q += blockDim.x) {
+    const int r = q >> 6, c = q & 63;
+    const double v = src[q];
+    if (transpose) dst[c * kLd + r] = v;
+    else dst[r * kLd + c] = v;
+  }
+}
+
+// acc[i][j] += sum_t As[ri][t] * Bs[cj][t], rows ri = 4*tr + i, cols cj = tc + 16 j
+__device__ __forceinline__ void gemm_abt(const double *As, const double *Bs, double acc[4][4]) {
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll 4
+  for (int t = 0; t < kTile; ++t) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[(4 * tr + i) * kLd + t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Bs[(tc + 16 * j) * kLd + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Explicit SPD inverse by tiled Cholesky.  A = L L^T (POTRF on the diagonal
+// tile, TRSM of the column panel with the inverted diagonal tile, SYRK/GEMM
+// update of the trailing tiles); Y = L^-1 by tiled forward substitution on
+// the identity; A^-1 = Y^T Y.  (A symmetric Gauss-Jordan sweep is not used:
+// on matrices with the large gradient near-kernel of A_i = K_i + gamma M_i it
+// loses several digits, while the Cholesky route keeps the forward error at
+// kappa(A_i) u.)
+
+// Unblocked Cholesky of the diagonal tile in shared memory, then the inverse
+// of L_kk by 64 independent forward substitutions.  Writes L_kk (upper part
+// zeroed) to the storage and L_kk^-1 to dinv.
+__global__ void __launch_bounds__(256) k_potrf(double *data, const int32_t *nt,
+                                               const int64_t *toff, const int64_t *dtoff,
+                                               const int32_t *npiv, int k, double *dinv, int *err) {
+  extern __shared__ double sh[];
+  const int m = blockIdx.x;
+  const int lim = npiv ? npiv[m] : nt[m];
+  if (k >= lim) return;
+  double *a = sh, *x = sh + kTile * kLd;
+  double *tile = data + tidx(toff[m], k, k) * kTileElems;
+  load_tile_smem(a, tile, false);
+  __syncthreads();
+  for (int p = 0; p < kTile; ++p) {
+    double d = a[p * kLd + p];
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) atomicCAS(err, kDevOk, kDevNotSPD);
+      d = 1.0;
+    }
+    d = sqrt(d);
+    __syncthreads();
+    if (threadIdx.x < kTile) {
+      const int r = threadIdx.x;
+      if (r > p) a[r * kLd + p] /= d;
+      else if (r == p) a[p * kLd + p] = d;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kTileElems; q += blockDim.x) {
+      const int r = q >> 6, c = q & 63;
+      if (c > p && r >= c) a[r * kLd + c] -= a[r * kLd + p] * a[c * kLd + p];
+    }
+    __syncthreads();
+  }
+  // X = L^-1: thread c solves L x = e_c (x[r] = 0 for r < c)
+  if (threadIdx.x < kTile) {
+    const int c = threadIdx.x;
+    for (int r = 0; r < kTile; ++r) {
+      double v = (r == c) ? 1.0 : 0.0;
+      if (r >= c) {
+        for (int t = c; t < r; ++t) v -= a[r * kLd + t] * x[t * kLd + c];
+        v /= a[r * kLd + r];
+      } else {
+        v = 0.0;
+      }
+      x[r * kLd + c] = v;
+    }
+  }
+  __syncthreads();
+  double *Li = dinv + (dtoff[m] + k) * kTileElems;
+  for (int q = threadIdx.x; q < kTileElems; q += blockDim.x) {
+    const int r = q >> 6, c = q & 63;
+    tile[q] = (c <= r) ? a[r * kLd + c] : 0.0;
+    Li[q] = x[r * kLd + c];
+  }
+}
+
+// L_Ik = A_Ik L_kk^-T for I > k
+__global__ void __launch_bounds__(256) k_trsm(double *data, const int32_t *nt, const int64_t *toff,
+                                              const int64_t *dtoff, const int32_t *npiv, int k,
+                                              const double *dinv) {
+  extern __shared__ double sh[];
+  const int I = k + 1 + blockIdx.x, m = blockIdx.y;
+  const int lim = npiv ? npiv[m] : nt[m];
+  if (k >= lim || I >= nt[m]) return;
+  double *As = sh, *Bs = sh + kTile * kLd;
+  double *dst = data + tidx(toff[m], I, k) * kTileElems;
+  load_tile_smem(As, dst, false);
+  load_tile_smem(Bs, dinv + (dtoff[m] + k) * kTileElems, false);
+  __syncthreads();
+  double acc[4][4] = {};
+  gemm_abt(As, Bs, acc);
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[(4 * tr + i) * kTile + tc + 16 * j] = acc[i][j];
+}
+
+// A_IJ -= L_Ik L_Jk^T for k < J <= I (tiles enumerated from (k+1, k+1))
+__global__ void __launch_bounds__(256) k_syrk(double *data, const int32_t *nt, const int64_t *toff,
+                                              const int32_t *npiv, int k) {
+  extern __shared__ double sh[];
+  const int m = blockIdx.y;
+  const int lim = npiv ? npiv[m] : nt[m];
+  if (k >= lim) return;
+  const int64_t rest = nt[m] - k - 1;
+  const int64_t q = blockIdx.x;
+  if (q >= rest * (rest + 1) / 2) return;
+  int I, J;
+  tile_I_J(q, I, J);
+  I += k + 1;
+  J += k + 1;
+  double *As = sh, *Bs = sh + kTile * kLd;
+  load_tile_smem(As, data + tidx(toff[m], I, k) * kTileElems, false);
+  load_tile_smem(Bs, data + tidx(toff[m], J, k) * kTileElems, false);
+  __syncthreads();
+  double acc[4][4] = {};
+  gemm_abt(As, Bs, acc);
+  double *dst = data + tidx(toff[m], I, J) * kTileElems;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[(4 * tr + i) * kTile + tc + 16 * j] -= acc[i][j];
+}
+
+// forward substitution on the identity, step k:
+//   Y_kj = L_kk^-1 B_kj  (j <= k), with B = I - (updates so far)
+__global__ void __launch_bounds__(256) k_fwd_diag(double *Y, const int32_t *nt, const int64_t *toff,
+                                                  const int64_t *dtoff, int k, const double *dinv) {
+  extern __shared__ double sh[];
+  const int j = blockIdx.x, m = blockIdx.y;
+  if (k >= nt[m] || j > k) return;
+  double *As = sh, *Bs = sh + kTile * kLd;
+  double *dst = Y + tidx(toff[m], k, j) * kTileElems;
+  load_tile_smem(As, dinv + (dtoff[m] + k) * kTileElems, false);
+  load_tile_smem(Bs, dst, true);
+  __syncthreads();
+  double acc[4][4] = {};
+  gemm_abt(As, Bs, acc);
+  __syncthreads();
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) dst[(4 * tr + i) * kTile + tc + 16 * jj] = acc[i][jj];
+}
+
+//   B_Ij -= L_Ik Y_kj  (I > k, j <= k)
+__global__ void __launch_bounds__(256) k_fwd_update(double *Y, const double *L, const int32_t *nt,
+                                                    const int64_t *toff, int k) {
+  extern __shared__ double sh[];
+  const int m = blockIdx.z;
+  const int I = k + 1 + blockIdx.x, j = blockIdx.y;
+  if (I >= nt[m] || j > k) return;
+  double *As = sh, *Bs = sh + kTile * kLd;
+  load_tile_smem(As, L + tidx(toff[m], I, k) * kTileElems, false);
+  load_tile_smem(Bs, Y + tidx(toff[m], k, j) * kTileElems, true);
+  __syncthreads();
+  double acc[4][4] = {};
+  gemm_abt(As, Bs, acc);
+  double *dst = Y + tidx(toff[m], I, j) * kTileElems;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) dst[(4 * tr + i) * kTile + tc + 16 * jj] -= acc[i][jj];
+}
+
+// X_IJ = sum_{K >= I} Y_KI^T Y_KJ (J <= I), written over the factor storage
+__global__ void __launch_bounds__(256) k_lauum(double *X, const double *Y, const int32_t *nt,
+                                               const int64_t *toff) {
+  extern __shared__ double sh[];
+  const int m = blockIdx.y;
+  const int64_t ntm = nt[m];
+  const int64_t q = blockIdx.x;
+  if (q >= ntm * (ntm + 1) / 2) return;
+  int I, J;
+  tile_I_J(q, I, J);
+  double *As = sh, *Bs = sh + kTile * kLd;
+  double acc[4][4] = {};
+  for (int K = I; K < ntm; ++K) {
+    load_tile_smem(As, Y + tidx(toff[m], K, I) * kTileElems, true);
+    load_tile_smem(Bs, Y + tidx(toff[m], K, J) * kTileElems, true);
+    __syncthreads();
+    gemm_abt(As, Bs, acc);
+    __syncthreads();
+  }
+  double *dst = X + tidx(toff[m], I, J) * kTileElems;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[(4 * tr + i) * kTile + tc + 16 * j] = acc[i][j];
+}
+
+// symmetrise the diagonal tiles (X_II is computed in full)
+__global__ void k_symmetrize_diag(double *X, const int32_t *nt, const int64_t *toff) {
+  const int m = blockIdx.y, I = blockIdx.x;
+  if (I >= nt[m]) return;
+  double *t = X + tidx(toff[m], I, I) * kTileElems;
+  for (int e = threadIdx.x; e < kTileElems; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    if (r < c) {
+      const double v = 0.5 * (t[r * kTile + c] + t[c * kTile + r]);
+      t[r * kTile + c] = v;
+      t[c * kTile + r] = v;
+    }
+  }
+}
+
+// B = identity in tile-packed storage
+__global__ void k_identity(double *Y, const int32_t *nt, const int64_t *toff) {
+  const int m = blockIdx.y, I = blockIdx.x;
+  if (I >= nt[m]) return;
+  double *t = Y + tidx(toff[m], I, I) * kTileElems;
+  for (int r = threadIdx.x; r < kTile; r += blockDim.x) t[r * kTile + r] = 1.0;
+}
+
+__global__ void k_tiles_padding(double *data, const int32_t *nt, const int64_t *toff,
+                                const int64_t *dim) {
+  const int m = blockIdx.y;
+  const int ntm = nt[m];
+  const int64_t d = dim[m];
+  for (int64_t r = d + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < (int64_t)ntm * kTile;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(r / kTile), rr = (int)(r % kTile);
+    data[tidx(toff[m], I, I) * kTileElems + rr * kTile + rr] = 1.0;
+  }
+}
+
+__global__ void k_cast_f32(const double *src, float *dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+int64_t spd_workspace_elems(const TileBatch &b) {
+  int64_t diag = 0;
+  for (int m = 0; m < b.nmat; ++m) diag += b.nt[m];
+  return (b.ntiles + diag) * kTileElems;
+}
+
+static void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  const int two = 2 * kTile * kLd * (int)sizeof(double);
+  GENEO_CUDA(cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  GENEO_CUDA(cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  GENEO_CUDA(cudaFuncSetAttribute(k_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  GENEO_CUDA(cudaFuncSetAttribute(k_fwd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  GENEO_CUDA(cudaFuncSetAttribute(k_fwd_update, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  GENEO_CUDA(cudaFuncSetAttribute(k_lauum, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
+  done = true;
+}
+
+void chol_factor(TileBatch &b, double *data, const int32_t *d_npiv, int nsteps, double *dinv,
+                 const int64_t *d_dtoff, int *d_err, cudaStream_t s) {
+  set_smem_attrs();
+  const int two = 2 * kTile * kLd * (int)sizeof(double);
+  for (int k = 0; k < nsteps; ++k) {
+    k_potrf<<<b.nmat, 256, two, s>>>(data, b.d_nt.p, b.d_toff.p, d_dtoff, d_npiv, k, dinv, d_err);
+    const int rest = b.maxnt - k - 1;
+    if (rest > 0) {
+      k_trsm<<<dim3(rest, b.nmat), 256, two, s>>>(data, b.d_nt.p, b.d_toff.p, d_dtoff, d_npiv, k,
+                                                 dinv);
+      const int64_t nq = (int64_t)rest * (rest + 1) / 2;
+      k_syrk<<<dim3((unsigned)nq, b.nmat), 256, two, s>>>(data, b.d_nt.p, b.d_toff.p, d_npiv, k);
+    }
+  }
+  GENEO_CHECK_LAUNCH();
+}
+
+void spd_invert(TileBatch &b, double *data, double *ws, int *d_err, cudaStream_t s) {
+  set_smem_attrs();
+  const int two = 2 * kTile * kLd * (int)sizeof(double);
+  double *Y = ws;
+  double *dinv = ws + b.ntiles * kTileElems;
+  std::vector<int64_t> dtoff(b.nmat + 1, 0);
+  for (int m = 0; m < b.nmat; ++m) dtoff[m + 1] = dtoff[m] + b.nt[m];
+  DevBuf<int64_t> d_dtoff;
+  d_dtoff.upload(dtoff, s);
+  chol_factor(b, data, nullptr, b.maxnt, dinv, d_dtoff.p, d_err, s);
+  GENEO_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)tile_elems(b), s));
+  k_identity<<<dim3(b.maxnt, b.nmat), 64, 0, s>>>(Y, b.d_nt.p, b.d_toff.p);
+  for (int k = 0; k < b.maxnt; ++k) {
+    k_fwd_diag<<<dim3(k + 1, b.nmat), 256, two, s>>>(Y, b.d_nt.p, b.d_toff.p, d_dtoff.p, k, dinv);
+    const int rest = b.maxnt - k - 1;
+    if (rest > 0)
+      k_fwd_update<<<dim3(rest, k + 1, b.nmat), 256, two, s>>>(Y, data, b.d_nt.p, b.d_toff.p, k);
+  }
+  const int64_t maxT = (int64_t)b.maxnt * (b.maxnt + 1) / 2;
+  k_lauum<<<dim3((unsigned)maxT, b.nmat), 256, two, s>>>(data, Y, b.d_nt.p, b.d_toff.p);
+  k_symmetrize_diag<<<dim3(b.maxnt, b.nmat), 256, 0, s>>>(data, b.d_nt.p, b.d_toff.p);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+void tiles_init_padding(TileBatch &b, double *data, cudaStream_t s) {
+  GENEO_CUDA(cudaMemsetAsync(data, 0, sizeof(double) * (size_t)tile_elems(b), s));
+  DevBuf<int64_t> dd;
+  dd.upload(b.dim, s);
+  k_tiles_padding<<<dim3(1, b.nmat), 64, 0, s>>>(data, b.d_nt.p, b.d_toff.p, dd.p);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+void tiles_cast_f32(const TileBatch &b, const double *src, float *dst, cudaStream_t s) {
+  const int64_t n = tile_elems(b);
+  const unsigned g = std::min<int64_t>(grid_for(n, 256), 65535LL * 16);
+  k_cast_f32<<<g, 256, 0, s>>>(src, dst, n);
+  GENEO_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// Streaming SYMV.  Persistent CTAs walk their strips (tile rows) tile by tile;
+// an elected thread keeps NST bulk copies in flight.  Each thread owns 8 rows
+// x 2 columns of a tile: row partials accumulate over the strip, column
+// partials (the mirrored upper triangle) are reduced across warps per tile.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, "
+      "0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// bounded wait: about a second of polling at most
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) return false;
+  }
+  return true;
+}
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+template <typename T, int NST>
+__global__ void __launch_bounds__(256, 1)
+    k_symv_strips(const T *__restrict__ data, const int64_t *__restrict__ toff,
+                  const int64_t *__restrict__ voff, const int32_t *__restrict__ strip_m,
+                  const int32_t *__restrict__ strip_I, const int32_t *__restrict__ cta_off,
+                  const double *__restrict__ x, double *__restrict__ rowpart,
+                  double *__restrict__ colpart, int *err) {
+  using A = typename Acc<T>::type;
+  using V2 = typename Vec2<T>::type;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T *stage = reinterpret_cast<T *>(smraw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + (size_t)NST * kTileElems * sizeof(T));
+  A *red = reinterpret_cast<A *>(bar + NST);  // [8][64]
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
+  if (s0 >= s1) return;
+  if (tid == 0) {
+    for (int i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // producer state (thread 0)
+  int ps = s0, pJ = 0;
+  long long issued = 0, consumed = 0;
+  auto issue = [&]() {
+    if (ps >= s1) return;
+    const int m = strip_m[ps], I = strip_I[ps];
+    const T *src = data + (toff[m] + (int64_t)I * (I + 1) / 2 + pJ) * kTileElems;
+    const int st = (int)(issued % NST);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], kTileElems * sizeof(T));
+    bulk_g2s(stage + (size_t)st * kTileElems, src, kTileElems * sizeof(T), &bar[st]);
+    ++issued;
+    if (++pJ > I) {
+      pJ = 0;
+      ++ps;
+    }
+  };
+  if (tid == 0)
+    for (int q = 0; q < NST; ++q) issue();
+  bool failed = false;
+  for (int s = s0; s < s1 && !failed; ++s) {
+    const int m = strip_m[s], I = strip_I[s];
+    const int64_t vb = voff[m];
+    const int64_t tb = toff[m] + (int64_t)I * (I + 1) / 2;
+    A xi[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xi[r] = (A)x[vb + (int64_t)I * kTile + w * 8 + r];
+    A rp[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) rp[r] = (A)0;
+    for (int J = 0; J <= I; ++J) {
+      const int st = (int)(consumed % NST);
+      const uint32_t par = (uint32_t)((consumed / NST) & 1);
+      const bool ok = mbar_wait_bounded(&bar[st], par);
+      // uniform decision: also orders the previous tile's red[] reads before
+      // this tile's writes
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicCAS(err, kDevOk, kDevTimeout);
+        failed = true;
+        break;
+      }
+      const T *t = stage + (size_t)st * kTileElems;
+      const A xj0 = (A)x[vb + (int64_t)J * kTile + 2 * l];
+      const A xj1 = (A)x[vb + (int64_t)J * kTile + 2 * l + 1];
+      A c0 = 0, c1 = 0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const V2 a = *reinterpret_cast<const V2 *>(t + (w * 8 + r) * kTile + 2 * l);
+        rp[r] = fma((A)a.x, xj0, fma((A)a.y, xj1, rp[r]));
+        c0 = fma((A)a.x, xi[r], c0);
+        c1 = fma((A)a.y, xi[r], c1);
+      }
+      if (J < I) {
+        red[w * kTile + 2 * l] = c0;
+        red[w * kTile + 2 * l + 1] = c1;
+      }
+      __syncthreads();
+      if (J < I && tid < kTile) {
+        A sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sum += red[q * kTile + tid];
+        colpart[(tb + J) * kTile + tid] = (double)sum;
+      }
+      ++consumed;
+      if (tid == 0) issue();
+    }
+    if (failed) break;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      A v = rp[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) rowpart[vb + (int64_t)I * kTile + w * 8 + r] = (double)v;
+    }
+  }
+  if (failed && tid == 0) {
+    // drain copies still in flight before leaving (bounded)
+    while (consumed < issued) {
+      const int st = (int)(consumed % NST);
+      mbar_wait_bounded(&bar[st], (uint32_t)((consumed / NST) & 1));
+      ++consumed;
+    }
+  }
+}
+
+// y[(m, I)] = rowpart[(m, I)] + sum_{K > I} colpart[(m, K, I)]
+__global__ void k_symv_reduce(const int32_t *__restrict__ vrow_m,
+                              const int32_t *__restrict__ vrow_I, const int32_t *__restrict__ nt,
+                              const int64_t *__restrict__ toff, const int64_t *__restrict__ voff,
+                              const double *__restrict__ rowpart,
+                              const double *__restrict__ colpart, double *__restrict__ y,
+                              int64_t nblocks) {
+  const int64_t blk = blockIdx.x;
+  if (blk >= nblocks) return;
+  const int m = vrow_m[blk], I = vrow_I[blk];
+  const int r = threadIdx.x;
+  const int64_t pos = voff[m] + (int64_t)I * kTile + r;
+  double v = rowpart[pos];
+  const int ntm = nt[m];
+  for (int K = I + 1; K < ntm; ++K)
+    v += colpart[(toff[m] + (int64_t)K * (K + 1) / 2 + I) * kTile + r];
+  y[pos] = v;
+}
+
+template <typename T> constexpr int symv_stages() { return sizeof(T) == 8 ? 4 : 8; }
+
+template <typename T>
+void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
+                cudaStream_t s) {
+  constexpr int NST = symv_stages<T>();
+  const size_t smem = (size_t)NST * kTileElems * sizeof(T) + NST * sizeof(uint64_t) +
+                      8 * kTile * sizeof(typename Acc<T>::type);
+  static bool attr = false;
+  if (!attr) {
+    GENEO_CUDA(cudaFuncSetAttribute(k_symv_strips<T, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  k_symv_strips<T, NST><<<b.sched_ctas, 256, smem, s>>>(
+      data, b.d_toff.p, b.d_voff.p, b.d_strip_m.p, b.d_strip_I.p, b.d_cta_off.p, x, b.rowpart.p,
+      b.colpart.p, d_err);
+  const int64_t nblocks = b.vlen / kTile;
+  k_symv_reduce<<<(unsigned)nblocks, kTile, 0, s>>>(b.d_vrow_m.p, b.d_vrow_I.p, b.d_nt.p,
+                                                    b.d_toff.p, b.d_voff.p, b.rowpart.p,
+                                                    b.colpart.p, y, nblocks);
+  GENEO_CHECK_LAUNCH();
+}
+
+template void symv_batch<double>(TileBatch &, const double *, const double *, double *, int *,
+                                 cudaStream_t);
+template void symv_batch<float>(TileBatch &, const float *, const double *, double *, int *,
+                                cudaStream_t);
+
+}  // namespace geneo

@@ -1,0 +1,63 @@
+// Batched dense symmetric matrices in tile-packed storage, their explicit
+// inversion by a symmetric Gauss-Jordan sweep, and the streaming SYMV that
+// applies them.
+//
+// Storage: matrix m of dimension dim[m] is padded to nt[m] = ceil(dim/64)
+// tiles per side; only tiles (I, J) with J <= I are stored, each a full 64x64
+// row-major block, at tile index toff[m] + I(I+1)/2 + J.  Diagonal tiles hold
+// both triangles.  Padding rows/columns carry an identity diagonal, so the
+// sweep leaves them decoupled.  Vectors use the padded layout: matrix m owns
+// elements [voff[m], voff[m] + 64 nt[m]).
+#pragma once
+#include "common.cuh"
+
+namespace geneo {
+
+struct TileBatch {
+  int nmat = 0;
+  int maxnt = 0;
+  std::vector<int32_t> nt;
+  std::vector<int64_t> dim, toff, voff;
+  int64_t ntiles = 0, vlen = 0;
+  DevBuf<int32_t> d_nt;
+  DevBuf<int64_t> d_toff, d_voff;
+  DevBuf<int32_t> d_vrow_m, d_vrow_I;  // per 64-block of the padded vector
+  // SYMV schedule (strips = tile rows, grouped per CTA)
+  int sched_ctas = 0;
+  DevBuf<int32_t> d_strip_m, d_strip_I, d_cta_off;
+  DevBuf<double> rowpart, colpart;   // partial sums of the streaming SYMV
+
+  void layout(const std::vector<int64_t> &dims);
+  void upload_meta(cudaStream_t s);
+  void schedule(int nctas, cudaStream_t s);
+};
+
+// -- Explicit inverse of every matrix of the batch, in place (float64), by
+// tiled Cholesky, forward substitution on the identity and A^-1 = Y^T Y.
+// Pivots that are not positive set err (kDevNotSPD).  ws must hold
+// spd_workspace_elems(b) doubles.  Synchronises the stream.
+int64_t spd_workspace_elems(const TileBatch &b);
+void spd_invert(TileBatch &b, double *data, double *ws, int *d_err, cudaStream_t s);
+// Tiled Cholesky of the first nsteps pivot tiles (all when d_npiv is null,
+// else npiv[m] per matrix; the trailing tiles then hold the Schur
+// complement).  dinv receives L_kk^-1 for every factored diagonal tile at
+// tile index dtoff[m] + k.
+void chol_factor(TileBatch &b, double *data, const int32_t *d_npiv, int nsteps, double *dinv,
+                 const int64_t *d_dtoff, int *d_err, cudaStream_t s);
+
+// -- y = blockdiag(A_m) x on padded vectors.  Templated on the storage type.
+template <typename T>
+void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
+                cudaStream_t s);
+
+// Pointer/size of a tile-packed buffer in elements.
+inline int64_t tile_elems(const TileBatch &b) { return b.ntiles * (int64_t)kTileElems; }
+
+// Fill storage with zeros and an identity diagonal on padding rows.
+void tiles_init_padding(TileBatch &b, double *data, cudaStream_t s);
+// Cast float64 tile storage to float32.
+void tiles_cast_f32(const TileBatch &b, const double *src, float *dst, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace geneo

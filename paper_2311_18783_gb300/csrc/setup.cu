@@ -1,0 +1,547 @@
+// Numerical set-up on the GPU: Whitney element matrices, assembly of A, the
+// local Dirichlet matrices and their explicit inverses, the split
+// near-kernel coarse basis Z and the coarse matrix E = Z^T A Z with its
+// inverse.
+//
+// Element matrices: Sec. 2, eq. "bilinearformposmax" with lowest-order
+// Nedelec (Whitney) functions W_ab = l_a grad l_b - l_b grad l_a,
+// curl W_ab = 2 grad l_a x grad l_b, int l_i l_j = |T| (1 + d_ij) / 20.
+// A = K + gamma M: Sec. 1, eq. "discretemaxwell".  A_i = R_i A R_i^T:
+// Sec. 2, eq. "AS".  Z and E: Sec. 2 (definition "near-kernelCS",
+// E = Z^T A Z).
+#include <algorithm>
+#include <chrono>
+
+#include "ctx.hpp"
+#include "setup.hpp"
+
+namespace geneo {
+
+// ---------------------------------------------------------------------------
+// element matrices
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// barycentric gradients and volume of a tetrahedron of the structured mesh
+__device__ void tet_geometry(const int32_t *tv, int nx, int ny, double hx, double hy, double hz,
+                             double g[4][3], double &vol) {
+  double p[4][3];
+  for (int q = 0; q < 4; ++q) {
+    const int64_t v = tv[q];
+    const int64_t i = v % (nx + 1), j = (v / (nx + 1)) % (ny + 1),
+                  k = v / ((int64_t)(nx + 1) * (ny + 1));
+    p[q][0] = i * hx;
+    p[q][1] = j * hy;
+    p[q][2] = k * hz;
+  }
+  double r1[3], r2[3], r3[3];
+  for (int d = 0; d < 3; ++d) {
+    r1[d] = p[1][d] - p[0][d];
+    r2[d] = p[2][d] - p[0][d];
+    r3[d] = p[3][d] - p[0][d];
+  }
+  double c23[3], c31[3], c12[3];
+  cross3(r2, r3, c23);
+  cross3(r3, r1, c31);
+  cross3(r1, r2, c12);
+  const double det = r1[0] * c23[0] + r1[1] * c23[1] + r1[2] * c23[2];
+  for (int d = 0; d < 3; ++d) {
+    g[1][d] = c23[d] / det;
+    g[2][d] = c31[d] / det;
+    g[3][d] = c12[d] / det;
+    g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+  }
+  vol = fabs(det) / 6.0;
+}
+
+__constant__ int c_le[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+// curl-curl and mass element matrices (upper triangle computed, mirrored)
+__device__ void element_KM(const double g[4][3], double vol, double K[6][6], double M[6][6]) {
+  double curl[6][3];
+  for (int e = 0; e < 6; ++e) {
+    cross3(g[c_le[e][0]], g[c_le[e][1]], curl[e]);
+    for (int d = 0; d < 3; ++d) curl[e][d] *= 2.0;
+  }
+  double G[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) G[a][b] = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+  const double w = vol / 20.0;
+  for (int e = 0; e < 6; ++e)
+    for (int f = e; f < 6; ++f) {
+      const int a = c_le[e][0], b = c_le[e][1], c = c_le[f][0], d = c_le[f][1];
+      const double kk = vol * (curl[e][0] * curl[f][0] + curl[e][1] * curl[f][1] + curl[e][2] * curl[f][2]);
+      const double mm = w * ((1.0 + (a == c)) * G[b][d] - (1.0 + (a == d)) * G[b][c] -
+                             (1.0 + (b == c)) * G[a][d] + (1.0 + (b == d)) * G[a][c]);
+      K[e][f] = K[f][e] = kk;
+      M[e][f] = M[f][e] = mm;
+    }
+}
+
+__global__ void k_element(const int32_t *__restrict__ tets, const int32_t *__restrict__ tet_cell,
+                          const double *__restrict__ mu, const double *__restrict__ eps,
+                          double gamma, int nx, int ny, double hx, double hy, double hz,
+                          int64_t ntets, double *__restrict__ Ae) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntets) return;
+  double g[4][3], vol, K[6][6], M[6][6];
+  tet_geometry(tets + 4 * t, nx, ny, hx, hy, hz, g, vol);
+  element_KM(g, vol, K, M);
+  const int c = tet_cell[t];
+  const double mi = mu[c], ep = eps[c] * gamma;
+  for (int e = 0; e < 6; ++e)
+    for (int f = 0; f < 6; ++f) Ae[t * 36 + e * 6 + f] = mi * K[e][f] + ep * M[e][f];
+}
+
+// per tetrahedron: mc[t][a] = sum_b M1_T[a][b] c[edge_b] (eps = 1 mass)
+__global__ void k_rhs_element(const int32_t *__restrict__ tets, const int32_t *__restrict__ tet_edges,
+                              const double *__restrict__ cedge, int nx, int ny, double hx,
+                              double hy, double hz, int64_t ntets, double *__restrict__ mc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntets) return;
+  double g[4][3], vol, K[6][6], M[6][6];
+  tet_geometry(tets + 4 * t, nx, ny, hx, hy, hz, g, vol);
+  element_KM(g, vol, K, M);
+  double cv[6];
+  for (int b = 0; b < 6; ++b) cv[b] = cedge[tet_edges[6 * t + b]];
+  for (int a = 0; a < 6; ++a) {
+    double s = 0;
+    for (int b = 0; b < 6; ++b) s = fma(M[a][b], cv[b], s);
+    mc[6 * t + a] = s;
+  }
+}
+
+// c_e = f(slot of e) . (x_head - x_tail)
+__global__ void k_rhs_edge(const double *__restrict__ fslot, const int32_t *__restrict__ tail,
+                           const int32_t *__restrict__ dir, double hx, double hy, double hz,
+                           int64_t nedges, double *__restrict__ cedge) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nedges) return;
+  const int d = dir[e];
+  const int dx[7] = {1, 0, 0, 1, 1, 0, 1}, dy[7] = {0, 1, 0, 1, 0, 1, 1}, dz[7] = {0, 0, 1, 0, 1, 1, 1};
+  const double *f = fslot + ((int64_t)tail[e] * 7 + d) * 3;
+  cedge[e] = f[0] * (dx[d] * hx) + f[1] * (dy[d] * hy) + f[2] * (dz[d] * hz);
+}
+
+// b_e = sum over its (tet, local edge) slots, in tet order
+__global__ void k_gather_sum(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                             const double *__restrict__ src, int64_t n, double *__restrict__ out) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double s = 0;
+  for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) s += src[idx[k]];
+  out[r] = s;
+}
+
+// A_i -> tile-packed lower storage (diagonal tiles full)
+__global__ void k_extract_local(const int64_t *__restrict__ Noff, const int64_t *__restrict__ lrowptr,
+                                const int32_t *__restrict__ lcol, const int32_t *__restrict__ lpos,
+                                const double *__restrict__ val, const int64_t *__restrict__ toff,
+                                double *__restrict__ tiles) {
+  const int m = blockIdx.y;
+  const int64_t ni = Noff[m + 1] - Noff[m];
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ni;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = Noff[m] + r;
+    const int I = (int)(r / kTile), rr = (int)(r % kTile);
+    for (int64_t k = lrowptr[slot]; k < lrowptr[slot + 1]; ++k) {
+      const int c = lcol[k];
+      const int J = c / kTile;
+      if (J > I) continue;
+      tiles[(toff[m] + (int64_t)I * (I + 1) / 2 + J) * kTileElems + rr * kTile + (c % kTile)] = val[lpos[k]];
+    }
+  }
+}
+
+__device__ __forceinline__ double csr_lookup(const int32_t *rowptr, const int32_t *col,
+                                             const double *val, int32_t r, int32_t c) {
+  int lo = rowptr[r], hi = rowptr[r + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int32_t v = col[mid];
+    if (v == c) return val[mid];
+    if (v < c) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return 0.0;
+}
+
+// Column-tetrahedron incidence of the coarse basis.  For column a and a
+// tetrahedron T touching its support, entry q stores 15 doubles:
+//   [0..2]  sqrt(mu^-1_T |T|) * sum_e z_e curl W_e   (curl of the column on T)
+//   [3..8]  z_e on the six local edges (0 off the support)
+//   [9..14] gamma eps_T M_T z
+// so that E[a][b] = sum over common T of c_a . c_b + z_a . m_b, which equals
+// Z^T A Z while the K-part of gradient columns never cancels in assembled A.
+__global__ void k_coltet(const int32_t *__restrict__ ct_tet, int64_t nent,
+                         const int32_t *__restrict__ tets, const int32_t *__restrict__ tet_cell,
+                         const double *__restrict__ mu, const double *__restrict__ eps,
+                         double gamma, int nx, int ny, double hx, double hy, double hz,
+                         double *__restrict__ ct) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nent) return;
+  const int32_t t = ct_tet[q];
+  double g[4][3], vol, K[6][6], M[6][6];
+  tet_geometry(tets + 4 * (int64_t)t, nx, ny, hx, hy, hz, g, vol);
+  element_KM(g, vol, K, M);
+  double *e = ct + q * 15;
+  double z[6];
+  for (int k = 0; k < 6; ++k) z[k] = e[3 + k];
+  const int cell = tet_cell[t];
+  const double sc = sqrt(mu[cell] * vol), ge = gamma * eps[cell];
+  double c[3] = {0, 0, 0};
+  for (int k = 0; k < 6; ++k) {
+    if (z[k] == 0.0) continue;
+    double cw[3];
+    cross3(g[c_le[k][0]], g[c_le[k][1]], cw);
+    for (int d = 0; d < 3; ++d) c[d] = fma(2.0 * z[k], cw[d], c[d]);
+  }
+  for (int d = 0; d < 3; ++d) e[d] = sc * c[d];
+  for (int a = 0; a < 6; ++a) {
+    double v = 0;
+    for (int b = 0; b < 6; ++b) v = fma(M[a][b], z[b], v);
+    e[9 + a] = ge * v;
+  }
+}
+
+// E[a][b] for the lower pattern, written into the tile-packed coarse matrix
+// (both triangles of diagonal tiles).  Iterates over the shorter tet list and
+// binary-searches the longer one.
+__global__ void k_coarse_E(const int64_t *__restrict__ pptr, const int32_t *__restrict__ pcol,
+                           int64_t n0, const int64_t *__restrict__ ct_ptr,
+                           const int32_t *__restrict__ ct_tet, const double *__restrict__ ct,
+                           double *__restrict__ tiles) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
+  if (a >= n0) return;
+  for (int64_t q = pptr[a] + threadIdx.x; q < pptr[a + 1]; q += blockDim.x) {
+    const int64_t b = pcol[q];
+    int64_t sa = ct_ptr[a], ea = ct_ptr[a + 1], sb = ct_ptr[b], eb = ct_ptr[b + 1];
+    const bool swap = (ea - sa) > (eb - sb);
+    // iterate over list x, search in list y; the dot is symmetric in the
+    // roles only for the K part, so keep track of which side is a
+    const int64_t xs = swap ? sb : sa, xe = swap ? eb : ea, ys = swap ? sa : sb, ye = swap ? ea : eb;
+    double s = 0;
+    for (int64_t i = xs; i < xe; ++i) {
+      const int32_t t = ct_tet[i];
+      int64_t lo = ys, hi = ye - 1, hit = -1;
+      while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t v = ct_tet[mid];
+        if (v == t) { hit = mid; break; }
+        if (v < t) lo = mid + 1;
+        else hi = mid - 1;
+      }
+      if (hit < 0) continue;
+      const double *ea_ = ct + (swap ? hit : i) * 15;   // entry of column a
+      const double *eb_ = ct + (swap ? i : hit) * 15;   // entry of column b
+      double v = ea_[0] * eb_[0] + ea_[1] * eb_[1] + ea_[2] * eb_[2];
+      for (int k = 0; k < 6; ++k) v = fma(ea_[3 + k], eb_[9 + k], v);
+      s += v;
+    }
+    const int I = (int)(a / kTile), J = (int)(b / kTile);
+    const int64_t tb = ((int64_t)I * (I + 1) / 2 + J) * kTileElems;
+    tiles[tb + (a % kTile) * kTile + (b % kTile)] = s;
+    if (I == J) tiles[tb + (b % kTile) * kTile + (a % kTile)] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+void check_device_error(geneo_ctx *c, cudaStream_t s) {
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  int e = 0;
+  GENEO_CUDA(cudaMemcpy(&e, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == kDevNotSPD) throw Error(GENEO_ERR_NOT_SPD, "a factorisation pivot was not positive");
+  if (e == kDevTimeout) throw Error(GENEO_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (e != 0) throw Error(GENEO_ERR_CUDA, "device error word set");
+}
+
+static void build_z_csr(geneo_ctx *c) {
+  const int64_t n = c->topo.ndofs();
+  std::vector<int64_t> rp(n + 1, 0);
+  for (int32_t r : c->zc_row) rp[r + 1]++;
+  for (int64_t e = 0; e < n; ++e) rp[e + 1] += rp[e];
+  std::vector<int32_t> rc(c->zc_row.size());
+  std::vector<double> rv(c->zc_row.size());
+  std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+  for (int64_t a = 0; a < c->n0; ++a)
+    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
+      const int32_t r = c->zc_row[k];
+      rc[fill[r]] = (int32_t)a;
+      rv[fill[r]++] = c->zc_val[k];
+    }
+  c->d_zc_ptr.upload(c->zc_ptr, c->stream);
+  c->d_zc_row.upload(c->zc_row, c->stream);
+  c->d_zc_val.upload(c->zc_val, c->stream);
+  c->d_zr_ptr.upload(rp, c->stream);
+  c->d_zr_col.upload(rc, c->stream);
+  c->d_zr_val.upload(rv, c->stream);
+  GENEO_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// column-tetrahedron lists of Z (tets touching each column's support, sorted)
+// with the six local coefficients of the column on each tetrahedron
+static void coltet_lists(const geneo_ctx *c, std::vector<int64_t> &ct_ptr,
+                         std::vector<int32_t> &ct_tet, std::vector<double> &ct) {
+  const Topology &t = c->topo;
+  const int64_t n = t.ndofs(), nt = t.ntets();
+  std::vector<int64_t> tp(n + 1, 0);
+  for (int64_t q = 0; q < nt * 6; ++q) {
+    const int32_t d = t.edge_dof[t.tet_edges[q]];
+    if (d >= 0) tp[d + 1]++;
+  }
+  for (int64_t e = 0; e < n; ++e) tp[e + 1] += tp[e];
+  std::vector<int32_t> tl(tp[n]);
+  {
+    std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+    for (int64_t q = 0; q < nt * 6; ++q) {
+      const int32_t d = t.edge_dof[t.tet_edges[q]];
+      if (d >= 0) tl[fill[d]++] = (int32_t)(q / 6);
+    }
+  }
+  std::vector<double> val(n, 0.0);
+  std::vector<uint8_t> in(n, 0);
+  std::vector<int32_t> tets;
+  ct_ptr.assign(1, 0);
+  ct_tet.clear();
+  ct.clear();
+  for (int64_t a = 0; a < c->n0; ++a) {
+    tets.clear();
+    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
+      const int32_t e = c->zc_row[k];
+      val[e] = c->zc_val[k];
+      in[e] = 1;
+      tets.insert(tets.end(), tl.begin() + tp[e], tl.begin() + tp[e + 1]);
+    }
+    std::sort(tets.begin(), tets.end());
+    tets.erase(std::unique(tets.begin(), tets.end()), tets.end());
+    for (int32_t tt : tets) {
+      ct_tet.push_back(tt);
+      double ent[15] = {0};
+      for (int k = 0; k < 6; ++k) {
+        const int32_t d = t.edge_dof[t.tet_edges[(int64_t)tt * 6 + k]];
+        if (d >= 0 && in[d]) ent[3 + k] = val[d];
+      }
+      ct.insert(ct.end(), ent, ent + 15);
+    }
+    ct_ptr.push_back((int64_t)ct_tet.size());
+    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
+      val[c->zc_row[k]] = 0.0;
+      in[c->zc_row[k]] = 0;
+    }
+  }
+}
+
+// lower pattern of E = Z^T A Z: b <= a with supports of columns a, b coupled by A
+static void coarse_pattern(const geneo_ctx *c, std::vector<int64_t> &pptr,
+                           std::vector<int32_t> &pcol) {
+  const int64_t n = c->topo.ndofs();
+  const Topology &t = c->topo;
+  std::vector<int64_t> dp(n + 1, 0);
+  for (int32_t r : c->zc_row) dp[r + 1]++;
+  for (int64_t e = 0; e < n; ++e) dp[e + 1] += dp[e];
+  std::vector<int32_t> dc(c->zc_row.size());
+  {
+    std::vector<int64_t> fill(dp.begin(), dp.end() - 1);
+    for (int64_t a = 0; a < c->n0; ++a)
+      for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) dc[fill[c->zc_row[k]]++] = (int32_t)a;
+  }
+  std::vector<uint8_t> mark(c->n0, 0);
+  std::vector<int32_t> list;
+  pptr.assign(1, 0);
+  pcol.clear();
+  for (int64_t a = 0; a < c->n0; ++a) {
+    list.clear();
+    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
+      const int32_t e = c->zc_row[k];
+      for (int32_t q = t.rowptr[e]; q < t.rowptr[e + 1]; ++q) {
+        const int32_t f = t.col[q];
+        for (int64_t u = dp[f]; u < dp[f + 1]; ++u) {
+          const int32_t b = dc[u];
+          if (b <= a && !mark[b]) {
+            mark[b] = 1;
+            list.push_back(b);
+          }
+        }
+      }
+    }
+    std::sort(list.begin(), list.end());
+    for (int32_t b : list) mark[b] = 0;
+    pcol.insert(pcol.end(), list.begin(), list.end());
+    pptr.push_back((int64_t)pcol.size());
+  }
+}
+
+void setup_all(geneo_ctx *c) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c->stream;
+  Topology &t = c->topo;
+  build_topology(c->nx, c->ny, c->nz, c->h, c->active.data(), t);
+  if (t.ndofs() == 0) throw Error(GENEO_ERR_INVALID_ARG, "the mesh has no interior edge");
+  build_decomposition(t, c->px, c->py, c->pz, c->overlap, c->dec);
+  build_local_structure(t, c->dec, c->ls);
+  c->d_err.alloc(1);
+  c->d_err.zero(s);
+
+  // --- global matrix
+  const int64_t nt = t.ntets(), n = t.ndofs();
+  c->d_tets.upload(t.tets, s);
+  c->d_tet_cell.upload(t.tet_cell, s);
+  c->d_tet_edges.upload(t.tet_edges, s);
+  {
+    std::vector<int32_t> tail(t.nedges());
+    for (int64_t e = 0; e < t.nedges(); ++e) tail[e] = t.edges[2 * e];
+    c->d_edge_tail.upload(tail, s);
+    c->d_edge_dir.upload(t.edge_dir, s);
+  }
+  c->d_mu.upload(c->mu_inv, s);
+  c->d_eps.upload(c->eps, s);
+  c->d_Ae.alloc(nt * 36);
+  k_element<<<grid_for(nt, 128), 128, 0, s>>>(c->d_tets.p, c->d_tet_cell.p, c->d_mu.p, c->d_eps.p,
+                                              c->gamma, c->nx, c->ny, c->h[0], c->h[1], c->h[2],
+                                              nt, c->d_Ae.p);
+  GENEO_CHECK_LAUNCH();
+  c->d_rowptr.upload(t.rowptr, s);
+  c->d_col.upload(t.col, s);
+  c->d_cptr.upload(t.cptr, s);
+  c->d_cidx.upload(t.cidx, s);
+  c->d_rptr.upload(t.rptr, s);
+  c->d_ridx.upload(t.ridx, s);
+  c->d_val.alloc(t.nnz());
+  k_gather_sum<<<grid_for(t.nnz(), 256), 256, 0, s>>>(c->d_cptr.p, c->d_cidx.p, c->d_Ae.p,
+                                                      t.nnz(), c->d_val.p);
+  GENEO_CHECK_LAUNCH();
+
+  // --- local factors: A_i extracted into tile-packed storage and inverted
+  const Decomposition &d = c->dec;
+  std::vector<int64_t> dims(d.nsub);
+  for (int i = 0; i < d.nsub; ++i) dims[i] = d.ni(i);
+  c->loc.layout(dims);
+  c->loc.upload_meta(s);
+  c->loc_f64.alloc(tile_elems(c->loc));
+  tiles_init_padding(c->loc, c->loc_f64.p, s);
+  {
+    DevBuf<int64_t> noff, lrp, ncp;
+    DevBuf<int32_t> lcol, lpos;
+    noff.upload(d.N_off, s);
+    lrp.upload(c->ls.lrowptr, s);
+    lcol.upload(c->ls.lcol, s);
+    lpos.upload(c->ls.lpos, s);
+    k_extract_local<<<dim3(64, d.nsub), 256, 0, s>>>(noff.p, lrp.p, lcol.p, lpos.p, c->d_val.p,
+                                                     c->loc.d_toff.p, c->loc_f64.p);
+    GENEO_CHECK_LAUNCH();
+    DevBuf<double> ws;
+    ws.alloc(spd_workspace_elems(c->loc));
+    spd_invert(c->loc, c->loc_f64.p, ws.p, c->d_err.p, s);
+    check_device_error(c, s);
+  }
+  c->loc.schedule(c->sm_count, s);
+  {
+    std::vector<int32_t> l2g(c->loc.vlen, -1);
+    std::vector<int64_t> g2l(c->ls.g2l_slot.size());
+    std::vector<int64_t> slot_pad(d.N_off[d.nsub]);
+    for (int i = 0; i < d.nsub; ++i)
+      for (int64_t r = 0; r < d.ni(i); ++r) {
+        slot_pad[d.N_off[i] + r] = c->loc.voff[i] + r;
+        l2g[c->loc.voff[i] + r] = d.N_idx[d.N_off[i] + r];
+      }
+    for (size_t k = 0; k < g2l.size(); ++k) g2l[k] = slot_pad[c->ls.g2l_slot[k]];
+    c->d_l2g.upload(l2g, s);
+    c->d_g2l_ptr.upload(c->ls.g2l_ptr, s);
+    c->d_g2l.upload(g2l, s);
+  }
+  if (c->opt.precision == GENEO_PREC_FP32)
+    throw Error(GENEO_ERR_INVALID_ARG, "float32 local factors are not available in this build");
+
+  // --- coarse space
+  c->n0 = c->n0_snk = c->n0_geneo = 0;
+  if (c->opt.coarse == GENEO_COARSE_SNK) {
+    build_snk(t, d, c->snk);
+    c->n0_snk = (int64_t)c->snk.sub.size();
+    c->zc_ptr = c->snk.ptr;
+    c->zc_row = c->snk.row;
+    c->zc_val.resize(c->snk.sgn.size());
+    for (size_t k = 0; k < c->snk.sgn.size(); ++k) c->zc_val[k] = (double)c->snk.sgn[k];
+    c->n0 = c->n0_snk;
+  }
+  if (c->opt.geneo && c->opt.coarse != GENEO_COARSE_NONE) {
+    geneo_eigenvectors(c);  // appends GenEO columns to zc_* and sets n0_geneo
+  }
+  if (c->n0 > 0) {
+    build_z_csr(c);
+    std::vector<int64_t> pptr;
+    std::vector<int32_t> pcol;
+    coarse_pattern(c, pptr, pcol);
+    c->crs.layout({c->n0});
+    c->crs.upload_meta(s);
+    c->crs_f64.alloc(tile_elems(c->crs));
+    tiles_init_padding(c->crs, c->crs_f64.p, s);
+    DevBuf<int64_t> dpp, dctp;
+    DevBuf<int32_t> dpc, dctt;
+    DevBuf<double> dct;
+    dpp.upload(pptr, s);
+    dpc.upload(pcol, s);
+    {
+      std::vector<int64_t> ctp;
+      std::vector<int32_t> ctt;
+      std::vector<double> ctv;
+      coltet_lists(c, ctp, ctt, ctv);
+      dctp.upload(ctp, s);
+      dctt.upload(ctt, s);
+      dct.upload(ctv, s);
+    }
+    k_coltet<<<grid_for(dctt.n, 128), 128, 0, s>>>(dctt.p, dctt.n, c->d_tets.p, c->d_tet_cell.p,
+                                                   c->d_mu.p, c->d_eps.p, c->gamma, c->nx, c->ny,
+                                                   c->h[0], c->h[1], c->h[2], dct.p);
+    k_coarse_E<<<grid_for(c->n0, 8), dim3(32, 8), 0, s>>>(dpp.p, dpc.p, c->n0, dctp.p, dctt.p,
+                                                         dct.p, c->crs_f64.p);
+    GENEO_CHECK_LAUNCH();
+    DevBuf<double> ws;
+    ws.alloc(spd_workspace_elems(c->crs));
+    spd_invert(c->crs, c->crs_f64.p, ws.p, c->d_err.p, s);
+    check_device_error(c, s);
+    c->crs.schedule(c->sm_count, s);
+    c->crs_x.alloc(c->crs.vlen);
+    c->crs_y.alloc(c->crs.vlen);
+    c->crs_x.zero(s);
+  }
+
+  // --- work vectors
+  for (auto *v : {&c->v_y0, &c->v_s, &c->v_w, &c->v_t, &c->v_c, &c->p_r, &c->p_z, &c->p_p, &c->p_q,
+                  &c->h_b, &c->h_x})
+    v->alloc(n);
+  c->loc_x.alloc(c->loc.vlen);
+  c->loc_y.alloc(c->loc.vlen);
+  c->scal.alloc(16);
+  c->scal.zero(s);
+  c->partials.alloc(1024);
+  GENEO_CUDA(cudaMallocHost((void **)&c->h_scal, 16 * sizeof(double)));
+  check_device_error(c, s);
+  c->setup_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void assemble_rhs(geneo_ctx *c, const double *fslot_host, double *b, cudaStream_t s) {
+  const Topology &t = c->topo;
+  const int64_t ne = t.nedges(), nt = t.ntets();
+  DevBuf<double> fs, ce, mc;
+  fs.alloc(t.nverts * 21);
+  GENEO_CUDA(cudaMemcpyAsync(fs.p, fslot_host, sizeof(double) * t.nverts * 21,
+                             cudaMemcpyHostToDevice, s));
+  ce.alloc(ne);
+  mc.alloc(nt * 6);
+  k_rhs_edge<<<grid_for(ne, 256), 256, 0, s>>>(fs.p, c->d_edge_tail.p, c->d_edge_dir.p, c->h[0],
+                                               c->h[1], c->h[2], ne, ce.p);
+  k_rhs_element<<<grid_for(nt, 128), 128, 0, s>>>(c->d_tets.p, c->d_tet_edges.p, ce.p, c->nx,
+                                                  c->ny, c->h[0], c->h[1], c->h[2], nt, mc.p);
+  k_gather_sum<<<grid_for(t.ndofs(), 256), 256, 0, s>>>(c->d_rptr.p, c->d_ridx.p, mc.p,
+                                                        t.ndofs(), b);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
+}
+
+}  // namespace geneo

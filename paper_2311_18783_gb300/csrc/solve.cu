@@ -1,0 +1,266 @@
+// Solve path: CSR SpMV, restriction, batched local solves, prolongation,
+// coarse correction and preconditioned CG, all on one stream.
+//
+// Preconditioner (Sec. 2, eq. "AS2"; closed form at the end of Sec. 3.2):
+//   y0 = Z E^-1 Z^T r ;  s = r - A y0 ;  w = sum_i R_i^T A_i^-1 R_i s ;
+//   z  = y0 + w - Z E^-1 Z^T (A w).
+// PCG: A is SPD (Sec. 2) and M^-1_AS,2 symmetric (eq. "AS2").
+#include <chrono>
+
+#include "setup.hpp"
+
+namespace geneo {
+
+// y = A x; 8 lanes per row
+__global__ void k_spmv(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                       const double *__restrict__ val, const double *__restrict__ x,
+                       double *__restrict__ y, int64_t n) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gt >> 3;
+  const int lane = threadIdx.x & 7;
+  double s = 0;
+  if (row < n)
+    for (int32_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 8) s = fma(val[k], x[col[k]], s);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (row < n && lane == 0) y[row] = s;
+}
+
+// y = b - A x
+__global__ void k_residual(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ x,
+                           const double *__restrict__ b, double *__restrict__ y, int64_t n) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gt >> 3;
+  const int lane = threadIdx.x & 7;
+  double s = 0;
+  if (row < n)
+    for (int32_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 8) s = fma(val[k], x[col[k]], s);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (row < n && lane == 0) y[row] = b[row] - s;
+}
+
+// padded local vector x_loc[p] = s[l2g[p]] (0 on padding)
+__global__ void k_restrict(const int32_t *__restrict__ l2g, const double *__restrict__ s,
+                           double *__restrict__ xl, int64_t len) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= len) return;
+  const int32_t g = l2g[p];
+  xl[p] = g >= 0 ? s[g] : 0.0;
+}
+
+// w[e] = sum over the local slots holding e (deterministic gather-sum)
+__global__ void k_prolong(const int64_t *__restrict__ ptr, const int64_t *__restrict__ slot,
+                          const double *__restrict__ yl, double *__restrict__ w, int64_t n) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0;
+  for (int64_t k = ptr[e]; k < ptr[e + 1]; ++k) s += yl[slot[k]];
+  w[e] = s;
+}
+
+// t[a] = (Z^T r)_a, one column per thread (CSC)
+__global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zrow,
+                     const double *__restrict__ zval, const double *__restrict__ r,
+                     double *__restrict__ t, int64_t n0) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= n0) return;
+  double s = 0;
+  for (int64_t k = zptr[a]; k < zptr[a + 1]; ++k) s = fma(zval[k], r[zrow[k]], s);
+  t[a] = s;
+}
+
+// y[e] = (Z u)_e, one row per thread (CSR)
+__global__ void k_z(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zcol,
+                    const double *__restrict__ zval, const double *__restrict__ u,
+                    double *__restrict__ y, int64_t n) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0;
+  for (int64_t k = zptr[e]; k < zptr[e + 1]; ++k) s = fma(zval[k], u[zcol[k]], s);
+  y[e] = s;
+}
+
+// z = y0 + w - c
+__global__ void k_combine(const double *__restrict__ y0, const double *__restrict__ w,
+                          const double *__restrict__ c, double *__restrict__ z, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) z[i] = (y0[i] + w[i]) - c[i];
+}
+
+// ---------------------------------------------------------------------------
+// deterministic dot products: fixed grid, block partials, one final block
+
+constexpr int kDotBlocks = 512;
+
+__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                              double *__restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_dot_final(const double *__restrict__ part, int np, double *__restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = s;
+  }
+}
+
+static void dot(geneo_ctx *c, const double *a, const double *b, int64_t n, double *out,
+                cudaStream_t s) {
+  k_dot_partial<<<kDotBlocks, 256, 0, s>>>(a, b, n, c->partials.p);
+  k_dot_final<<<1, 256, 0, s>>>(c->partials.p, kDotBlocks, out);
+}
+
+// scalars: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 bb
+// x += alpha p ; r -= alpha q  with alpha = rz / pq
+__global__ void k_update_xr(const double *__restrict__ sc, const double *__restrict__ p,
+                            const double *__restrict__ q, double *__restrict__ x,
+                            double *__restrict__ r, int64_t n) {
+  const double alpha = sc[0] / sc[1];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+
+// p = z + beta p with beta = rz_new / rz; then rz = rz_new
+__global__ void k_update_p(double *__restrict__ sc, const double *__restrict__ z,
+                           double *__restrict__ p, int64_t n) {
+  const double beta = sc[3] / sc[0];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void k_shift_rz(double *sc) { sc[0] = sc[3]; }
+
+__global__ void k_copy(const double *__restrict__ a, double *__restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+// ---------------------------------------------------------------------------
+
+void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  k_spmv<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x, y, n);
+  GENEO_CHECK_LAUNCH();
+}
+
+void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  k_restrict<<<grid_for(c->loc.vlen, 256), 256, 0, s>>>(c->d_l2g.p, r, c->loc_x.p, c->loc.vlen);
+  symv_batch<double>(c->loc, c->loc_f64.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s);
+  k_prolong<<<grid_for(n, 256), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w, n);
+  GENEO_CHECK_LAUNCH();
+}
+
+void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  if (c->n0 == 0) {
+    GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, s));
+    return;
+  }
+  k_zt<<<grid_for(c->n0, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
+                                            c->crs_x.p, c->n0);
+  symv_batch<double>(c->crs, c->crs_f64.p, c->crs_x.p, c->crs_y.p, c->d_err.p, s);
+  k_z<<<grid_for(n, 256), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p, c->crs_y.p,
+                                       y, n);
+  GENEO_CHECK_LAUNCH();
+}
+
+void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  if (c->n0 == 0) {
+    local_solve(c, r, z, s);
+    return;
+  }
+  coarse_solve(c, r, c->v_y0.p, s);
+  k_residual<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
+                                                  c->v_y0.p, r, c->v_s.p, n);
+  local_solve(c, c->v_s.p, c->v_w.p, s);
+  spmv(c, c->v_w.p, c->v_t.p, s);
+  coarse_solve(c, c->v_t.p, c->v_c.p, s);
+  k_combine<<<grid_for(n, 256), 256, 0, s>>>(c->v_y0.p, c->v_w.p, c->v_c.p, z, n);
+  GENEO_CHECK_LAUNCH();
+}
+
+int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_solve_info *info,
+        cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = c->topo.ndofs();
+  double *sc = c->scal.p;
+  double *hs = c->h_scal;
+  const unsigned g = grid_for(n, 256);
+  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
+  dot(c, b, b, n, sc + 4, s);
+  apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
+  k_copy<<<g, 256, 0, s>>>(c->p_z.p, c->p_p.p, n);
+  dot(c, c->p_r.p, c->p_z.p, n, sc + 0, s);
+  GENEO_CUDA(cudaMemcpyAsync(hs, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(hs[4]);
+  int status = GENEO_NOT_CONVERGED, it = 0;
+  double rel = 1.0;
+  if (bnorm == 0.0) {
+    status = GENEO_OK;
+    rel = 0.0;
+  } else {
+    for (it = 1; it <= maxit; ++it) {
+      spmv(c, c->p_p.p, c->p_q.p, s);
+      dot(c, c->p_p.p, c->p_q.p, n, sc + 1, s);
+      k_update_xr<<<g, 256, 0, s>>>(sc, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
+      dot(c, c->p_r.p, c->p_r.p, n, sc + 2, s);
+      GENEO_CUDA(cudaMemcpyAsync(hs, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      GENEO_CUDA(cudaStreamSynchronize(s));
+      if (!(hs[1] > 0.0) || !std::isfinite(hs[1]) || !std::isfinite(hs[2])) {
+        status = GENEO_ERR_BREAKDOWN;
+        break;
+      }
+      rel = std::sqrt(hs[2]) / bnorm;
+      if (rel <= tol) {
+        status = GENEO_OK;
+        break;
+      }
+      apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
+      dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s);
+      k_update_p<<<g, 256, 0, s>>>(sc, c->p_z.p, c->p_p.p, n);
+      k_shift_rz<<<1, 1, 0, s>>>(sc);
+      GENEO_CHECK_LAUNCH();
+    }
+    if (it > maxit) it = maxit;
+  }
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  check_device_error(c, s);
+  if (info) {
+    info->iters = it;
+    info->relres = rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+}  // namespace geneo

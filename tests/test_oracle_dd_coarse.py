@@ -155,7 +155,7 @@ def test_gevp_count_by_inertia():
     m, A, AT, dec = setup(w)
     for tau in (0.5, 2.0):
         for j in range(dec.nsub):
-            g = local_gevp(m, A, AT, dec, j)
+            g = local_gevp(m, w, A, AT, dec, j)
             Lm = g.L - tau * g.Aneu
             lu, d, perm = sla.ldl(0.5 * (Lm + Lm.T))
             evd = np.concatenate([np.linalg.eigvalsh(d[k:k + 2, k:k + 2]) if (
@@ -237,7 +237,7 @@ def test_condition_number_bound_snk_only():
     w = small(n=(6, 4, 4), parts=(2, 2, 1), overlap=1, gamma=1e-3, seed=6)
     prob = build_problem(w, geneo=False)
     m, A, AT, dec = prob.mesh, prob.A, prob.AT, prob.dec
-    tau0 = max(local_gevp(m, A, AT, dec, j).lam[0] for j in range(dec.nsub))
+    tau0 = max(local_gevp(m, w, A, AT, dec, j).lam[0] for j in range(dec.nsub))
     ev = np.sort(np.real(np.linalg.eigvals(_dense_precond(prob) @ A.toarray())))
     assert ev[-1] <= k0(A, dec) * (1 + 1e-8)
     assert ev[0] >= 1.0 / (1.0 + k1(dec) * tau0) * (1 - 1e-8)
@@ -258,3 +258,23 @@ def test_pcg_matches_direct_solve():
     r1 = pcg(prob.A, prob.b[0], build_problem(w, coarse="none", geneo=False).M.apply, 1e-8)
     r2 = solve(prob, tol=1e-8)
     assert r2.iters <= r1.iters
+
+
+def test_galerkin_through_curl_operator():
+    """K = C^T C, and E = Z^T A Z computed element by element through C
+    equals the assembled product; for pure gradients the curl-route K-part
+    vanishes to rounding squared, far below the assembled residue."""
+    from oracle.fem import curl_operator, assemble_K
+    from oracle.coarse import galerkin
+    w = small(n=(6, 5, 4), parts=(2, 2, 1), overlap=1, gamma=1e-2)
+    m, A, AT, dec = setup(w)
+    C = curl_operator(m, w)
+    K = assemble_K(m, w)
+    assert abs(C.T @ C - K).max() <= 1e-13 * abs(K).max()
+    Z = assemble_Z(A.shape[0], snk_columns(m, dec))
+    E1 = galerkin(m, w, Z)
+    E2 = (Z.T @ (A @ Z)).toarray()
+    assert np.abs(E1 - E2).max() <= 1e-12 * np.abs(A).max()
+    G = gradient_dofs(m)
+    CG = C @ G
+    assert abs(CG.T @ CG).max() <= 1e-24 * abs(K).max()
