@@ -90,7 +90,7 @@ typedef struct {
   int32_t coarse;            /* GENEO_COARSE_* */
   int32_t geneo;             /* 1: add GenEO eigenvectors to the coarse space */
   int32_t tau_convention;    /* GENEO_TAU_* */
-  int32_t lobpcg_block;      /* block size of the batched LOBPCG (>= 1) */
+  int32_t lobpcg_block;      /* block size of the batched LOBPCG, 1..16 */
   int32_t lobpcg_maxit;      /* iterations per block before giving up */
   double lobpcg_tol;         /* relative eigen-residual tolerance */
   uint64_t seed;             /* initial LOBPCG blocks (counter-based hash) */
@@ -165,6 +165,25 @@ int geneo_solve(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol, 
  * copies x back to x_host[n] before returning. */
 int geneo_solve_host(geneo_ctx *ctx, const double *b_host, double *x_host, double tol,
                      int32_t maxit, geneo_solve_info *info, void *stream);
+
+/* Per-stage counters of the solve path, collected while profiling is on. */
+typedef struct {
+  int64_t launches;          /* kernels this library launched since the last read */
+  int64_t local_symv_launches;  /* launches of the local-factor SYMV kernel */
+  double local_symv_ms;      /* their summed duration (CUDA events on the caller's stream) */
+  int64_t coarse_symv_launches;
+  double coarse_symv_ms;
+  int64_t local_symv_bytes;  /* algorithmic bytes of one local SYMV launch (stored tiles) */
+  int64_t local_symv_flops;  /* algorithmic flops of one local SYMV launch: 2 sum_i n_i^2 */
+} geneo_profile;
+
+/* on != 0: record CUDA events around every SYMV launch (adds two event
+ * records per launch) and count launches.  Off by default. */
+int geneo_profile_enable(geneo_ctx *ctx, int32_t on);
+
+/* Waits for the recorded events, fills *out with the counters accumulated
+ * since the previous read and resets them. */
+int geneo_profile_read(geneo_ctx *ctx, geneo_profile *out);
 
 /* Copies the internal array `name` into host memory dst (capacity bytes);
  * *size receives the byte size (call with dst = NULL to query).  For parity

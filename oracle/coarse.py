@@ -247,12 +247,17 @@ def galerkin(mesh, w, X, Y=None):
     M = assemble_mass(mesh, w)
     CX, CY = Cm @ X, Cm @ Y
     out = CX.T @ CY + w.gamma * (X.T @ (M @ Y))
-    return out.toarray() if sp.issparse(out) else np.asarray(out)
+    return out
 
 
-def coarse_matrix(mesh, w, Z):
-    """E = Z^T A Z (Sec. 2), element by element (see galerkin)."""
+def coarse_matrix(mesh, w, Z, dense_limit=6000):
+    """E = Z^T A Z (Sec. 2), element by element (see galerkin); dense below
+    dense_limit columns, sparse CSR above."""
     E = galerkin(mesh, w, Z)
+    if sp.issparse(E):
+        E = sp.csr_matrix(0.5 * (E + E.T))
+        return E.toarray() if E.shape[0] <= dense_limit else E
+    E = np.asarray(E)
     return 0.5 * (E + E.T)
 
 
@@ -263,12 +268,13 @@ def independent_geneo(E, n_snk):
     m = E.shape[0] - n_snk
     if m == 0:
         return np.zeros(0, np.int64)
-    Ehh = E[n_snk:, n_snk:]
+    dense = lambda X: X.toarray() if sp.issparse(X) else np.asarray(X)
+    Ehh = dense(E[n_snk:, n_snk:])
     diag = np.diag(Ehh).copy()
     if n_snk > 0:
         Egg = E[:n_snk, :n_snk]
-        Egh = E[:n_snk, n_snk:]
-        if n_snk <= 6000:
+        Egh = dense(E[:n_snk, n_snk:])
+        if not sp.issparse(Egg):
             S = Ehh - Egh.T @ sla.cho_solve(sla.cho_factor(Egg), Egh)
         else:
             import scipy.sparse.linalg as spla

@@ -56,7 +56,7 @@ def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
             E = coarse_matrix(mesh, w, assemble_Z(n, cols + gcols))
             keep = independent_geneo(E, len(cols))
             sel = np.concatenate([np.arange(len(cols)), len(cols) + keep])
-            E = E[np.ix_(sel, sel)]
+            E = E[np.ix_(sel, sel)] if not hasattr(E, "tocsr") else E.tocsr()[sel][:, sel]
             gcols = [gcols[k] for k in keep.tolist()]
     Z = assemble_Z(n, cols + gcols) if (cols or gcols) else None
     if Z is not None and E is None:

@@ -39,7 +39,7 @@ class TwoLevel:
     def local(self, s):
         w = np.zeros_like(s)
         for Ni, F in zip(self.N, self.Ainv_fact):
-            w[Ni] += sla.cho_solve(F, s[Ni])
+            w[Ni] += F(s[Ni])
         return w
 
     def apply(self, r):
@@ -50,11 +50,13 @@ class TwoLevel:
 
 
 def factor_dense(E):
+    """Dense Cholesky (library primitive); returns the solve."""
     F = sla.cho_factor(E, lower=True)
     return lambda c: sla.cho_solve(F, c)
 
 
 def factor_sparse(E):
+    """Sparse LU (library primitive) for large SPD blocks; returns the solve."""
     lu = spla.splu(sp.csc_matrix(E))
     return lu.solve
 
@@ -64,15 +66,20 @@ def build_preconditioner(A, dec, Z, local_mats=None, E=None):
     from the assembled A unless given)."""
     Ainv = []
     for i in range(dec.nsub):
-        Ai = A[dec.N[i]][:, dec.N[i]].toarray() if local_mats is None else local_mats[i]
-        Ainv.append(sla.cho_factor(Ai, lower=True))
+        Ni = dec.N[i]
+        if local_mats is not None:
+            Ainv.append(factor_dense(local_mats[i]))
+        elif len(Ni) <= 2000:
+            Ainv.append(factor_dense(A[Ni][:, Ni].toarray()))
+        else:
+            Ainv.append(factor_sparse(A[Ni][:, Ni]))
     if Z is None or Z.shape[1] == 0:
         return TwoLevel(A, dec.N, Ainv, None, None)
     if E is None:
         E = (Z.T @ (A @ Z))
         E = E.toarray() if sp.issparse(E) else E
         E = 0.5 * (E + E.T)
-    fact = factor_dense(E) if E.shape[0] <= 6000 else factor_sparse(E)
+    fact = factor_dense(E) if not sp.issparse(E) else factor_sparse(E)
     return TwoLevel(A, dec.N, Ainv, Z, fact)
 
 

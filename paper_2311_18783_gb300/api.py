@@ -55,6 +55,16 @@ class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double), ("seconds", C.c_double)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("local_symv_launches", C.c_int64),
+                ("local_symv_ms", C.c_double), ("coarse_symv_launches", C.c_int64),
+                ("coarse_symv_ms", C.c_double), ("local_symv_bytes", C.c_int64),
+                ("local_symv_flops", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _LIB = None
 
 # exported C functions and their argument types
@@ -74,6 +84,8 @@ _SIGS = {
                                    C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_export": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64,
                                C.POINTER(C.c_int64)]),
+    "geneo_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "geneo_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "geneo_last_error": (C.c_char_p, []),
     "geneo_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -220,6 +232,14 @@ class Solver:
                                           _stream(stream)))
         return xh, {"status": st, "iters": info.iters, "relres": info.relres,
                     "seconds": info.seconds}
+
+    def profile(self, on=True):
+        _check(_LIB.geneo_profile_enable(self._ctx, 1 if on else 0))
+
+    def profile_read(self):
+        p = Profile()
+        _check(_LIB.geneo_profile_read(self._ctx, C.byref(p)))
+        return p.as_dict()
 
     def export(self, name):
         size = C.c_int64(0)

@@ -32,8 +32,22 @@ cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 }  // namespace
 
 geneo_ctx::~geneo_ctx() {
+  for (auto &p : ev_local) ev_free.insert(ev_free.end(), {p.first, p.second});
+  for (auto &p : ev_coarse) ev_free.insert(ev_free.end(), {p.first, p.second});
+  for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
   if (h_scal) cudaFreeHost(h_scal);
   if (stream) cudaStreamDestroy(stream);
+}
+
+cudaEvent_t geneo_ctx::ev_take() {
+  if (ev_free.empty()) {
+    cudaEvent_t e;
+    GENEO_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  cudaEvent_t e = ev_free.back();
+  ev_free.pop_back();
+  return e;
 }
 
 extern "C" {
@@ -74,7 +88,7 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
     return fail(GENEO_ERR_INVALID_ARG, "unknown precision");
   if (o.coarse != GENEO_COARSE_NONE && o.coarse != GENEO_COARSE_SNK)
     return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
-  if (o.lobpcg_block < 1 || o.lobpcg_block > 32 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
+  if (o.lobpcg_block < 1 || o.lobpcg_block > 16 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
     return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");
   return guarded([&]() {
     auto c = new geneo_ctx();
@@ -198,6 +212,42 @@ int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int
     GENEO_CUDA(cudaMemcpyAsync(xh, c->h_x.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     GENEO_CUDA(cudaStreamSynchronize(st));
     return rc;
+  });
+}
+
+int geneo_profile_enable(geneo_ctx *c, int32_t on) {
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  c->prof = on != 0;
+  return GENEO_OK;
+}
+
+int geneo_profile_read(geneo_ctx *c, geneo_profile *o) {
+  if (!c || !o) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    std::memset(o, 0, sizeof(*o));
+    o->launches = c->launches;
+    auto sum = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, double &ms) {
+      for (auto &p : v) {
+        GENEO_CUDA(cudaEventSynchronize(p.second));
+        float t = 0;
+        GENEO_CUDA(cudaEventElapsedTime(&t, p.first, p.second));
+        ms += t;
+        c->ev_free.push_back(p.first);
+        c->ev_free.push_back(p.second);
+      }
+      const int64_t k = (int64_t)v.size();
+      v.clear();
+      return k;
+    };
+    o->local_symv_launches = sum(c->ev_local, o->local_symv_ms);
+    o->coarse_symv_launches = sum(c->ev_coarse, o->coarse_symv_ms);
+    o->local_symv_bytes = c->loc.ntiles * (int64_t)geneo::kTileElems *
+                          (c->loc_f32.p ? (int64_t)sizeof(float) : (int64_t)sizeof(double));
+    int64_t fl = 0;
+    for (int i = 0; i < c->dec.nsub; ++i) fl += 2 * c->dec.ni(i) * c->dec.ni(i);
+    o->local_symv_flops = fl;
+    c->launches = 0;
+    return GENEO_OK;
   });
 }
 

@@ -59,5 +59,12 @@ struct geneo_ctx {
   geneo::DevBuf<int> d_err;
   double *h_scal = nullptr;  // pinned host mirror of the PCG scalars
 
+  // profiling: host launch counter and event pairs around SYMV launches
+  bool prof = false;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_local, ev_coarse;
+  cudaEvent_t ev_take();
+
   ~geneo_ctx();
 };

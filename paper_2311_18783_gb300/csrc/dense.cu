@@ -620,7 +620,7 @@ template <typename T> constexpr int symv_stages() { return sizeof(T) == 8 ? 4 : 
 
 template <typename T>
 void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
-                cudaStream_t s) {
+                cudaStream_t s, cudaEvent_t ev_before, cudaEvent_t ev_after) {
   constexpr int NST = symv_stages<T>();
   const size_t smem = (size_t)NST * kTileElems * sizeof(T) + NST * sizeof(uint64_t) +
                       8 * kTile * sizeof(typename Acc<T>::type);
@@ -630,9 +630,11 @@ void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
+  if (ev_before) GENEO_CUDA(cudaEventRecord(ev_before, s));
   k_symv_strips<T, NST><<<b.sched_ctas, 256, smem, s>>>(
       data, b.d_toff.p, b.d_voff.p, b.d_strip_m.p, b.d_strip_I.p, b.d_cta_off.p, x, b.rowpart.p,
       b.colpart.p, d_err);
+  if (ev_after) GENEO_CUDA(cudaEventRecord(ev_after, s));
   const int64_t nblocks = b.vlen / kTile;
   k_symv_reduce<<<(unsigned)nblocks, kTile, 0, s>>>(b.d_vrow_m.p, b.d_vrow_I.p, b.d_nt.p,
                                                     b.d_toff.p, b.d_voff.p, b.rowpart.p,
@@ -641,8 +643,8 @@ void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_
 }
 
 template void symv_batch<double>(TileBatch &, const double *, const double *, double *, int *,
-                                 cudaStream_t);
+                                 cudaStream_t, cudaEvent_t, cudaEvent_t);
 template void symv_batch<float>(TileBatch &, const float *, const double *, double *, int *,
-                                cudaStream_t);
+                                cudaStream_t, cudaEvent_t, cudaEvent_t);
 
 }  // namespace geneo

@@ -46,9 +46,10 @@ void chol_factor(TileBatch &b, double *data, const int32_t *d_npiv, int nsteps, 
                  const int64_t *d_dtoff, int *d_err, cudaStream_t s);
 
 // -- y = blockdiag(A_m) x on padded vectors.  Templated on the storage type.
+// ev_before / ev_after, when given, are recorded around the streaming kernel.
 template <typename T>
 void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
-                cudaStream_t s);
+                cudaStream_t s, cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 
 // Pointer/size of a tile-packed buffer in elements.
 inline int64_t tile_elems(const TileBatch &b) { return b.ntiles * (int64_t)kTileElems; }

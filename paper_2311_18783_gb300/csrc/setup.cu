@@ -208,21 +208,20 @@ __global__ void k_coltet(const int32_t *__restrict__ ct_tet, int64_t nent,
   }
 }
 
-// E[a][b] for the lower pattern, written into the tile-packed coarse matrix
-// (both triangles of diagonal tiles).  Iterates over the shorter tet list and
-// binary-searches the longer one.
-__global__ void k_coarse_E(const int64_t *__restrict__ pptr, const int32_t *__restrict__ pcol,
-                           int64_t n0, const int64_t *__restrict__ ct_ptr,
+// (X^T A X)[a][b] for the lower pattern of each matrix of a tile batch:
+// column a belongs to matrix cmat[a] at local index cloc[a]; iterates over
+// the shorter tet list and binary-searches the longer one.
+__global__ void k_galerkin(const int64_t *__restrict__ pptr, const int32_t *__restrict__ pcol,
+                           int64_t ncols, const int64_t *__restrict__ ct_ptr,
                            const int32_t *__restrict__ ct_tet, const double *__restrict__ ct,
-                           double *__restrict__ tiles) {
+                           const int32_t *__restrict__ cmat, const int32_t *__restrict__ cloc,
+                           const int64_t *__restrict__ toff, double *__restrict__ tiles) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
-  if (a >= n0) return;
+  if (a >= ncols) return;
   for (int64_t q = pptr[a] + threadIdx.x; q < pptr[a + 1]; q += blockDim.x) {
     const int64_t b = pcol[q];
-    int64_t sa = ct_ptr[a], ea = ct_ptr[a + 1], sb = ct_ptr[b], eb = ct_ptr[b + 1];
+    const int64_t sa = ct_ptr[a], ea = ct_ptr[a + 1], sb = ct_ptr[b], eb = ct_ptr[b + 1];
     const bool swap = (ea - sa) > (eb - sb);
-    // iterate over list x, search in list y; the dot is symmetric in the
-    // roles only for the K part, so keep track of which side is a
     const int64_t xs = swap ? sb : sa, xe = swap ? eb : ea, ys = swap ? sa : sb, ye = swap ? ea : eb;
     double s = 0;
     for (int64_t i = xs; i < xe; ++i) {
@@ -231,22 +230,70 @@ __global__ void k_coarse_E(const int64_t *__restrict__ pptr, const int32_t *__re
       while (lo <= hi) {
         const int64_t mid = (lo + hi) >> 1;
         const int32_t v = ct_tet[mid];
-        if (v == t) { hit = mid; break; }
+        if (v == t) {
+          hit = mid;
+          break;
+        }
         if (v < t) lo = mid + 1;
         else hi = mid - 1;
       }
       if (hit < 0) continue;
-      const double *ea_ = ct + (swap ? hit : i) * 15;   // entry of column a
-      const double *eb_ = ct + (swap ? i : hit) * 15;   // entry of column b
+      const double *ea_ = ct + (swap ? hit : i) * 15;  // entry of column a
+      const double *eb_ = ct + (swap ? i : hit) * 15;  // entry of column b
       double v = ea_[0] * eb_[0] + ea_[1] * eb_[1] + ea_[2] * eb_[2];
       for (int k = 0; k < 6; ++k) v = fma(ea_[3 + k], eb_[9 + k], v);
       s += v;
     }
-    const int I = (int)(a / kTile), J = (int)(b / kTile);
-    const int64_t tb = ((int64_t)I * (I + 1) / 2 + J) * kTileElems;
-    tiles[tb + (a % kTile) * kTile + (b % kTile)] = s;
-    if (I == J) tiles[tb + (b % kTile) * kTile + (a % kTile)] = s;
+    const int m = cmat[a];
+    const int64_t la = cloc[a], lb = cloc[b];
+    const int I = (int)(la / kTile), J = (int)(lb / kTile);
+    const int64_t tb = (toff[m] + (int64_t)I * (I + 1) / 2 + J) * kTileElems;
+    tiles[tb + (la % kTile) * kTile + (lb % kTile)] = s;
+    if (I == J) tiles[tb + (lb % kTile) * kTile + (la % kTile)] = s;
   }
+}
+
+__global__ void k_set_diag(double *tiles, const int64_t *toff, int m, int64_t r0, int64_t r1) {
+  const int64_t r = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= r1) return;
+  const int I = (int)(r / kTile);
+  tiles[(toff[m] + (int64_t)I * (I + 1) / 2 + I) * kTileElems + (r % kTile) * (kTile + 1)] = 1.0;
+}
+
+__global__ void k_take(const double *__restrict__ src, const int32_t *__restrict__ idx,
+                       double *__restrict__ dst, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+// per tetrahedron: scaled curls (18) and gamma eps M_T (36)
+__global__ void k_tet_ops(const int32_t *__restrict__ tets, const int32_t *__restrict__ tet_cell,
+                          const double *__restrict__ mu, const double *__restrict__ eps,
+                          double gamma, int nx, int ny, double hx, double hy, double hz,
+                          int64_t ntets, double *__restrict__ tcurl, double *__restrict__ tmass) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntets) return;
+  double g[4][3], vol, K[6][6], M[6][6];
+  tet_geometry(tets + 4 * t, nx, ny, hx, hy, hz, g, vol);
+  element_KM(g, vol, K, M);
+  const int cell = tet_cell[t];
+  const double sc = sqrt(mu[cell] * vol), ge = gamma * eps[cell];
+  for (int e = 0; e < 6; ++e) {
+    double cw[3];
+    cross3(g[c_le[e][0]], g[c_le[e][1]], cw);
+    for (int d = 0; d < 3; ++d) tcurl[t * 18 + e * 3 + d] = sc * 2.0 * cw[d];
+    for (int f = 0; f < 6; ++f) tmass[t * 36 + e * 6 + f] = ge * M[e][f];
+  }
+}
+
+void tet_operators(geneo_ctx *c, DevBuf<double> &tcurl, DevBuf<double> &tmass, cudaStream_t s) {
+  const int64_t nt = c->topo.ntets();
+  tcurl.alloc(nt * 18);
+  tmass.alloc(nt * 36);
+  k_tet_ops<<<grid_for(nt, 128), 128, 0, s>>>(c->d_tets.p, c->d_tet_cell.p, c->d_mu.p, c->d_eps.p,
+                                              c->gamma, c->nx, c->ny, c->h[0], c->h[1], c->h[2], nt,
+                                              tcurl.p, tmass.p);
+  GENEO_CHECK_LAUNCH();
 }
 
 // ---------------------------------------------------------------------------
@@ -283,12 +330,15 @@ static void build_z_csr(geneo_ctx *c) {
   GENEO_CUDA(cudaStreamSynchronize(c->stream));
 }
 
-// column-tetrahedron lists of Z (tets touching each column's support, sorted)
-// with the six local coefficients of the column on each tetrahedron
-static void coltet_lists(const geneo_ctx *c, std::vector<int64_t> &ct_ptr,
-                         std::vector<int32_t> &ct_tet, std::vector<double> &ct) {
+// Column-tetrahedron lists of sparse columns: for each column the sorted
+// tetrahedra touching its support (only those of Omega_mat when X.neumann),
+// with the 15-double entries of k_coltet computed on the device.
+void coltet_build(geneo_ctx *c, const Columns &X, std::vector<int64_t> &ct_ptr,
+                  std::vector<int32_t> &ct_tet, DevBuf<int64_t> &dctp, DevBuf<int32_t> &dctt,
+                  DevBuf<double> &dct, cudaStream_t s) {
   const Topology &t = c->topo;
-  const int64_t n = t.ndofs(), nt = t.ntets();
+  const int64_t n = t.ndofs(), nt = t.ntets(), ncol = (int64_t)X.mat.size();
+  // unknown -> tetrahedra
   std::vector<int64_t> tp(n + 1, 0);
   for (int64_t q = 0; q < nt * 6; ++q) {
     const int32_t d = t.edge_dof[t.tet_edges[q]];
@@ -303,23 +353,25 @@ static void coltet_lists(const geneo_ctx *c, std::vector<int64_t> &ct_ptr,
       if (d >= 0) tl[fill[d]++] = (int32_t)(q / 6);
     }
   }
+  ct_ptr.assign(1, 0);
+  ct_tet.clear();
+  std::vector<double> ct;
   std::vector<double> val(n, 0.0);
   std::vector<uint8_t> in(n, 0);
   std::vector<int32_t> tets;
-  ct_ptr.assign(1, 0);
-  ct_tet.clear();
-  ct.clear();
-  for (int64_t a = 0; a < c->n0; ++a) {
+  for (int64_t a = 0; a < ncol; ++a) {
     tets.clear();
-    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
-      const int32_t e = c->zc_row[k];
-      val[e] = c->zc_val[k];
+    for (int64_t k = X.ptr[a]; k < X.ptr[a + 1]; ++k) {
+      const int32_t e = X.row[k];
+      val[e] = X.val[k];
       in[e] = 1;
       tets.insert(tets.end(), tl.begin() + tp[e], tl.begin() + tp[e + 1]);
     }
     std::sort(tets.begin(), tets.end());
     tets.erase(std::unique(tets.begin(), tets.end()), tets.end());
+    const std::vector<int32_t> *cells = X.neumann ? &c->dec.sub_cells[X.mat[a]] : nullptr;
     for (int32_t tt : tets) {
+      if (cells && !std::binary_search(cells->begin(), cells->end(), t.tet_cell[tt])) continue;
       ct_tet.push_back(tt);
       double ent[15] = {0};
       for (int k = 0; k < 6; ++k) {
@@ -329,51 +381,165 @@ static void coltet_lists(const geneo_ctx *c, std::vector<int64_t> &ct_ptr,
       ct.insert(ct.end(), ent, ent + 15);
     }
     ct_ptr.push_back((int64_t)ct_tet.size());
-    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
-      val[c->zc_row[k]] = 0.0;
-      in[c->zc_row[k]] = 0;
+    for (int64_t k = X.ptr[a]; k < X.ptr[a + 1]; ++k) {
+      val[X.row[k]] = 0.0;
+      in[X.row[k]] = 0;
     }
   }
+  dctp.upload(ct_ptr, s);
+  dctt.upload(ct_tet, s);
+  dct.upload(ct, s);
+  if (dctt.n)
+    k_coltet<<<grid_for(dctt.n, 128), 128, 0, s>>>(dctt.p, dctt.n, c->d_tets.p, c->d_tet_cell.p,
+                                                   c->d_mu.p, c->d_eps.p, c->gamma, c->nx, c->ny,
+                                                   c->h[0], c->h[1], c->h[2], dct.p);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));
 }
 
-// lower pattern of E = Z^T A Z: b <= a with supports of columns a, b coupled by A
-static void coarse_pattern(const geneo_ctx *c, std::vector<int64_t> &pptr,
-                           std::vector<int32_t> &pcol) {
-  const int64_t n = c->topo.ndofs();
+// X^T A X for the columns, element by element through per-tet curls (see
+// k_coltet), written into `tiles` of batch b at (cloc[a], cloc[b]).
+void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles, cudaStream_t s) {
   const Topology &t = c->topo;
-  std::vector<int64_t> dp(n + 1, 0);
-  for (int32_t r : c->zc_row) dp[r + 1]++;
-  for (int64_t e = 0; e < n; ++e) dp[e + 1] += dp[e];
-  std::vector<int32_t> dc(c->zc_row.size());
+  const int64_t nt = t.ntets(), ncol = (int64_t)X.mat.size();
+  if (ncol == 0) return;
+  std::vector<int64_t> ct_ptr;
+  std::vector<int32_t> ct_tet;
+  DevBuf<int64_t> dctp;
+  DevBuf<int32_t> dctt;
+  DevBuf<double> dct;
+  coltet_build(c, X, ct_ptr, ct_tet, dctp, dctt, dct, s);
+  // lower pattern: columns of the same matrix sharing a tetrahedron
+  std::vector<int64_t> tcp(nt + 1, 0);
+  for (int32_t tt : ct_tet) tcp[tt + 1]++;
+  for (int64_t q = 0; q < nt; ++q) tcp[q + 1] += tcp[q];
+  std::vector<int32_t> tcl(ct_tet.size());
   {
-    std::vector<int64_t> fill(dp.begin(), dp.end() - 1);
-    for (int64_t a = 0; a < c->n0; ++a)
-      for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) dc[fill[c->zc_row[k]]++] = (int32_t)a;
+    std::vector<int64_t> fill(tcp.begin(), tcp.end() - 1);
+    for (int64_t a = 0; a < ncol; ++a)
+      for (int64_t q = ct_ptr[a]; q < ct_ptr[a + 1]; ++q) tcl[fill[ct_tet[q]]++] = (int32_t)a;
   }
-  std::vector<uint8_t> mark(c->n0, 0);
-  std::vector<int32_t> list;
-  pptr.assign(1, 0);
-  pcol.clear();
-  for (int64_t a = 0; a < c->n0; ++a) {
+  std::vector<int64_t> pptr(1, 0);
+  std::vector<int32_t> pcol, list;
+  std::vector<uint8_t> mark(ncol, 0);
+  for (int64_t a = 0; a < ncol; ++a) {
     list.clear();
-    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
-      const int32_t e = c->zc_row[k];
-      for (int32_t q = t.rowptr[e]; q < t.rowptr[e + 1]; ++q) {
-        const int32_t f = t.col[q];
-        for (int64_t u = dp[f]; u < dp[f + 1]; ++u) {
-          const int32_t b = dc[u];
-          if (b <= a && !mark[b]) {
-            mark[b] = 1;
-            list.push_back(b);
-          }
+    for (int64_t q = ct_ptr[a]; q < ct_ptr[a + 1]; ++q) {
+      const int32_t tt = ct_tet[q];
+      for (int64_t u = tcp[tt]; u < tcp[tt + 1]; ++u) {
+        const int32_t bb = tcl[u];
+        if (X.mat[bb] == X.mat[a] && X.loc[bb] <= X.loc[a] && !mark[bb]) {
+          mark[bb] = 1;
+          list.push_back(bb);
         }
       }
     }
     std::sort(list.begin(), list.end());
-    for (int32_t b : list) mark[b] = 0;
+    for (int32_t bb : list) mark[bb] = 0;
     pcol.insert(pcol.end(), list.begin(), list.end());
     pptr.push_back((int64_t)pcol.size());
   }
+  DevBuf<int64_t> dpp;
+  DevBuf<int32_t> dpc, dmat, dloc;
+  dpp.upload(pptr, s);
+  dpc.upload(pcol, s);
+  dmat.upload(X.mat, s);
+  dloc.upload(X.loc, s);
+  k_galerkin<<<grid_for(ncol, 8), dim3(32, 8), 0, s>>>(dpp.p, dpc.p, ncol, dctp.p, dctt.p, dct.p,
+                                                      dmat.p, dloc.p, b.d_toff.p, tiles);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+// Coarse columns as Galerkin input; column a placed at local index loc(a)
+static Columns coarse_columns(const geneo_ctx *c, int64_t gap_after_snk) {
+  Columns X;
+  for (int64_t a = 0; a < c->n0; ++a) {
+    for (int64_t k = c->zc_ptr[a]; k < c->zc_ptr[a + 1]; ++k) {
+      X.row.push_back(c->zc_row[k]);
+      X.val.push_back(c->zc_val[k]);
+    }
+    X.ptr.push_back((int64_t)X.row.size());
+    X.mat.push_back(0);
+    X.loc.push_back((int32_t)(a < c->n0_snk ? a : a + gap_after_snk));
+  }
+  return X;
+}
+
+// Z must be a full-rank basis of V_G + V_GenEO (Sec. 3.2, eq. "V0GenEOAS"):
+// drop GenEO columns whose pivot in the ordered Cholesky of the GenEO Schur
+// complement E_hh - E_hg E_gg^-1 E_gh is below kDepTol times their diagonal.
+constexpr double kDepTol = 1e-8;
+
+static void geneo_filter(geneo_ctx *c) {
+  cudaStream_t s = c->stream;
+  const int64_t ns = c->n0_snk, nh = c->n0_geneo;
+  const int64_t off = (ns + kTile - 1) / kTile * kTile;
+  TileBatch fb;
+  fb.layout({off + nh});
+  fb.upload_meta(s);
+  DevBuf<double> tiles;
+  tiles.alloc(tile_elems(fb));
+  tiles_init_padding(fb, tiles.p, s);
+  if (off > ns) k_set_diag<<<1, 64, 0, s>>>(tiles.p, fb.d_toff.p, 0, ns, off);
+  galerkin_tiles(c, coarse_columns(c, off - ns), fb, tiles.p, s);
+  auto get = [&](int64_t r, int64_t q) {  // entry (r, q), r >= q, of the tile storage
+    const int64_t I = r / kTile, J = q / kTile;
+    return ((I * (I + 1) / 2 + J) * kTileElems) + (r % kTile) * kTile + (q % kTile);
+  };
+  std::vector<double> host = tiles.download(s);
+  std::vector<double> diag(nh);
+  for (int64_t h = 0; h < nh; ++h) diag[h] = host[get(off + h, off + h)];
+  if (off > 0) {
+    const int npiv = (int)(off / kTile);
+    DevBuf<int32_t> dn;
+    dn.upload(std::vector<int32_t>{npiv}, s);
+    DevBuf<int64_t> dtoff;
+    dtoff.upload(std::vector<int64_t>{0, (int64_t)fb.nt[0]}, s);
+    DevBuf<double> dinv;
+    dinv.alloc((int64_t)fb.nt[0] * kTileElems);
+    chol_factor(fb, tiles.p, dn.p, npiv, dinv.p, dtoff.p, c->d_err.p, s);
+    check_device_error(c, s);
+    host = tiles.download(s);
+  }
+  std::vector<double> S(nh * nh), Lm(nh * nh, 0.0);
+  for (int64_t i = 0; i < nh; ++i)
+    for (int64_t j = 0; j <= i; ++j) S[i * nh + j] = S[j * nh + i] = host[get(off + i, off + j)];
+  std::vector<int64_t> keep;
+  for (int64_t kk = 0; kk < nh; ++kk) {
+    double piv = S[kk * nh + kk];
+    for (int64_t q : keep) piv -= Lm[kk * nh + q] * Lm[kk * nh + q];
+    if (!(piv >= kDepTol * diag[kk])) continue;
+    const double d = std::sqrt(piv);
+    Lm[kk * nh + kk] = d;
+    for (int64_t r = kk + 1; r < nh; ++r) {
+      double v = S[r * nh + kk];
+      for (int64_t q : keep) v -= Lm[r * nh + q] * Lm[kk * nh + q];
+      Lm[r * nh + kk] = v / d;
+    }
+    keep.push_back(kk);
+  }
+  if ((int64_t)keep.size() == nh) return;
+  std::vector<int64_t> ptr(c->zc_ptr.begin(), c->zc_ptr.begin() + ns + 1);
+  std::vector<int32_t> row(c->zc_row.begin(), c->zc_row.begin() + c->zc_ptr[ns]);
+  std::vector<double> val(c->zc_val.begin(), c->zc_val.begin() + c->zc_ptr[ns]);
+  std::vector<int32_t> gs;
+  std::vector<double> gl;
+  for (int64_t h : keep) {
+    const int64_t a = ns + h;
+    row.insert(row.end(), c->zc_row.begin() + c->zc_ptr[a], c->zc_row.begin() + c->zc_ptr[a + 1]);
+    val.insert(val.end(), c->zc_val.begin() + c->zc_ptr[a], c->zc_val.begin() + c->zc_ptr[a + 1]);
+    ptr.push_back((int64_t)row.size());
+    gs.push_back(c->geneo_sub[h]);
+    gl.push_back(c->geneo_lambda[h]);
+  }
+  c->zc_ptr = ptr;
+  c->zc_row = row;
+  c->zc_val = val;
+  c->geneo_sub = gs;
+  c->geneo_lambda = gl;
+  c->n0_geneo = (int64_t)keep.size();
+  c->n0 = ns + c->n0_geneo;
 }
 
 void setup_all(geneo_ctx *c) {
@@ -468,38 +634,18 @@ void setup_all(geneo_ctx *c) {
     for (size_t k = 0; k < c->snk.sgn.size(); ++k) c->zc_val[k] = (double)c->snk.sgn[k];
     c->n0 = c->n0_snk;
   }
-  if (c->opt.geneo && c->opt.coarse != GENEO_COARSE_NONE) {
-    geneo_eigenvectors(c);  // appends GenEO columns to zc_* and sets n0_geneo
+  if (c->zc_ptr.empty()) c->zc_ptr.push_back(0);
+  if (c->opt.geneo) {
+    geneo_eigenvectors(c);  // appends GenEO candidates to zc_* and sets n0_geneo
+    if (c->n0_geneo > 0) geneo_filter(c);
   }
   if (c->n0 > 0) {
     build_z_csr(c);
-    std::vector<int64_t> pptr;
-    std::vector<int32_t> pcol;
-    coarse_pattern(c, pptr, pcol);
     c->crs.layout({c->n0});
     c->crs.upload_meta(s);
     c->crs_f64.alloc(tile_elems(c->crs));
     tiles_init_padding(c->crs, c->crs_f64.p, s);
-    DevBuf<int64_t> dpp, dctp;
-    DevBuf<int32_t> dpc, dctt;
-    DevBuf<double> dct;
-    dpp.upload(pptr, s);
-    dpc.upload(pcol, s);
-    {
-      std::vector<int64_t> ctp;
-      std::vector<int32_t> ctt;
-      std::vector<double> ctv;
-      coltet_lists(c, ctp, ctt, ctv);
-      dctp.upload(ctp, s);
-      dctt.upload(ctt, s);
-      dct.upload(ctv, s);
-    }
-    k_coltet<<<grid_for(dctt.n, 128), 128, 0, s>>>(dctt.p, dctt.n, c->d_tets.p, c->d_tet_cell.p,
-                                                   c->d_mu.p, c->d_eps.p, c->gamma, c->nx, c->ny,
-                                                   c->h[0], c->h[1], c->h[2], dct.p);
-    k_coarse_E<<<grid_for(c->n0, 8), dim3(32, 8), 0, s>>>(dpp.p, dpc.p, c->n0, dctp.p, dctt.p,
-                                                         dct.p, c->crs_f64.p);
-    GENEO_CHECK_LAUNCH();
+    galerkin_tiles(c, coarse_columns(c, 0), c->crs, c->crs_f64.p, s);
     DevBuf<double> ws;
     ws.alloc(spd_workspace_elems(c->crs));
     spd_invert(c->crs, c->crs_f64.p, ws.p, c->d_err.p, s);

@@ -4,6 +4,30 @@
 
 namespace geneo {
 
+// Sparse columns for a Galerkin product X^T A X, each column assigned to a
+// matrix of a tile batch and a local index in it.
+struct Columns {
+  std::vector<int64_t> ptr{0};
+  std::vector<int32_t> row;       // unknowns
+  std::vector<double> val;
+  std::vector<int32_t> mat, loc;  // target matrix and local index
+  // true: only tetrahedra of subdomain Omega_mat enter (a Neumann matrix,
+  // Sec. 2), else every tetrahedron touching the column
+  bool neumann = false;
+};
+
+// X^T A X summed per tetrahedron (curl-curl part through the curl of each
+// column on the tetrahedron), written into the tile-packed batch.
+void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles, cudaStream_t s);
+// Column-tetrahedron lists and entries (15 doubles: scaled curl of the column
+// on the tetrahedron, its six local values, gamma eps M_T times them).
+void coltet_build(geneo_ctx *c, const Columns &X, std::vector<int64_t> &ct_ptr,
+                  std::vector<int32_t> &ct_tet, DevBuf<int64_t> &dctp, DevBuf<int32_t> &dctt,
+                  DevBuf<double> &dct, cudaStream_t s);
+// per tetrahedron: sqrt(mu^-1 |T|) curl W_e for the six edges (18 doubles)
+// and gamma eps M_T (36 doubles)
+void tet_operators(geneo_ctx *c, DevBuf<double> &tcurl, DevBuf<double> &tmass, cudaStream_t s);
+
 void setup_all(geneo_ctx *c);
 void assemble_rhs(geneo_ctx *c, const double *fslot_host, double *b, cudaStream_t s);
 void check_device_error(geneo_ctx *c, cudaStream_t s);

@@ -129,6 +129,7 @@ __global__ void k_dot_final(const double *__restrict__ part, int np, double *__r
 
 static void dot(geneo_ctx *c, const double *a, const double *b, int64_t n, double *out,
                 cudaStream_t s) {
+  c->launches += 2;
   k_dot_partial<<<kDotBlocks, 256, 0, s>>>(a, b, n, c->partials.p);
   k_dot_final<<<1, 256, 0, s>>>(c->partials.p, kDotBlocks, out);
 }
@@ -165,14 +166,22 @@ __global__ void k_copy(const double *__restrict__ a, double *__restrict__ b, int
 
 void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s) {
   const int64_t n = c->topo.ndofs();
+  c->launches += 1;
   k_spmv<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x, y, n);
   GENEO_CHECK_LAUNCH();
 }
 
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s) {
   const int64_t n = c->topo.ndofs();
+  c->launches += 4;
   k_restrict<<<grid_for(c->loc.vlen, 256), 256, 0, s>>>(c->d_l2g.p, r, c->loc_x.p, c->loc.vlen);
-  symv_batch<double>(c->loc, c->loc_f64.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof) {
+    e0 = c->ev_take();
+    e1 = c->ev_take();
+    c->ev_local.push_back({e0, e1});
+  }
+  symv_batch<double>(c->loc, c->loc_f64.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s, e0, e1);
   k_prolong<<<grid_for(n, 256), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w, n);
   GENEO_CHECK_LAUNCH();
 }
@@ -183,9 +192,16 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
     GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, s));
     return;
   }
+  c->launches += 4;
   k_zt<<<grid_for(c->n0, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
                                             c->crs_x.p, c->n0);
-  symv_batch<double>(c->crs, c->crs_f64.p, c->crs_x.p, c->crs_y.p, c->d_err.p, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof) {
+    e0 = c->ev_take();
+    e1 = c->ev_take();
+    c->ev_coarse.push_back({e0, e1});
+  }
+  symv_batch<double>(c->crs, c->crs_f64.p, c->crs_x.p, c->crs_y.p, c->d_err.p, s, e0, e1);
   k_z<<<grid_for(n, 256), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p, c->crs_y.p,
                                        y, n);
   GENEO_CHECK_LAUNCH();
@@ -197,6 +213,7 @@ void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t
     local_solve(c, r, z, s);
     return;
   }
+  c->launches += 2;
   coarse_solve(c, r, c->v_y0.p, s);
   k_residual<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
                                                   c->v_y0.p, r, c->v_s.p, n);
@@ -215,6 +232,7 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
   double *hs = c->h_scal;
   const unsigned g = grid_for(n, 256);
   GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  c->launches += 2;
   k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
   dot(c, b, b, n, sc + 4, s);
   apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
@@ -232,6 +250,7 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
     for (it = 1; it <= maxit; ++it) {
       spmv(c, c->p_p.p, c->p_q.p, s);
       dot(c, c->p_p.p, c->p_q.p, n, sc + 1, s);
+      c->launches += 1;
       k_update_xr<<<g, 256, 0, s>>>(sc, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
       dot(c, c->p_r.p, c->p_r.p, n, sc + 2, s);
       GENEO_CUDA(cudaMemcpyAsync(hs, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -247,6 +266,7 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
       }
       apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
       dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s);
+      c->launches += 2;
       k_update_p<<<g, 256, 0, s>>>(sc, c->p_z.p, c->p_p.p, n);
       k_shift_rz<<<1, 1, 0, s>>>(sc);
       GENEO_CHECK_LAUNCH();
