@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark: PCG time-to-1e-8 with the two-level GenEO preconditioner.
+
+Workload: the 32^3 unit cube with a through-hole (central 8x8x32 column
+removed), mu^-1 log-uniform in [1, 1e3] inside four random 2x2 channels,
+eps = 1, gamma = 1e-4, f uniform in [-1, 1]^3 per edge (seeded), 4x4x4 = 64
+subdomains, overlap 2, GenEO threshold lambda > 10 (tau = 0.1, reciprocal).
+
+A step is one preconditioned CG solve to ||r|| / ||b|| <= 1e-8 from x0 = 0
+on the GPU, the right-hand side resident in HBM (the local factors, 10-22 GB,
+exceed the 129 MB L2, so no flush is needed).  Set-up (assembly, local
+inverses, GenEO eigensolves, coarse factor) is timed separately.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; each rank solves its own
+replica of the problem (replicas only: the method is not sharded here).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-1e-8 (s)"
+TOL = 1e-8
+WORKLOAD = "cube32_hole_channels"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 FMA rate of GB300: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2070 MHz
+# (the recipe's 1.25 TFLOP/s nominal figure at the maximum SM clock)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = str(index)
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9 or f[0] != self.index:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle, bounded sample (baseline only)
+
+class OracleSample:
+    """One preconditioned CG iteration of the CPU oracle on the same
+    workload, with the local solves measured on `nsample` of the 64
+    subdomains and scaled to all of them, the coarse solve on the split
+    near-kernel columns (the GenEO columns add about 1% to n0), the global
+    SpMVs and the vector updates.  Set-up happens once in the constructor."""
+
+    def __init__(self, nsample=4, seed=0):
+        import numpy as np
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spla
+        import workloads as W
+        from oracle.mesh import build_mesh
+        from oracle.fem import assemble_A
+        from oracle.dd import decompose
+        from oracle.coarse import snk_columns, assemble_Z, coarse_matrix
+        w = getattr(W, WORKLOAD)()
+        m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+        self.A = assemble_A(m, w)
+        dec = decompose(m, w.parts, w.overlap)
+        self.nsub, self.nsample = dec.nsub, nsample
+        self.Z = assemble_Z(self.A.shape[0], snk_columns(m, dec))
+        self.Elu = spla.splu(sp.csc_matrix(coarse_matrix(m, w, self.Z)))
+        rng = np.random.default_rng(seed)
+        pick = sorted(rng.choice(dec.nsub, size=nsample, replace=False).tolist())
+        self.facs = [(dec.N[i], spla.splu(sp.csc_matrix(self.A[dec.N[i]][:, dec.N[i]])))
+                     for i in pick]
+        self.r = rng.standard_normal(self.A.shape[0])
+        self.info = {"sample": f"one PCG iteration of the oracle on {WORKLOAD} "
+                               f"(n={self.A.shape[0]}), local sparse-LU solves timed on "
+                               f"{nsample} of {dec.nsub} subdomains and scaled, coarse sparse-LU "
+                               f"solves on the {self.Z.shape[1]} split near-kernel columns",
+                     "cores": os.cpu_count()}
+
+    def step(self):
+        import numpy as np
+        A, Z, Elu, r = self.A, self.Z, self.Elu, self.r
+        t0 = time.perf_counter()
+        y0 = Z @ Elu.solve(Z.T @ r)
+        s = r - A @ y0
+        tl = time.perf_counter()
+        wv = np.zeros_like(r)
+        for Ni, f in self.facs:
+            wv[Ni] += f.solve(s[Ni])
+        t_loc = (time.perf_counter() - tl) * self.nsub / self.nsample
+        tc = time.perf_counter()
+        z = y0 + wv - Z @ Elu.solve(Z.T @ (A @ wv))
+        q = A @ z
+        alpha = (r @ z) / (z @ q)
+        rr = r - alpha * q
+        _ = rr @ rr
+        return (tl - t0) + t_loc + (time.perf_counter() - tc)
+
+
+def oracle_iterations(default):
+    path = os.path.join(ROOT, "tests", "golden", "cube32_reference.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return int(json.load(f)["pcg_iters"]), "oracle PCG iteration count (tests/golden)"
+    return default, "iteration count of the GPU run (same method)"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    o = OracleSample()
+    for _ in range(args.warmup):
+        o.step()
+    per_iter = statistics.median([o.step() for _ in range(max(1, args.steps))])
+    info = o.info
+    iters, src = oracle_iterations(40)
+    value = per_iter * iters
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tol": TOL, "iterations": iters,
+                       "iterations_source": src},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": info["cores"],
+                             "kind": "oracle", "sample": info["sample"]},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import numpy as np
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import workloads as W
+    import paper_2311_18783_gb300 as pkg
+    w = getattr(W, WORKLOAD)()
+    prec = pkg.PREC_FP32 if args.precision == "fp32" else pkg.PREC_FP64
+    t0 = time.perf_counter()
+    s = pkg.Solver.from_workload(w, precision=prec)
+    setup_s = time.perf_counter() - t0
+    n = s.n
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    s.assemble_rhs(w.f_slot[0], b)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        info = s.solve(b, x, tol=TOL, maxit=1000)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    s.profile_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        info = s.solve(b, x, tol=TOL, maxit=1000)
+        iters.append(info["iters"])
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof = s.profile_read()
+    s.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    clk = clocks.stop()
+    # end to end through the host-buffer entry point (copies inside)
+    bh = b.cpu().pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    s.solve_host(bh, tol=TOL, maxit=1000, out=xh)
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        s.solve_host(bh, tol=TOL, maxit=1000, out=xh)
+        te.append(time.perf_counter() - t1)
+    e2e_s = statistics.mean(te)
+    # roofline of the dominant kernel: the local-factor SYMV
+    peaks, peak_src = load_peaks()
+    launches = max(1, prof["local_symv_launches"])
+    t_launch = prof["local_symv_ms"] / launches * 1e-3
+    if prec == pkg.PREC_FP64:
+        achieved = prof["local_symv_flops"] / t_launch / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        roof = {"kernel": "k_symv_strips<double> (local A_i^-1 apply)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "FP64 FMA rate derived from unit counts and the 2070 MHz clock",
+                "traffic": None, "algorithmic_flops_per_launch": prof["local_symv_flops"],
+                "launch_ms": t_launch * 1e3}
+    else:
+        achieved = prof["local_symv_bytes"] / t_launch / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"kernel": "k_symv_strips<float> (local split factors)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"hbm_gbs of {peak_src}", "traffic": None,
+                "algorithmic_bytes_per_launch": prof["local_symv_bytes"],
+                "launch_ms": t_launch * 1e3}
+    applies_per_s = (sum(iters) + len(iters)) / (ms * args.steps / 1e3)
+    line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == pkg.PREC_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nsub": s.sizes["nsub"],
+                       "n0": s.sizes["n0"], "n0_geneo": s.sizes["n0_geneo"], "tol": TOL,
+                       "pcg_iters": iters[-1], "precision": args.precision,
+                       "l2": "inputs larger than L2 (local factors "
+                             f"{s.sizes['local_factor_bytes'] / 1e9:.1f} GB)",
+                       "setup_s": setup_s},
+            "applies_per_s": applies_per_s,
+            "roofline": roof, "clocks": clk, "gpu_launches": prof["launches"],
+            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8,
+                    "d2h_bytes_per_step": n * 8}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o = OracleSample()
+        o.step()
+        per_iter, oinfo = statistics.median([o.step() for _ in range(2)]), o.info
+        oit, src = oracle_iterations(iters[-1])
+        line["cpu_baseline"] = {"value": per_iter * oit, "unit": "s", "cores": oinfo["cores"],
+                                "kind": "oracle", "sample": oinfo["sample"] + f"; x {oit} "
+                                f"iterations ({src})"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
