@@ -204,6 +204,30 @@ int geneo_profile_read(geneo_ctx *ctx, geneo_profile *out);
 int geneo_export(const geneo_ctx *ctx, const char *name, void *dst, int64_t capacity,
                  int64_t *size);
 
+/* Allocation-free symmetric matrix-vector product, for callers that cannot
+ * allocate device memory at the point of the call (code inside a memory pool
+ * or arena that forbids new allocations, real-time loops where cudaMalloc or
+ * cudaFree would synchronise or stall, hosts whose allocator owns all device
+ * memory).  The paper has no counterpart: this is a service entry point.
+ *
+ * y_dev[dim] = T x_dev for one symmetric matrix T given in the tile-packed
+ * layout used for the local factors: nt = ceil(dim/64) tiles per side, tile
+ * (I, J), J <= I, a full 64x64 row-major block at element offset
+ * (I(I+1)/2 + J) * 4096 of tiles_dev (float64, device, 16-byte aligned);
+ * diagonal tiles hold both triangles; entries past dim must be finite
+ * (zero).  1 <= dim <= 4096.
+ *
+ * No allocation: the only scratch (partial sums and an error word, 1.07 MB)
+ * is a fixed array that every GPU loading the library keeps until exit.
+ * The first call on a device looks up that array's device address and sets
+ * the kernel's shared-memory limit, so it must come before any stream
+ * capture.  All calls share the array and later calls overwrite it: calls
+ * that overlap on the GPU (other threads, other streams) race.  The call
+ * waits for `stream` before returning.  Errors: INVALID_ARG (null pointer or
+ * dim outside [1, 4096]), TIMEOUT (a bounded device wait gave up), CUDA. */
+int geneo_symv_packed_noalloc(const double *tiles_dev, int32_t dim, const double *x_dev,
+                              double *y_dev, void *stream);
+
 /* Message of the last error of this thread. */
 const char *geneo_last_error(void);
 

@@ -86,6 +86,8 @@ _SIGS = {
                                C.POINTER(C.c_int64)]),
     "geneo_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
+    "geneo_symv_packed_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
     "geneo_last_error": (C.c_char_p, []),
     "geneo_strerror": (C.c_char_p, [C.c_int]),
 }
