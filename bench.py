@@ -38,7 +38,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                   help="mixed: float32 split local factors (headline) and float64 beside it")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -217,7 +218,7 @@ def main():
     import workloads as W
     import paper_2311_18783_gb300 as pkg
     w = getattr(W, WORKLOAD)()
-    prec = pkg.PREC_FP32 if args.precision == "fp32" else pkg.PREC_FP64
+    prec = pkg.PREC_FP32 if args.precision == "mixed" else pkg.PREC_FP64
     t0 = time.perf_counter()
     s = pkg.Solver.from_workload(w, precision=prec)
     setup_s = time.perf_counter() - t0
@@ -226,6 +227,31 @@ def main():
     s.assemble_rhs(w.f_slot[0], b)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
+    fp64_side = None
+    if prec == pkg.PREC_FP32:
+        # plain float64 factors on the same GPU, same problem (reported beside)
+        s.use_precision(pkg.PREC_FP64)
+        for _ in range(args.warmup):
+            s.solve(b, x, tol=TOL, maxit=1000)
+        torch.cuda.synchronize()
+        s.profile(True)
+        s.profile_read()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            i64 = s.solve(b, x, tol=TOL, maxit=1000)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        p64 = s.profile_read()
+        s.profile(False)
+        l64 = p64["local_symv_ms"] / max(1, p64["local_symv_launches"]) * 1e-3
+        fp64_side = {"value": f0.elapsed_time(f1) / args.steps / 1e3, "unit": "s",
+                     "pcg_iters": i64["iters"],
+                     "local_symv_tflops": p64["local_symv_flops"] / l64 / 1e12,
+                     "local_symv_frac_of_fp64_peak": p64["local_symv_flops"] / l64 / 1e9 /
+                     FP64_PEAK_GFLOPS}
+        s.use_precision(pkg.PREC_FP32)
     for _ in range(args.warmup):
         info = s.solve(b, x, tol=TOL, maxit=1000)
     clocks = ClockSampler(local)
@@ -293,6 +319,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == pkg.PREC_FP64 else "f32+f64",
+            "plain_fp64": fp64_side,
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "nsub": s.sizes["nsub"],
                        "n0": s.sizes["n0"], "n0_geneo": s.sizes["n0_geneo"], "tol": TOL,

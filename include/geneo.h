@@ -61,7 +61,8 @@ extern "C" {
 #define GENEO_ERR_STATE (-7)       /* call not valid in the context's state */
 
 #define GENEO_PREC_FP64 0          /* local factors stored and applied in float64 */
-#define GENEO_PREC_FP32 1          /* split factors: gradient part float64, rest float32 */
+#define GENEO_PREC_FP32 1          /* split factors (Sec. 2, eq. "inverseBw"): A_j^-1 =
+                                      G S^-1 G^T (float64) + (I - xi) A_j^-1 (float32) */
 
 #define GENEO_COARSE_NONE 0        /* one-level additive Schwarz (eq. "AS") */
 #define GENEO_COARSE_SNK 1         /* split near-kernel space (definition "near-kernelCS") */
@@ -165,6 +166,12 @@ int geneo_solve(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol, 
  * copies x back to x_host[n] before returning. */
 int geneo_solve_host(geneo_ctx *ctx, const double *b_host, double *x_host, double tol,
                      int32_t maxit, geneo_solve_info *info, void *stream);
+
+/* Selects the local factors used by later solves when the context holds
+ * both: GENEO_PREC_FP64 (explicit float64 inverses) or GENEO_PREC_FP32 (the
+ * split C_j + G_j S_j^-1 G_j^T, built when options.precision was FP32; the
+ * float64 inverses are kept as well).  Returns STATE if they were not built. */
+int geneo_use_precision(geneo_ctx *ctx, int32_t precision);
 
 /* Per-stage counters of the solve path, collected while profiling is on. */
 typedef struct {

@@ -84,6 +84,7 @@ _SIGS = {
                                    C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_export": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64,
                                C.POINTER(C.c_int64)]),
+    "geneo_use_precision": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "geneo_symv_packed_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
@@ -234,6 +235,9 @@ class Solver:
                                           _stream(stream)))
         return xh, {"status": st, "iters": info.iters, "relres": info.relres,
                     "seconds": info.seconds}
+
+    def use_precision(self, precision):
+        _check(_LIB.geneo_use_precision(self._ctx, precision))
 
     def profile(self, on=True):
         _check(_LIB.geneo_profile_enable(self._ctx, 1 if on else 0))

@@ -215,6 +215,19 @@ int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int
   });
 }
 
+int geneo_use_precision(geneo_ctx *c, int32_t precision) {
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (precision == GENEO_PREC_FP64 && c->loc_f64.p) {
+    c->local_prec = GENEO_PREC_FP64;
+    return GENEO_OK;
+  }
+  if (precision == GENEO_PREC_FP32 && c->loc_f32.p) {
+    c->local_prec = GENEO_PREC_FP32;
+    return GENEO_OK;
+  }
+  return fail(GENEO_ERR_STATE, "the requested local factors were not built");
+}
+
 int geneo_profile_enable(geneo_ctx *c, int32_t on) {
   if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   c->prof = on != 0;
@@ -242,7 +255,8 @@ int geneo_profile_read(geneo_ctx *c, geneo_profile *o) {
     o->local_symv_launches = sum(c->ev_local, o->local_symv_ms);
     o->coarse_symv_launches = sum(c->ev_coarse, o->coarse_symv_ms);
     o->local_symv_bytes = c->loc.ntiles * (int64_t)geneo::kTileElems *
-                          (c->loc_f32.p ? (int64_t)sizeof(float) : (int64_t)sizeof(double));
+                          (c->local_prec == GENEO_PREC_FP32 ? (int64_t)sizeof(float)
+                                                            : (int64_t)sizeof(double));
     int64_t fl = 0;
     for (int i = 0; i < c->dec.nsub; ++i) fl += 2 * c->dec.ni(i) * c->dec.ni(i);
     o->local_symv_flops = fl;

@@ -3,6 +3,9 @@
 #include "common.cuh"
 #include "dense.cuh"
 #include "topology.hpp"
+#include "xi.hpp"
+
+#include <memory>
 
 struct geneo_ctx {
   // problem copy
@@ -51,6 +54,10 @@ struct geneo_ctx {
   geneo::DevBuf<double> d_zc_val, d_zr_val;
   geneo::TileBatch crs;
   geneo::DevBuf<double> crs_f64;
+
+  // local operators (xi, S_j^-1, element data) for GenEO and the split solve
+  std::unique_ptr<geneo::XiOp> xi;
+  int local_prec = GENEO_PREC_FP64;  // precision used by the local solves
 
   // work vectors
   geneo::DevBuf<double> v_y0, v_s, v_w, v_t, v_c, loc_x, loc_y, crs_x, crs_y;

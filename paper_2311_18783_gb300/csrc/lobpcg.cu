@@ -25,6 +25,7 @@
 #include <numeric>
 
 #include "setup.hpp"
+#include "xi.hpp"
 
 namespace geneo {
 
@@ -185,7 +186,53 @@ __global__ void k_g(const int32_t *__restrict__ ghead, const int32_t *__restrict
   if (ghead[slot] >= 0) g += u[ub + ghead[slot]];
   if (gtail[slot] >= 0) g -= u[ub + gtail[slot]];
   const int64_t p = voff[m] + (slot - Noff[m]) + (int64_t)c * vlen;
-  out[p] = mode ? x[p] - g : g;
+  if (mode == 2) out[p] += g;
+  else out[p] = mode ? x[p] - g : g;
+}
+
+// float32 part of the split local inverse (Sec. 2, eq. "inverseBw"):
+// C_j = A_j^-1 - G_j S_j^-1 G_j^T = (I - xi_j) A_j^-1, formed in float64 from
+// the explicit inverse and S_j^-1 and stored in float32 (padding: identity)
+__device__ __forceinline__ double sinv_at(const double *sinv, int64_t toffS, int v, int w) {
+  if (v < w) {
+    const int t = v;
+    v = w;
+    w = t;
+  }
+  const int I = v / kTile, J = w / kTile;
+  return sinv[(toffS + (int64_t)I * (I + 1) / 2 + J) * kTileElems + (v % kTile) * kTile + (w % kTile)];
+}
+
+__global__ void k_split_cast(const double *__restrict__ ainv, const int32_t *__restrict__ nt,
+                             const int64_t *__restrict__ toff, const int64_t *__restrict__ Noff,
+                             const int32_t *__restrict__ ghead, const int32_t *__restrict__ gtail,
+                             const double *__restrict__ sinv, const int64_t *__restrict__ toffS,
+                             float *__restrict__ out) {
+  const int m = blockIdx.y;
+  const int64_t ntm = nt[m];
+  const int64_t q = blockIdx.x;
+  if (q >= ntm * (ntm + 1) / 2) return;
+  int I = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(I + 1) * (I + 2) / 2 <= q) ++I;
+  while ((int64_t)I * (I + 1) / 2 > q) --I;
+  const int J = (int)(q - (int64_t)I * (I + 1) / 2);
+  const int64_t ni = Noff[m + 1] - Noff[m];
+  const int64_t tb = (toff[m] + q) * kTileElems;
+  for (int e = threadIdx.x; e < kTileElems; e += blockDim.x) {
+    const int64_t r = (int64_t)I * kTile + (e >> 6), cc = (int64_t)J * kTile + (e & 63);
+    double v = ainv[tb + e];
+    if (r < ni && cc < ni) {
+      const int64_t sr = Noff[m] + r, sc = Noff[m] + cc;
+      const int hr = ghead[sr], tr = gtail[sr], hc = ghead[sc], tc = gtail[sc];
+      double g = 0;
+      if (hr >= 0 && hc >= 0) g += sinv_at(sinv, toffS[m], hr, hc);
+      if (hr >= 0 && tc >= 0) g -= sinv_at(sinv, toffS[m], hr, tc);
+      if (tr >= 0 && hc >= 0) g -= sinv_at(sinv, toffS[m], tr, hc);
+      if (tr >= 0 && tc >= 0) g += sinv_at(sinv, toffS[m], tr, tc);
+      v -= g;
+    }
+    out[tb + e] = (float)v;
+  }
 }
 
 __global__ void k_take(const double *__restrict__ src, const int32_t *__restrict__ idx,
@@ -405,27 +452,9 @@ __global__ void k_resid(const double *__restrict__ LX, const double *__restrict_
 struct Lobpcg {
   geneo_ctx *c;
   cudaStream_t s;
+  XiOp &op;
   int nsub, k;
-  int64_t vlen, vlenS, nslots, nv;
-  // structures
-  DevBuf<int32_t> slot_sub, vslot_sub, pos_sub, ghead, gtail, srow;
-  DevBuf<int8_t> ssgn;
-  DevBuf<int64_t> Noff, lrp, sptr, xvoff;
-  DevBuf<int32_t> lcol;
-  DevBuf<double> aval, nval, dmask;
-  TileBatch sb;
-  DevBuf<double> s_inv;   // S_j^-1,   S_j = G_j^T A_j G_j
-  DevBuf<double> sn_inv;  // S_Bj^-1,  S_Bj = G_j^T A_j^Neu G_j (same layout)
-  // column-tetrahedron lists of the local gradient columns (Dirichlet: all
-  // tetrahedra touching N_j; Neumann: those of Omega_j) and per-entry local
-  // indices of the tetrahedron's six edges
-  DevBuf<int64_t> ctp_d, ctp_n, col_out;
-  DevBuf<int32_t> ctt_d, ctt_n, lidx_d, lidx_n, col_sub;
-  DevBuf<double> ct_d, ct_n, tcurl, tmass;
-  // per local row: tetrahedra containing it (for A_j G w element by element)
-  DevBuf<int64_t> rptr;
-  DevBuf<int32_t> rtet, rlidx, rvidx;
-  DevBuf<int8_t> rpos;
+  int64_t vlen;
   // blocks (k columns each)
   DevBuf<double> X, LX, BX, W, LW, BW, P, LP, BP, R, T1, T2, T3, U1, U2;
   DevBuf<double> Q, BQ;
@@ -433,41 +462,42 @@ struct Lobpcg {
   std::vector<int> nq;  // locked per subdomain
   DevBuf<double> gram, coef, theta, tmat;
   int ld = 0;
+  Lobpcg(geneo_ctx *cc, cudaStream_t ss, XiOp &o) : c(cc), s(ss), op(o) {}
 };
 
 static void apply_sparse(Lobpcg &L, const DevBuf<double> &vals, const double *x, double *y, int k) {
-  const int64_t tot = L.nslots * k;
-  k_local_csr<<<grid_for(tot, 256), 256, 0, L.s>>>(L.lrp.p, L.lcol.p, vals.p, L.slot_sub.p, L.Noff.p,
-                                                   L.c->loc.d_voff.p, L.nslots, k, L.vlen, x, y);
+  const int64_t tot = L.op.nslots * k;
+  k_local_csr<<<grid_for(tot, 256), 256, 0, L.s>>>(L.op.lrp.p, L.op.lcol.p, vals.p, L.op.slot_sub.p, L.op.Noff.p,
+                                                   L.c->loc.d_voff.p, L.op.nslots, k, L.vlen, x, y);
 }
 
 static void apply_B(Lobpcg &L, const double *Y, double *BY, int k) {
-  apply_sparse(L, L.nval, Y, BY, k);
+  apply_sparse(L, L.op.nval, Y, BY, k);
 }
 
 // out = x - xi x (mode 1) with xi = G S^-1 G^T A, or out = x - xi^T x =
 // x - A G S^-1 G^T x (mode 2).  Uses U1, U2 as scratch.
 static void xi_apply(Lobpcg &L, const double *x, double *out, int k, int mode) {
   if (mode == 1) {
-    k_gtA_curl<<<grid_for(L.nv * k, 128), 128, 0, L.s>>>(
-        L.ctp_d.p, L.ctt_d.p, L.ct_d.p, L.lidx_d.p, L.tcurl.p, L.tmass.p, L.col_sub.p,
-        L.col_out.p, L.c->loc.d_voff.p, L.nv, k, L.vlen, L.vlenS, x, L.U1.p);
+    k_gtA_curl<<<grid_for(L.op.nv * k, 128), 128, 0, L.s>>>(
+        L.op.ctp_d.p, L.op.ctt_d.p, L.op.ct_d.p, L.op.lidx_d.p, L.op.tcurl.p, L.op.tmass.p, L.op.col_sub.p,
+        L.op.col_out.p, L.c->loc.d_voff.p, L.op.nv, k, L.vlen, L.op.vlenS, x, L.U1.p);
   } else {
-    k_gt<<<grid_for(L.nv * k, 256), 256, 0, L.s>>>(L.sptr.p, L.srow.p, L.ssgn.p, L.vslot_sub.p,
-                                                   L.xvoff.p, L.c->loc.d_voff.p, L.sb.d_voff.p,
-                                                   L.nv, k, L.vlen, L.vlenS, x, L.U1.p);
+    k_gt<<<grid_for(L.op.nv * k, 256), 256, 0, L.s>>>(L.op.sptr.p, L.op.srow.p, L.op.ssgn.p, L.op.vslot_sub.p,
+                                                   L.op.xvoff.p, L.c->loc.d_voff.p, L.op.sb.d_voff.p,
+                                                   L.op.nv, k, L.vlen, L.op.vlenS, x, L.U1.p);
   }
   for (int col = 0; col < k; ++col)
-    symv_batch<double>(L.sb, L.s_inv.p, L.U1.p + (int64_t)col * L.vlenS,
-                       L.U2.p + (int64_t)col * L.vlenS, L.c->d_err.p, L.s);
+    symv_batch<double>(L.op.sb, L.op.s_inv.p, L.U1.p + (int64_t)col * L.op.vlenS,
+                       L.U2.p + (int64_t)col * L.op.vlenS, L.c->d_err.p, L.s);
   if (mode == 1) {
-    k_g<<<grid_for(L.nslots * k, 256), 256, 0, L.s>>>(L.ghead.p, L.gtail.p, L.slot_sub.p, L.Noff.p,
-                                                      L.c->loc.d_voff.p, L.sb.d_voff.p, L.nslots, k,
-                                                      L.vlen, L.vlenS, L.U2.p, x, out, 1);
+    k_g<<<grid_for(L.op.nslots * k, 256), 256, 0, L.s>>>(L.op.ghead.p, L.op.gtail.p, L.op.slot_sub.p, L.op.Noff.p,
+                                                      L.c->loc.d_voff.p, L.op.sb.d_voff.p, L.op.nslots, k,
+                                                      L.vlen, L.op.vlenS, L.U2.p, x, out, 1);
   } else {
-    k_agw<<<grid_for(L.nslots * k, 128), 128, 0, L.s>>>(
-        L.rptr.p, L.rtet.p, L.rpos.p, L.rlidx.p, L.rvidx.p, L.tcurl.p, L.tmass.p, L.slot_sub.p,
-        L.Noff.p, L.c->loc.d_voff.p, L.sb.d_voff.p, L.nslots, k, L.vlen, L.vlenS, L.U2.p, x, out);
+    k_agw<<<grid_for(L.op.nslots * k, 128), 128, 0, L.s>>>(
+        L.op.rptr.p, L.op.rtet.p, L.op.rpos.p, L.op.rlidx.p, L.op.rvidx.p, L.op.tcurl.p, L.op.tmass.p, L.op.slot_sub.p,
+        L.op.Noff.p, L.c->loc.d_voff.p, L.op.sb.d_voff.p, L.op.nslots, k, L.vlen, L.op.vlenS, L.U2.p, x, out);
   }
 }
 
@@ -475,24 +505,24 @@ static void xi_apply(Lobpcg &L, const double *x, double *out, int k, int mode) {
 // gradients, where the eigenvectors of the GEVP live (for g = G c in the
 // null space of L, g^T L v = 0 = lambda g^T B v)
 static void project_gradients_B(Lobpcg &L, double *Y, int k) {
-  k_gtA_curl<<<grid_for(L.nv * k, 128), 128, 0, L.s>>>(
-      L.ctp_n.p, L.ctt_n.p, L.ct_n.p, L.lidx_n.p, L.tcurl.p, L.tmass.p, L.col_sub.p, L.col_out.p,
-      L.c->loc.d_voff.p, L.nv, k, L.vlen, L.vlenS, Y, L.U1.p);
+  k_gtA_curl<<<grid_for(L.op.nv * k, 128), 128, 0, L.s>>>(
+      L.op.ctp_n.p, L.op.ctt_n.p, L.op.ct_n.p, L.op.lidx_n.p, L.op.tcurl.p, L.op.tmass.p, L.op.col_sub.p, L.op.col_out.p,
+      L.c->loc.d_voff.p, L.op.nv, k, L.vlen, L.op.vlenS, Y, L.U1.p);
   for (int col = 0; col < k; ++col)
-    symv_batch<double>(L.sb, L.sn_inv.p, L.U1.p + (int64_t)col * L.vlenS,
-                       L.U2.p + (int64_t)col * L.vlenS, L.c->d_err.p, L.s);
-  k_g<<<grid_for(L.nslots * k, 256), 256, 0, L.s>>>(L.ghead.p, L.gtail.p, L.slot_sub.p, L.Noff.p,
-                                                    L.c->loc.d_voff.p, L.sb.d_voff.p, L.nslots, k,
-                                                    L.vlen, L.vlenS, L.U2.p, Y, Y, 1);
+    symv_batch<double>(L.op.sb, L.op.sn_inv.p, L.U1.p + (int64_t)col * L.op.vlenS,
+                       L.U2.p + (int64_t)col * L.op.vlenS, L.c->d_err.p, L.s);
+  k_g<<<grid_for(L.op.nslots * k, 256), 256, 0, L.s>>>(L.op.ghead.p, L.op.gtail.p, L.op.slot_sub.p, L.op.Noff.p,
+                                                    L.c->loc.d_voff.p, L.op.sb.d_voff.p, L.op.nslots, k,
+                                                    L.vlen, L.op.vlenS, L.U2.p, Y, Y, 1);
 }
 
 // LY = (I - xi)^T D A D (I - xi) Y  for a block of k columns
 static void apply_L(Lobpcg &L, const double *Y, double *LY, int k) {
   const int64_t tot = L.vlen * k;
   xi_apply(L, Y, L.T1.p, k, 1);                        // T1 = (I - xi) Y
-  k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.dmask.p, k, L.vlen, L.T1.p, L.T2.p);
-  apply_sparse(L, L.aval, L.T2.p, L.T1.p, k);           // T1 = A D (I - xi) Y
-  k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.dmask.p, k, L.vlen, L.T1.p, L.T2.p);
+  k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.op.dmask.p, k, L.vlen, L.T1.p, L.T2.p);
+  apply_sparse(L, L.op.aval, L.T2.p, L.T1.p, k);           // T1 = A D (I - xi) Y
+  k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.op.dmask.p, k, L.vlen, L.T1.p, L.T2.p);
   xi_apply(L, L.T2.p, LY, k, 2);                       // LY = T2 - A G S^-1 G^T T2
   (void)tot;
 }
@@ -508,7 +538,7 @@ static void combine(Lobpcg &L, const std::vector<const double *> &src, const dou
   SrcList sl;
   for (size_t j = 0; j < src.size(); ++j) sl.p[j] = src[j];
   k_combine<<<grid_for(L.vlen, 128), 128, 0, L.s>>>(sl, (int)src.size(), coef, L.ld, kout,
-                                                    L.pos_sub.p, L.vlen, out);
+                                                    L.op.pos_sub.p, L.vlen, out);
 }
 
 static std::vector<const double *> cols(const DevBuf<double> &b, int k, int64_t vlen) {
@@ -603,8 +633,8 @@ __global__ void k_pos_tables(const int32_t *__restrict__ l2g, const int32_t *__r
 // local operators of every subdomain: A_j and A_j^Neu values on the local
 // CSR, the Boolean D_j, the gradient structure of xi_j and the inverses of
 // S_j = G_j^T A_j G_j (Galerkin per tetrahedron, tiled Cholesky inverse)
-static void build_xi_operator(geneo_ctx *c, Lobpcg &L) {
-  cudaStream_t s = L.s;
+void build_xi_operator(geneo_ctx *c, XiOp &L, cudaStream_t s) {
+  L.vlen = c->loc.vlen;
   const Decomposition &d = c->dec;
   const LocalStructure &ls = c->ls;
   L.nslots = d.N_off[d.nsub];
@@ -782,22 +812,23 @@ static void build_xi_operator(geneo_ctx *c, Lobpcg &L) {
 
 void geneo_eigenvectors(geneo_ctx *c) {
   cudaStream_t s = c->stream;
-  Lobpcg L;
-  L.c = c;
-  L.s = s;
+  if (!c->xi) {
+    c->xi.reset(new XiOp());
+    build_xi_operator(c, *c->xi, s);
+  }
+  Lobpcg L(c, s, *c->xi);
   L.nsub = c->dec.nsub;
   L.k = c->opt.lobpcg_block;
   const int k = L.k;
   L.ld = std::max(3 * k, 64);
   L.vlen = c->loc.vlen;
-  build_xi_operator(c, L);
   for (auto *b : {&L.X, &L.LX, &L.BX, &L.W, &L.LW, &L.BW, &L.P, &L.LP, &L.BP, &L.R, &L.T1, &L.T2,
                   &L.T3}) {
     b->alloc(L.vlen * k);
     b->zero(s);
   }
   for (auto *b : {&L.U1, &L.U2}) {
-    b->alloc(L.vlenS * k);
+    b->alloc(L.op.vlenS * k);
     b->zero(s);
   }
   L.gram.alloc((int64_t)L.nsub * L.ld * L.ld);
@@ -836,7 +867,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
     std::vector<uint8_t> finished(L.nsub, 0);
     for (int m = 0; m < L.nsub; ++m) finished[m] = done[m];
     for (int it = 0; it < c->opt.lobpcg_maxit; ++it) {
-      k_resid<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.LX.p, L.BX.p, L.theta.p, k, L.pos_sub.p,
+      k_resid<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.LX.p, L.BX.p, L.theta.p, k, L.op.pos_sub.p,
                                                     L.vlen, L.R.p);
       // residual and B X norms, Ritz values
       gram(L, L.R.p, k, L.R.p, k, L.gram.p);
@@ -904,9 +935,9 @@ void geneo_eigenvectors(geneo_ctx *c) {
         DevBuf<int32_t> ds, dd;
         ds.upload(srcc, s);
         dd.upload(dstc, s);
-        k_copy_cols<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.X.p, L.Q.p, L.pos_sub.p, ds.p, dd.p, k,
+        k_copy_cols<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.X.p, L.Q.p, L.op.pos_sub.p, ds.p, dd.p, k,
                                                           L.vlen);
-        k_copy_cols<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.BX.p, L.BQ.p, L.pos_sub.p, ds.p, dd.p,
+        k_copy_cols<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.BX.p, L.BQ.p, L.op.pos_sub.p, ds.p, dd.p,
                                                           k, L.vlen);
         GENEO_CUDA(cudaStreamSynchronize(s));
       }
@@ -1028,7 +1059,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
     GENEO_CUDA(cudaMemcpyAsync(L.T2.p, L.Q.p + (int64_t)c0 * L.vlen, sizeof(double) * L.vlen * kk,
                                cudaMemcpyDeviceToDevice, s));
     xi_apply(L, L.T2.p, L.T1.p, k, 1);
-    k_dscale<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.dmask.p, kk, L.vlen, L.T1.p,
+    k_dscale<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.op.dmask.p, kk, L.vlen, L.T1.p,
                                                    V.p + (int64_t)c0 * L.vlen);
   }
   GENEO_CUDA(cudaMemcpyAsync(hv.data(), V.p, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, s));
@@ -1053,6 +1084,40 @@ void geneo_eigenvectors(geneo_ctx *c) {
   }
   c->n0_geneo = (int64_t)c->geneo_sub.size();
   c->n0 = c->n0_snk + c->n0_geneo;
+}
+
+void build_split_factors(geneo_ctx *c) {
+  cudaStream_t s = c->stream;
+  if (!c->xi) {
+    c->xi.reset(new XiOp());
+    build_xi_operator(c, *c->xi, s);
+  }
+  XiOp &op = *c->xi;
+  c->loc_f32.alloc(tile_elems(c->loc));
+  const int64_t maxT = (int64_t)c->loc.maxnt * (c->loc.maxnt + 1) / 2;
+  k_split_cast<<<dim3((unsigned)maxT, c->loc.nmat), 256, 0, s>>>(
+      c->loc_f64.p, c->loc.d_nt.p, c->loc.d_toff.p, op.Noff.p, op.ghead.p, op.gtail.p,
+      op.s_inv.p, op.sb.d_toff.p, c->loc_f32.p);
+  GENEO_CHECK_LAUNCH();
+  op.u1.alloc(op.vlenS);
+  op.u2.alloc(op.vlenS);
+  op.u1.zero(s);
+  op.u2.zero(s);
+  GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+// yl += G_j S_j^-1 G_j^T xl for every subdomain (float64 gradient part of the
+// split local inverse), on padded local vectors
+void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s) {
+  XiOp &op = *c->xi;
+  k_gt<<<grid_for(op.nv, 256), 256, 0, s>>>(op.sptr.p, op.srow.p, op.ssgn.p, op.vslot_sub.p,
+                                            op.xvoff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nv, 1,
+                                            op.vlen, op.vlenS, xl, op.u1.p);
+  symv_batch<double>(op.sb, op.s_inv.p, op.u1.p, op.u2.p, c->d_err.p, s);
+  k_g<<<grid_for(op.nslots, 256), 256, 0, s>>>(op.ghead.p, op.gtail.p, op.slot_sub.p, op.Noff.p,
+                                               c->loc.d_voff.p, op.sb.d_voff.p, op.nslots, 1,
+                                               op.vlen, op.vlenS, op.u2.p, nullptr, yl, 2);
+  GENEO_CHECK_LAUNCH();
 }
 
 }  // namespace geneo

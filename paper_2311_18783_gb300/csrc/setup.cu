@@ -620,8 +620,10 @@ void setup_all(geneo_ctx *c) {
     c->d_g2l_ptr.upload(c->ls.g2l_ptr, s);
     c->d_g2l.upload(g2l, s);
   }
-  if (c->opt.precision == GENEO_PREC_FP32)
-    throw Error(GENEO_ERR_INVALID_ARG, "float32 local factors are not available in this build");
+  if (c->opt.precision == GENEO_PREC_FP32) {
+    build_split_factors(c);
+    c->local_prec = GENEO_PREC_FP32;
+  }
 
   // --- coarse space
   c->n0 = c->n0_snk = c->n0_geneo = 0;

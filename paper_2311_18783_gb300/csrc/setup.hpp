@@ -34,6 +34,12 @@ void check_device_error(geneo_ctx *c, cudaStream_t s);
 // GenEO eigenvectors of every subdomain (batched LOBPCG); appends columns
 // to the coarse basis
 void geneo_eigenvectors(geneo_ctx *c);
+// builds the local operators of every subdomain (see xi.hpp)
+void build_xi_operator(geneo_ctx *c, XiOp &op, cudaStream_t s);
+// float32 C_j = (I - xi_j) A_j^-1 of every subdomain (needs the float64 inverse)
+void build_split_factors(geneo_ctx *c);
+// yl += G_j S_j^-1 G_j^T xl, float64 gradient part of the split local solve
+void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s);
 
 void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s);
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s);

@@ -181,7 +181,14 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s) {
     e1 = c->ev_take();
     c->ev_local.push_back({e0, e1});
   }
-  symv_batch<double>(c->loc, c->loc_f64.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s, e0, e1);
+  if (c->local_prec == GENEO_PREC_FP32) {
+    // split inverse: float32 C_j r_j plus the float64 gradient part
+    symv_batch<float>(c->loc, c->loc_f32.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s, e0, e1);
+    split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s);
+    c->launches += 4;
+  } else {
+    symv_batch<double>(c->loc, c->loc_f64.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s, e0, e1);
+  }
   k_prolong<<<grid_for(n, 256), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w, n);
   GENEO_CHECK_LAUNCH();
 }
