@@ -95,6 +95,10 @@ typedef struct {
   int32_t lobpcg_maxit;      /* iterations per block before giving up */
   double lobpcg_tol;         /* relative eigen-residual tolerance */
   uint64_t seed;             /* initial LOBPCG blocks (counter-based hash) */
+  int32_t coarse_dense;      /* 0: sparse multifrontal Cholesky of E (nested dissection);
+                                1: explicit dense E^-1 (small coarse spaces, testing) */
+  int32_t coarse_leaf;       /* sparse factor: nested-dissection regions of at most this
+                                many columns become leaf fronts; 0 selects 256 */
 } geneo_options;
 
 typedef struct {
@@ -120,7 +124,8 @@ typedef struct {
 } geneo_solve_info;
 
 /* Fills `opt` with the defaults: FP64, SNK coarse space, GenEO on,
- * reciprocal tau, LOBPCG block 8, 200 iterations, tolerance 1e-8, seed 1. */
+ * reciprocal tau, LOBPCG block 8, 200 iterations, tolerance 1e-8, seed 1,
+ * sparse coarse factor. */
 void geneo_default_options(geneo_options *opt);
 
 /* Builds topology, decomposition, A, the local factors, the GenEO

@@ -90,6 +90,8 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
     return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
   if (o.lobpcg_block < 1 || o.lobpcg_block > 16 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
     return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");
+  if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0)
+    return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor options");
   return guarded([&]() {
     auto c = new geneo_ctx();
     try {
@@ -147,7 +149,7 @@ int geneo_query(const geneo_ctx *c, geneo_sizes *o) {
   o->n0_snk = c->n0_snk;
   o->n0_geneo = c->n0_geneo;
   o->local_factor_bytes = c->loc_f64.bytes() + c->loc_f32.bytes();
-  o->coarse_factor_bytes = c->crs_f64.bytes();
+  o->coarse_factor_bytes = c->mf ? geneo::mf_factor_bytes(c) : c->crs_f64.bytes();
   o->setup_seconds = c->setup_seconds;
   return GENEO_OK;
 }

@@ -7,6 +7,13 @@
 
 #include <memory>
 
+namespace geneo {
+struct Multifrontal;
+struct MfDeleter {
+  void operator()(Multifrontal *m) const;
+};
+}  // namespace geneo
+
 struct geneo_ctx {
   // problem copy
   int nx = 0, ny = 0, nz = 0;
@@ -54,6 +61,9 @@ struct geneo_ctx {
   geneo::DevBuf<double> d_zc_val, d_zr_val;
   geneo::TileBatch crs;
   geneo::DevBuf<double> crs_f64;
+
+  // sparse coarse factor (multifrontal); the dense E^-1 above is the alternative
+  std::unique_ptr<geneo::Multifrontal, geneo::MfDeleter> mf;
 
   // local operators (xi, S_j^-1, element data) for GenEO and the split solve
   std::unique_ptr<geneo::XiOp> xi;

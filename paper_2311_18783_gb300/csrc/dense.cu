@@ -251,10 +251,11 @@ __global__ void __launch_bounds__(256) k_syrk(double *data, const int32_t *nt, c
 // forward substitution on the identity, step k:
 //   Y_kj = L_kk^-1 B_kj  (j <= k), with B = I - (updates so far)
 __global__ void __launch_bounds__(256) k_fwd_diag(double *Y, const int32_t *nt, const int64_t *toff,
-                                                  const int64_t *dtoff, int k, const double *dinv) {
+                                                  const int64_t *dtoff, int k, const double *dinv,
+                                                  const int32_t *lim) {
   extern __shared__ double sh[];
   const int j = blockIdx.x, m = blockIdx.y;
-  if (k >= nt[m] || j > k) return;
+  if (k >= (lim ? lim[m] : nt[m]) || j > k) return;
   double *As = sh, *Bs = sh + kTile * kLd;
   double *dst = Y + tidx(toff[m], k, j) * kTileElems;
   load_tile_smem(As, dinv + (dtoff[m] + k) * kTileElems, false);
@@ -272,11 +273,11 @@ __global__ void __launch_bounds__(256) k_fwd_diag(double *Y, const int32_t *nt, 
 
 //   B_Ij -= L_Ik Y_kj  (I > k, j <= k)
 __global__ void __launch_bounds__(256) k_fwd_update(double *Y, const double *L, const int32_t *nt,
-                                                    const int64_t *toff, int k) {
+                                                    const int64_t *toff, int k, const int32_t *lim) {
   extern __shared__ double sh[];
   const int m = blockIdx.z;
   const int I = k + 1 + blockIdx.x, j = blockIdx.y;
-  if (I >= nt[m] || j > k) return;
+  if (I >= (lim ? lim[m] : nt[m]) || j > k) return;
   double *As = sh, *Bs = sh + kTile * kLd;
   load_tile_smem(As, L + tidx(toff[m], I, k) * kTileElems, false);
   load_tile_smem(Bs, Y + tidx(toff[m], k, j) * kTileElems, true);
@@ -408,16 +409,36 @@ void spd_invert(TileBatch &b, double *data, double *ws, int *d_err, cudaStream_t
   GENEO_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)tile_elems(b), s));
   k_identity<<<dim3(b.maxnt, b.nmat), 64, 0, s>>>(Y, b.d_nt.p, b.d_toff.p);
   for (int k = 0; k < b.maxnt; ++k) {
-    k_fwd_diag<<<dim3(k + 1, b.nmat), 256, two, s>>>(Y, b.d_nt.p, b.d_toff.p, d_dtoff.p, k, dinv);
+    k_fwd_diag<<<dim3(k + 1, b.nmat), 256, two, s>>>(Y, b.d_nt.p, b.d_toff.p, d_dtoff.p, k, dinv,
+                                                     nullptr);
     const int rest = b.maxnt - k - 1;
     if (rest > 0)
-      k_fwd_update<<<dim3(rest, k + 1, b.nmat), 256, two, s>>>(Y, data, b.d_nt.p, b.d_toff.p, k);
+      k_fwd_update<<<dim3(rest, k + 1, b.nmat), 256, two, s>>>(Y, data, b.d_nt.p, b.d_toff.p, k,
+                                                               nullptr);
   }
   const int64_t maxT = (int64_t)b.maxnt * (b.maxnt + 1) / 2;
   k_lauum<<<dim3((unsigned)maxT, b.nmat), 256, two, s>>>(data, Y, b.d_nt.p, b.d_toff.p);
   k_symmetrize_diag<<<dim3(b.maxnt, b.nmat), 256, 0, s>>>(data, b.d_nt.p, b.d_toff.p);
   GENEO_CHECK_LAUNCH();
   GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+void pivot_block_inverse(TileBatch &b, const double *L, double *Y, const double *dinv,
+                         const int64_t *d_dtoff, const int32_t *d_npiv, int max_npiv,
+                         cudaStream_t s) {
+  set_smem_attrs();
+  const int two = 2 * kTile * kLd * (int)sizeof(double);
+  GENEO_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)tile_elems(b), s));
+  k_identity<<<dim3(b.maxnt, b.nmat), 64, 0, s>>>(Y, b.d_nt.p, b.d_toff.p);
+  for (int k = 0; k < max_npiv; ++k) {
+    k_fwd_diag<<<dim3(k + 1, b.nmat), 256, two, s>>>(Y, b.d_nt.p, b.d_toff.p, d_dtoff, k, dinv,
+                                                     d_npiv);
+    const int rest = max_npiv - k - 1;
+    if (rest > 0)
+      k_fwd_update<<<dim3(rest, k + 1, b.nmat), 256, two, s>>>(Y, L, b.d_nt.p, b.d_toff.p, k,
+                                                               d_npiv);
+  }
+  GENEO_CHECK_LAUNCH();
 }
 
 void tiles_init_padding(TileBatch &b, double *data, cudaStream_t s) {

@@ -45,6 +45,12 @@ void spd_invert(TileBatch &b, double *data, double *ws, int *d_err, cudaStream_t
 void chol_factor(TileBatch &b, double *data, const int32_t *d_npiv, int nsteps, double *dinv,
                  const int64_t *d_dtoff, int *d_err, cudaStream_t s);
 
+// Y = L11^-1 for the leading npiv[m] pivot tiles of every matrix (L from
+// chol_factor with the same npiv, dinv its inverted diagonal tiles).
+void pivot_block_inverse(TileBatch &b, const double *L, double *Y, const double *dinv,
+                         const int64_t *d_dtoff, const int32_t *d_npiv, int max_npiv,
+                         cudaStream_t s);
+
 // -- y = blockdiag(A_m) x on padded vectors.  Templated on the storage type.
 // ev_before / ev_after, when given, are recorded around the streaming kernel.
 template <typename T>

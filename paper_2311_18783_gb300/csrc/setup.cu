@@ -397,19 +397,16 @@ void coltet_build(geneo_ctx *c, const Columns &X, std::vector<int64_t> &ct_ptr,
   GENEO_CUDA(cudaStreamSynchronize(s));
 }
 
-// X^T A X for the columns, element by element through per-tet curls (see
-// k_coltet), written into `tiles` of batch b at (cloc[a], cloc[b]).
-void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles, cudaStream_t s) {
+// Galerkin plan of sparse columns: column-tetrahedron entries on the device
+// and the lower pattern (pairs of columns of the same matrix sharing a
+// tetrahedron, b with loc(b) <= loc(a), per column a, ascending b).
+void galerkin_plan(geneo_ctx *c, const Columns &X, GalerkinPlan &P, cudaStream_t s) {
   const Topology &t = c->topo;
   const int64_t nt = t.ntets(), ncol = (int64_t)X.mat.size();
-  if (ncol == 0) return;
+  P.ncol = ncol;
   std::vector<int64_t> ct_ptr;
   std::vector<int32_t> ct_tet;
-  DevBuf<int64_t> dctp;
-  DevBuf<int32_t> dctt;
-  DevBuf<double> dct;
-  coltet_build(c, X, ct_ptr, ct_tet, dctp, dctt, dct, s);
-  // lower pattern: columns of the same matrix sharing a tetrahedron
+  coltet_build(c, X, ct_ptr, ct_tet, P.dctp, P.dctt, P.dct, s);
   std::vector<int64_t> tcp(nt + 1, 0);
   for (int32_t tt : ct_tet) tcp[tt + 1]++;
   for (int64_t q = 0; q < nt; ++q) tcp[q + 1] += tcp[q];
@@ -419,8 +416,9 @@ void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles,
     for (int64_t a = 0; a < ncol; ++a)
       for (int64_t q = ct_ptr[a]; q < ct_ptr[a + 1]; ++q) tcl[fill[ct_tet[q]]++] = (int32_t)a;
   }
-  std::vector<int64_t> pptr(1, 0);
-  std::vector<int32_t> pcol, list;
+  P.pptr.assign(1, 0);
+  P.pcol.clear();
+  std::vector<int32_t> list;
   std::vector<uint8_t> mark(ncol, 0);
   for (int64_t a = 0; a < ncol; ++a) {
     list.clear();
@@ -436,17 +434,71 @@ void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles,
     }
     std::sort(list.begin(), list.end());
     for (int32_t bb : list) mark[bb] = 0;
-    pcol.insert(pcol.end(), list.begin(), list.end());
-    pptr.push_back((int64_t)pcol.size());
+    P.pcol.insert(P.pcol.end(), list.begin(), list.end());
+    P.pptr.push_back((int64_t)P.pcol.size());
   }
-  DevBuf<int64_t> dpp;
-  DevBuf<int32_t> dpc, dmat, dloc;
-  dpp.upload(pptr, s);
-  dpc.upload(pcol, s);
+  P.dpp.upload(P.pptr, s);
+  P.dpc.upload(P.pcol, s);
+  GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+// vals[q] = (X^T A X)[a][pcol[q]] for every pattern entry q
+__global__ void k_galerkin_vals(const int64_t *__restrict__ pptr, const int32_t *__restrict__ pcol,
+                                int64_t ncols, const int64_t *__restrict__ ct_ptr,
+                                const int32_t *__restrict__ ct_tet, const double *__restrict__ ct,
+                                double *__restrict__ vals) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.y + threadIdx.y;
+  if (a >= ncols) return;
+  for (int64_t q = pptr[a] + threadIdx.x; q < pptr[a + 1]; q += blockDim.x) {
+    const int64_t b = pcol[q];
+    const int64_t sa = ct_ptr[a], ea = ct_ptr[a + 1], sb = ct_ptr[b], eb = ct_ptr[b + 1];
+    const bool swap = (ea - sa) > (eb - sb);
+    const int64_t xs = swap ? sb : sa, xe = swap ? eb : ea, ys = swap ? sa : sb, ye = swap ? ea : eb;
+    double s = 0;
+    for (int64_t i = xs; i < xe; ++i) {
+      const int32_t t = ct_tet[i];
+      int64_t lo = ys, hi = ye - 1, hit = -1;
+      while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t v = ct_tet[mid];
+        if (v == t) {
+          hit = mid;
+          break;
+        }
+        if (v < t) lo = mid + 1;
+        else hi = mid - 1;
+      }
+      if (hit < 0) continue;
+      const double *ea_ = ct + (swap ? hit : i) * 15;
+      const double *eb_ = ct + (swap ? i : hit) * 15;
+      double v = ea_[0] * eb_[0] + ea_[1] * eb_[1] + ea_[2] * eb_[2];
+      for (int k = 0; k < 6; ++k) v = fma(ea_[3 + k], eb_[9 + k], v);
+      s += v;
+    }
+    vals[q] = s;
+  }
+}
+
+void galerkin_values(GalerkinPlan &P, double *vals, cudaStream_t s) {
+  if (P.ncol == 0) return;
+  k_galerkin_vals<<<grid_for(P.ncol, 8), dim3(32, 8), 0, s>>>(P.dpp.p, P.dpc.p, P.ncol, P.dctp.p,
+                                                             P.dctt.p, P.dct.p, vals);
+  GENEO_CHECK_LAUNCH();
+}
+
+// X^T A X for the columns, element by element through per-tet curls (see
+// k_coltet), written into `tiles` of batch b at (cloc[a], cloc[b]).
+void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles, cudaStream_t s) {
+  const int64_t ncol = (int64_t)X.mat.size();
+  if (ncol == 0) return;
+  GalerkinPlan P;
+  galerkin_plan(c, X, P, s);
+  DevBuf<int32_t> dmat, dloc;
   dmat.upload(X.mat, s);
   dloc.upload(X.loc, s);
-  k_galerkin<<<grid_for(ncol, 8), dim3(32, 8), 0, s>>>(dpp.p, dpc.p, ncol, dctp.p, dctt.p, dct.p,
-                                                      dmat.p, dloc.p, b.d_toff.p, tiles);
+  k_galerkin<<<grid_for(ncol, 8), dim3(32, 8), 0, s>>>(P.dpp.p, P.dpc.p, ncol, P.dctp.p,
+                                                      P.dctt.p, P.dct.p, dmat.p, dloc.p,
+                                                      b.d_toff.p, tiles);
   GENEO_CHECK_LAUNCH();
   GENEO_CUDA(cudaStreamSynchronize(s));
 }
@@ -641,7 +693,13 @@ void setup_all(geneo_ctx *c) {
     geneo_eigenvectors(c);  // appends GenEO candidates to zc_* and sets n0_geneo
     if (c->n0_geneo > 0) geneo_filter(c);
   }
-  if (c->n0 > 0) {
+  if (c->n0 > 0 && !c->opt.coarse_dense) {
+    build_z_csr(c);
+    mf_setup(c);
+    c->crs_x.alloc(c->n0);
+    c->crs_y.alloc(c->n0);
+    c->crs_x.zero(s);
+  } else if (c->n0 > 0) {
     build_z_csr(c);
     c->crs.layout({c->n0});
     c->crs.upload_meta(s);

@@ -16,6 +16,19 @@ struct Columns {
   bool neumann = false;
 };
 
+// Galerkin plan: column-tetrahedron entries and the lower pattern of X^T A X
+struct GalerkinPlan {
+  int64_t ncol = 0;
+  std::vector<int64_t> pptr;
+  std::vector<int32_t> pcol;
+  DevBuf<int64_t> dpp, dctp;
+  DevBuf<int32_t> dpc, dctt;
+  DevBuf<double> dct;
+};
+void galerkin_plan(geneo_ctx *c, const Columns &X, GalerkinPlan &P, cudaStream_t s);
+// vals[q] for every pattern entry (device array of pcol.size() doubles)
+void galerkin_values(GalerkinPlan &P, double *vals, cudaStream_t s);
+
 // X^T A X summed per tetrahedron (curl-curl part through the curl of each
 // column on the tetrahedron), written into the tile-packed batch.
 void galerkin_tiles(geneo_ctx *c, const Columns &X, TileBatch &b, double *tiles, cudaStream_t s);
@@ -40,6 +53,12 @@ void build_xi_operator(geneo_ctx *c, XiOp &op, cudaStream_t s);
 void build_split_factors(geneo_ctx *c);
 // yl += G_j S_j^-1 G_j^T xl, float64 gradient part of the split local solve
 void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s);
+
+// multifrontal coarse factor: set-up, solve y = E^-1 t (column order), sizes
+void mf_setup(geneo_ctx *c);
+void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s);
+int mf_launches_per_solve(const geneo_ctx *c);
+int64_t mf_factor_bytes(const geneo_ctx *c);
 
 void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s);
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s);

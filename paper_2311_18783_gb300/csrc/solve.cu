@@ -199,6 +199,24 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
     GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, s));
     return;
   }
+  if (c->mf) {
+    c->launches += 2 + mf_launches_per_solve(c);
+    k_zt<<<grid_for(c->n0, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
+                                              c->crs_x.p, c->n0);
+    if (c->prof) {
+      cudaEvent_t e0 = c->ev_take(), e1 = c->ev_take();
+      c->ev_coarse.push_back({e0, e1});
+      GENEO_CUDA(cudaEventRecord(e0, s));
+      mf_solve(c, c->crs_x.p, c->crs_y.p, s);
+      GENEO_CUDA(cudaEventRecord(e1, s));
+    } else {
+      mf_solve(c, c->crs_x.p, c->crs_y.p, s);
+    }
+    k_z<<<grid_for(n, 256), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p, c->crs_y.p,
+                                         y, n);
+    GENEO_CHECK_LAUNCH();
+    return;
+  }
   c->launches += 4;
   k_zt<<<grid_for(c->n0, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
                                             c->crs_x.p, c->n0);
