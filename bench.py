@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                    help="mixed: float32 split local factors (headline) and float64 beside it")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=[WORKLOAD, "cube16_hole_channels"],
+                   help="cube16_hole_channels: the profiling-size companion (ncu captures)")
     return p.parse_args()
 
 
@@ -217,7 +220,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import workloads as W
     import paper_2311_18783_gb300 as pkg
-    w = getattr(W, WORKLOAD)()
+    w = getattr(W, args.workload)()
     prec = pkg.PREC_FP32 if args.precision == "mixed" else pkg.PREC_FP64
     t0 = time.perf_counter()
     s = pkg.Solver.from_workload(w, precision=prec)
@@ -321,8 +324,9 @@ def main():
             "dtype": "f64" if prec == pkg.PREC_FP64 else "f32+f64",
             "plain_fp64": fp64_side,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "nsub": s.sizes["nsub"],
+            "config": {"workload": args.workload, "n": n, "nsub": s.sizes["nsub"],
                        "n0": s.sizes["n0"], "n0_geneo": s.sizes["n0_geneo"], "tol": TOL,
+                       "coarse_factor_gb": s.sizes["coarse_factor_bytes"] / 1e9,
                        "pcg_iters": iters[-1], "precision": args.precision,
                        "l2": "inputs larger than L2 (local factors "
                              f"{s.sizes['local_factor_bytes'] / 1e9:.1f} GB)",
@@ -331,7 +335,7 @@ def main():
             "roofline": roof, "clocks": clk, "gpu_launches": prof["launches"],
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8,
                     "d2h_bytes_per_step": n * 8}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         o = OracleSample()
         o.step()
         per_iter, oinfo = statistics.median([o.step() for _ in range(2)]), o.info

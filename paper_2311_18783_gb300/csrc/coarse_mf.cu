@@ -25,6 +25,7 @@ namespace geneo {
 
 namespace {
 constexpr int kLeafDefault = 256;
+constexpr int kChunk = 4;  // tiles per task of the solve's tile GEMVs
 
 struct Front {
   std::vector<int32_t> cols;      // pivot columns (coarse column ids)
@@ -131,85 +132,121 @@ __global__ void k_mf_gather(const int32_t *__restrict__ rf, const int32_t *__res
   w[voff[f] + l] = v;
 }
 
-// tile-row GEMV: out_I (op) sum_{J in [J0, J1)} T(I, J) v_J with T = tiles of
-// matrix f; mode 0: out = sum (to y and the global y at pivots), mode 1:
-// out -= sum (update rows)
-__global__ void __launch_bounds__(256) k_mf_rows(const int32_t *__restrict__ it_f,
-                                                 const int32_t *__restrict__ it_I,
-                                                 const int32_t *__restrict__ npivt,
-                                                 const int32_t *__restrict__ npiv,
-                                                 const int64_t *__restrict__ first,
-                                                 const int64_t *__restrict__ toff,
-                                                 const int64_t *__restrict__ voff,
-                                                 const double *__restrict__ T,
-                                                 const double *__restrict__ vin,
-                                                 double *__restrict__ vout,
-                                                 double *__restrict__ ypos, int mode) {
-  const int f = it_f[blockIdx.x], I = it_I[blockIdx.x];
-  const int J1 = mode == 0 ? I + 1 : npivt[f];
-  const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
-  double acc = 0;
-  for (int J = 0; J < J1; ++J) {
-    const double *t = T + (toff[f] + (int64_t)I * (I + 1) / 2 + J) * kTileElems + r * kTile + q * 16;
-    const double *v = vin + voff[f] + (int64_t)J * kTile + q * 16;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc = fma(t[k], v[k], acc);
-  }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  if (q) return;
-  const int64_t row = (int64_t)I * kTile + r;
-  if (mode == 0) {
-    vout[voff[f] + row] = acc;
-    if (ypos && row < npiv[f]) ypos[first[f] + row] = acc;
-  } else {
-    vout[voff[f] + row] -= acc;
-  }
-}
+// One task of a tile GEMV phase: tiles j0 <= K < j1 of tile row I (row
+// modes) or tile column I (column modes) of front f.  Tasks of one output
+// tile are consecutive (slots rbase .. rbase + nch - 1) and share counter cnt.
+struct MfTask {
+  int32_t f, I, j0, j1;
+  int32_t slot, rbase, nch, cnt;
+};
 
-// tile-column GEMV (transposed): mode 0: t_J = y_J - sum_{I >= npivt} L(I,J)^T xU_I
-// with xU gathered from the global solution at the update rows; mode 1:
-// x_J = sum_{npivt > I >= J} Y(I,J)^T t_I, written to the global solution
-__global__ void __launch_bounds__(256) k_mf_cols(
-    const int32_t *__restrict__ it_f, const int32_t *__restrict__ it_J,
-    const int32_t *__restrict__ npivt, const int32_t *__restrict__ nt,
-    const int32_t *__restrict__ npiv, const int32_t *__restrict__ npivp,
-    const int64_t *__restrict__ nupd, const int64_t *__restrict__ first,
-    const int64_t *__restrict__ uoff, const int64_t *__restrict__ upos,
-    const int64_t *__restrict__ toff, const int64_t *__restrict__ voff,
-    const double *__restrict__ T, const double *__restrict__ ybuf, double *__restrict__ tbuf,
-    double *__restrict__ xpos, int mode) {
-  const int f = it_f[blockIdx.x], J = it_J[blockIdx.x];
-  const int c = threadIdx.x >> 2, q = threadIdx.x & 3;
-  __shared__ double xv[kTile];
-  double acc = 0;
-  const int I0 = mode == 0 ? npivt[f] : J, I1 = mode == 0 ? nt[f] : npivt[f];
-  for (int I = I0; I < I1; ++I) {
+// Phases of the solve (T = tiles of front f, v = input, o = output tile):
+//   0: y_I  = sum_{J<=I} Y(I,J) w_J            (forward, pivot rows)
+//   1: w_I -= sum_{J<npivt} L(I,J) y_J          (forward, update rows)
+//   2: t_J  = y_J - sum_{I>=npivt} L(I,J)^T x_I (backward, x_I gathered from the
+//                                                solution at the update rows)
+//   3: x_J  = sum_{J<=I<npivt} Y(I,J)^T t_I      (backward, to the solution)
+// Each task reduces its tiles to a 64-vector; a task whose output tile has
+// several tasks stores it to part[slot] and the last of them to finish sums
+// the stored vectors in slot order (deterministic) and writes the output.
+struct MfArgs {
+  const int32_t *npivt, *npiv, *npivp;
+  const int64_t *nupd, *first, *uoff, *upos, *toff, *voff;
+  const double *T;
+  double *wbuf, *ybuf, *tbuf, *xpos, *part;
+  int32_t *cnt;
+};
+
+template <int kMode>
+__global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tasks, MfArgs a) {
+  const MfTask tk = tasks[blockIdx.x];
+  const int f = tk.f, O = tk.I;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __shared__ double red[8][kTile];
+  __shared__ double vec[kTile];
+  __shared__ int last;
+  const int64_t vo = a.voff[f];
+  if (kMode <= 1) {
+    // row modes: warp w owns rows 8w..8w+7, lane l columns 2l, 2l+1
+    double acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = 0.0;
+    const double *vin = kMode == 0 ? a.wbuf : a.ybuf;
+    for (int K = tk.j0; K < tk.j1; ++K) {
+      const double *t = a.T + (a.toff[f] + (int64_t)O * (O + 1) / 2 + K) * kTileElems;
+      const double2 x = *reinterpret_cast<const double2 *>(vin + vo + (int64_t)K * kTile + 2 * l);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
+        acc[r] = fma(v.x, x.x, fma(v.y, x.y, acc[r]));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      double v = acc[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) vec[w * 8 + r] = v;
+    }
+  } else {
+    // column modes: warp w owns rows 8w..8w+7 of every tile, lane l columns 2l, 2l+1
+    double c0 = 0.0, c1 = 0.0;
+    for (int K = tk.j0; K < tk.j1; ++K) {
+      const double *t = a.T + (a.toff[f] + (int64_t)K * (K + 1) / 2 + O) * kTileElems;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t row = (int64_t)K * kTile + w * 8 + r;
+        double x;
+        if (kMode == 2) {
+          const int64_t u = row - a.npivp[f];
+          x = (u >= 0 && u < a.nupd[f]) ? a.xpos[a.upos[a.uoff[f] + u]] : 0.0;
+        } else {
+          x = a.tbuf[vo + row];
+        }
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
+        c0 = fma(v.x, x, c0);
+        c1 = fma(v.y, x, c1);
+      }
+    }
+    red[w][2 * l] = c0;
+    red[w][2 * l + 1] = c1;
     __syncthreads();
     if (threadIdx.x < kTile) {
-      const int64_t row = (int64_t)I * kTile + threadIdx.x;
-      double v = 0;
-      if (mode == 0) {
-        const int64_t u = row - npivp[f];
-        if (u >= 0 && u < nupd[f]) v = xpos[upos[uoff[f] + u]];
-      } else {
-        v = tbuf[voff[f] + row];
-      }
-      xv[threadIdx.x] = v;
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += red[q][threadIdx.x];
+      vec[threadIdx.x] = v;
+    }
+  }
+  __syncthreads();
+  if (tk.nch > 1) {
+    if (threadIdx.x < kTile) {
+      a.part[(int64_t)tk.slot * kTile + threadIdx.x] = vec[threadIdx.x];
+      __threadfence();
     }
     __syncthreads();
-    const double *t = T + (toff[f] + (int64_t)I * (I + 1) / 2 + J) * kTileElems + c;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc = fma(t[(q * 16 + k) * kTile], xv[q * 16 + k], acc);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(&a.cnt[tk.cnt], 1) == tk.nch - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < kTile) {
+      double v = 0.0;
+      for (int k = 0; k < tk.nch; ++k) v += __ldcg(a.part + (int64_t)(tk.rbase + k) * kTile + threadIdx.x);
+      vec[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) a.cnt[tk.cnt] = 0;
+    __syncthreads();
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  if (q) return;
-  const int64_t col = (int64_t)J * kTile + c;
-  if (mode == 0) {
-    tbuf[voff[f] + col] = ybuf[voff[f] + col] - acc;
-  } else if (col < npiv[f]) {
-    xpos[first[f] + col] = acc;
+  if (threadIdx.x < kTile) {
+    const int64_t idx = (int64_t)O * kTile + threadIdx.x;
+    const double v = vec[threadIdx.x];
+    if (kMode == 0) a.ybuf[vo + idx] = v;
+    else if (kMode == 1) a.wbuf[vo + idx] -= v;
+    else if (kMode == 2) a.tbuf[vo + idx] = a.ybuf[vo + idx] - v;
+    else if (idx < a.npiv[f]) a.xpos[a.first[f] + idx] = v;
   }
 }
 
@@ -231,16 +268,15 @@ struct MfLevel {
   DevBuf<int32_t> rf, rl;                           // gather rows
   DevBuf<int64_t> gptr, gidx;
   int64_t nrows = 0;
-  DevBuf<int32_t> piv_f, piv_I, upd_f, upd_I;       // row items
-  int npiv_items = 0, nupd_items = 0;
-  DevBuf<int32_t> col_f, col_J;                     // backward column items
-  int ncol_items = 0;
+  DevBuf<MfTask> task[4];                           // tile GEMV tasks per phase
+  int ntask[4] = {0, 0, 0, 0};
 };
 
 struct Multifrontal {
   int nfront = 0;
   TileBatch fb;
-  DevBuf<double> L, Y, dinv, wbuf, ybuf, tbuf, cpos, xpos;
+  DevBuf<double> L, Y, dinv, wbuf, ybuf, tbuf, cpos, xpos, part;
+  DevBuf<int32_t> cnt;
   DevBuf<int64_t> dtoff, first, nupd, uoff, upos, pos;
   DevBuf<int32_t> npiv, npivp, npivt, parent, nt;
   std::vector<MfLevel> levels;
@@ -452,6 +488,8 @@ void mf_setup(geneo_ctx *c) {
   int nlev = 0;
   for (int f = 0; f < nf; ++f) nlev = std::max(nlev, F[f].level + 1);
   M->levels.resize(nlev);
+  int nslot = 0, ncnt = 0;
+  std::vector<MfTask> tasks[4];
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M->levels[lv];
     std::vector<int32_t> np(nf, 0);
@@ -486,7 +524,7 @@ void mf_setup(geneo_ctx *c) {
       Lv.ea_J[sl].upload(jj, s);
     }
     // solve items
-    std::vector<int32_t> rf, rl, pf, pI, uf, uI, cf, cJ;
+    std::vector<int32_t> rf, rl;
     std::vector<int64_t> gp(1, 0), gi;
     for (int f = 0; f < nf; ++f) {
       if (F[f].level != lv) continue;
@@ -503,32 +541,46 @@ void mf_setup(geneo_ctx *c) {
         gi.insert(gi.end(), g[l].begin(), g[l].end());
         gp.push_back((int64_t)gi.size());
       }
-      for (int I = 0; I < h_npivt[f]; ++I) {
-        pf.push_back(f);
-        pI.push_back(I);
-        cf.push_back(f);
-        cJ.push_back(I);
-      }
-      for (int I = h_npivt[f]; I < fb.nt[f]; ++I) {
-        uf.push_back(f);
-        uI.push_back(I);
-      }
+      // tile GEMV tasks: output tile O of front f, input tiles [o0, o1)
+      // split into chunks of kChunk tiles
+      auto add = [&](int ph, int O, int o0, int o1) {
+        const int nch = std::max(1, (o1 - o0 + kChunk - 1) / kChunk);
+        const int rbase = nslot;
+        for (int k = 0; k < nch; ++k) {
+          MfTask tk;
+          tk.f = f;
+          tk.I = O;
+          tk.j0 = o0 + k * kChunk;
+          tk.j1 = std::min(o1, o0 + (k + 1) * kChunk);
+          tk.slot = nslot++;
+          tk.rbase = rbase;
+          tk.nch = nch;
+          tk.cnt = ncnt;
+          tasks[ph].push_back(tk);
+        }
+        ++ncnt;
+      };
+      const int npt = h_npivt[f], ntf = fb.nt[f];
+      for (int O = 0; O < npt; ++O) add(0, O, 0, O + 1);
+      for (int O = npt; O < ntf; ++O) add(1, O, 0, npt);
+      // (a front without update rows gets one empty task: t = y)
+      for (int O = 0; O < npt; ++O) add(2, O, npt, ntf);
+      for (int O = 0; O < npt; ++O) add(3, O, O, npt);
+    }
+    for (int ph = 0; ph < 4; ++ph) {
+      Lv.task[ph].upload(tasks[ph], s);
+      Lv.ntask[ph] = (int)tasks[ph].size();
+      tasks[ph].clear();
     }
     Lv.rf.upload(rf, s);
     Lv.rl.upload(rl, s);
     Lv.gptr.upload(gp, s);
     Lv.gidx.upload(gi, s);
     Lv.nrows = (int64_t)rf.size();
-    Lv.piv_f.upload(pf, s);
-    Lv.piv_I.upload(pI, s);
-    Lv.npiv_items = (int)pf.size();
-    Lv.upd_f.upload(uf, s);
-    Lv.upd_I.upload(uI, s);
-    Lv.nupd_items = (int)uf.size();
-    Lv.col_f.upload(cf, s);
-    Lv.col_J.upload(cJ, s);
-    Lv.ncol_items = (int)cf.size();
   }
+  M->part.alloc((int64_t)std::max(1, nslot) * kTile);
+  M->cnt.alloc(std::max(1, ncnt));
+  M->cnt.zero(s);
   // --- numeric factorisation, level by level
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M->levels[lv];
@@ -567,32 +619,24 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s) {
   TileBatch &fb = M.fb;
   const int64_t n0 = c->n0;
   k_perm<<<grid_for(n0, 256), 256, 0, s>>>(M.pos.p, t, M.cpos.p, n0, 1);
+  MfArgs al{M.npivt.p, M.npiv.p, M.npivp.p, M.nupd.p, M.first.p, M.uoff.p, M.upos.p,
+            fb.d_toff.p, fb.d_voff.p, M.L.p, M.wbuf.p, M.ybuf.p, M.tbuf.p, M.xpos.p,
+            M.part.p, M.cnt.p};
+  MfArgs ay = al;
+  ay.T = M.Y.p;
   const int nlev = (int)M.levels.size();
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M.levels[lv];
     k_mf_gather<<<grid_for(Lv.nrows, 256), 256, 0, s>>>(Lv.rf.p, Lv.rl.p, Lv.gptr.p, Lv.gidx.p,
                                                          M.first.p, M.npiv.p, fb.d_voff.p,
                                                          Lv.nrows, M.cpos.p, M.wbuf.p);
-    if (Lv.npiv_items)
-      k_mf_rows<<<Lv.npiv_items, 256, 0, s>>>(Lv.piv_f.p, Lv.piv_I.p, M.npivt.p, M.npiv.p,
-                                               M.first.p, fb.d_toff.p, fb.d_voff.p, M.Y.p, M.wbuf.p,
-                                               M.ybuf.p, nullptr, 0);
-    if (Lv.nupd_items)
-      k_mf_rows<<<Lv.nupd_items, 256, 0, s>>>(Lv.upd_f.p, Lv.upd_I.p, M.npivt.p, M.npiv.p,
-                                               M.first.p, fb.d_toff.p, fb.d_voff.p, M.L.p, M.ybuf.p,
-                                               M.wbuf.p, nullptr, 1);
+    if (Lv.ntask[0]) k_mf_tiles<0><<<Lv.ntask[0], 256, 0, s>>>(Lv.task[0].p, ay);
+    if (Lv.ntask[1]) k_mf_tiles<1><<<Lv.ntask[1], 256, 0, s>>>(Lv.task[1].p, al);
   }
   for (int lv = nlev - 1; lv >= 0; --lv) {
     MfLevel &Lv = M.levels[lv];
-    if (!Lv.ncol_items) continue;
-    k_mf_cols<<<Lv.ncol_items, 256, 0, s>>>(Lv.col_f.p, Lv.col_J.p, M.npivt.p, M.nt.p, M.npiv.p,
-                                             M.npivp.p, M.nupd.p, M.first.p, M.uoff.p, M.upos.p,
-                                             fb.d_toff.p, fb.d_voff.p, M.L.p, M.ybuf.p, M.tbuf.p,
-                                             M.xpos.p, 0);
-    k_mf_cols<<<Lv.ncol_items, 256, 0, s>>>(Lv.col_f.p, Lv.col_J.p, M.npivt.p, M.nt.p, M.npiv.p,
-                                             M.npivp.p, M.nupd.p, M.first.p, M.uoff.p, M.upos.p,
-                                             fb.d_toff.p, fb.d_voff.p, M.Y.p, M.ybuf.p, M.tbuf.p,
-                                             M.xpos.p, 1);
+    if (Lv.ntask[2]) k_mf_tiles<2><<<Lv.ntask[2], 256, 0, s>>>(Lv.task[2].p, al);
+    if (Lv.ntask[3]) k_mf_tiles<3><<<Lv.ntask[3], 256, 0, s>>>(Lv.task[3].p, ay);
   }
   k_perm<<<grid_for(n0, 256), 256, 0, s>>>(M.pos.p, M.xpos.p, y, n0, 0);
   GENEO_CHECK_LAUNCH();
@@ -601,7 +645,7 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s) {
 int mf_launches_per_solve(const geneo_ctx *c) {
   int n = 2;
   for (const MfLevel &Lv : c->mf->levels)
-    n += 1 + (Lv.npiv_items ? 1 : 0) + (Lv.nupd_items ? 1 : 0) + (Lv.ncol_items ? 2 : 0);
+    n += 1 + (Lv.ntask[0] > 0) + (Lv.ntask[1] > 0) + (Lv.ntask[2] > 0) + (Lv.ntask[3] > 0);
   return n;
 }
 

@@ -512,19 +512,24 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
-template <typename T, int NST>
+// Tiles are consumed in batches of up to D tiles of one strip: one barrier
+// after the D waits (also the uniform timeout decision), the D tiles'
+// products, one barrier, then the column partials of the D tiles reduced
+// across warps by all threads, and D new copies issued.
+template <typename T, int NST, int D>
 __global__ void __launch_bounds__(256, 1)
     k_symv_strips(const T *__restrict__ data, const int64_t *__restrict__ toff,
                   const int64_t *__restrict__ voff, const int32_t *__restrict__ strip_m,
                   const int32_t *__restrict__ strip_I, const int32_t *__restrict__ cta_off,
                   const double *__restrict__ x, double *__restrict__ rowpart,
                   double *__restrict__ colpart, int *err) {
+  static_assert(D <= NST && D * kTile <= 256, "batch must fit the stages and the block");
   using A = typename Acc<T>::type;
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(128) unsigned char smraw[];
   T *stage = reinterpret_cast<T *>(smraw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + (size_t)NST * kTileElems * sizeof(T));
-  A *red = reinterpret_cast<A *>(bar + NST);  // [8][64]
+  A *red = reinterpret_cast<A *>(bar + NST);  // [D][8][64]
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
   if (s0 >= s1) return;
@@ -557,47 +562,67 @@ __global__ void __launch_bounds__(256, 1)
     const int m = strip_m[s], I = strip_I[s];
     const int64_t vb = voff[m];
     const int64_t tb = toff[m] + (int64_t)I * (I + 1) / 2;
-    A xi[8];
+    A xi[8], rp[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) xi[r] = (A)x[vb + (int64_t)I * kTile + w * 8 + r];
-    A rp[8];
+    for (int r = 0; r < 8; ++r) {
+      xi[r] = (A)x[vb + (int64_t)I * kTile + w * 8 + r];
+      rp[r] = (A)0;
+    }
+    for (int J0 = 0; J0 <= I; J0 += D) {
+      const int nb = min(D, I + 1 - J0);
+      // x of the batch's columns, loaded before the waits
+      A xj[D][2];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) rp[r] = (A)0;
-    for (int J = 0; J <= I; ++J) {
-      const int st = (int)(consumed % NST);
-      const uint32_t par = (uint32_t)((consumed / NST) & 1);
-      const bool ok = mbar_wait_bounded(&bar[st], par);
-      // uniform decision: also orders the previous tile's red[] reads before
-      // this tile's writes
+      for (int d = 0; d < D; ++d) {
+        const int64_t c = vb + (int64_t)(J0 + d) * kTile + 2 * l;
+        xj[d][0] = d < nb ? (A)x[c] : (A)0;
+        xj[d][1] = d < nb ? (A)x[c + 1] : (A)0;
+      }
+      bool ok = true;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (d >= nb) break;
+        const long long q = consumed + d;
+        ok = ok && mbar_wait_bounded(&bar[(int)(q % NST)], (uint32_t)((q / NST) & 1));
+      }
+      // uniform decision; also orders the previous batch's red[] reads
+      // before this batch's writes
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicCAS(err, kDevOk, kDevTimeout);
         failed = true;
         break;
       }
-      const T *t = stage + (size_t)st * kTileElems;
-      const A xj0 = (A)x[vb + (int64_t)J * kTile + 2 * l];
-      const A xj1 = (A)x[vb + (int64_t)J * kTile + 2 * l + 1];
-      A c0 = 0, c1 = 0;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const V2 a = *reinterpret_cast<const V2 *>(t + (w * 8 + r) * kTile + 2 * l);
-        rp[r] = fma((A)a.x, xj0, fma((A)a.y, xj1, rp[r]));
-        c0 = fma((A)a.x, xi[r], c0);
-        c1 = fma((A)a.y, xi[r], c1);
-      }
-      if (J < I) {
-        red[w * kTile + 2 * l] = c0;
-        red[w * kTile + 2 * l + 1] = c1;
+      for (int d = 0; d < D; ++d) {
+        if (d < nb) {
+          const T *t = stage + (size_t)((consumed + d) % NST) * kTileElems;
+          A c0 = 0, c1 = 0;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const V2 a = *reinterpret_cast<const V2 *>(t + (w * 8 + r) * kTile + 2 * l);
+            rp[r] = fma((A)a.x, xj[d][0], fma((A)a.y, xj[d][1], rp[r]));
+            c0 = fma((A)a.x, xi[r], c0);
+            c1 = fma((A)a.y, xi[r], c1);
+          }
+          red[(d * 8 + w) * kTile + 2 * l] = c0;
+          red[(d * 8 + w) * kTile + 2 * l + 1] = c1;
+        }
       }
       __syncthreads();
-      if (J < I && tid < kTile) {
-        A sum = 0;
+      {
+        const int d = tid >> 6, c = tid & 63;
+        // column partials of the off-diagonal tiles (the diagonal tile is
+        // stored in full and counted by the row partials)
+        if (d < nb && J0 + d < I) {
+          A sum = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sum += red[q * kTile + tid];
-        colpart[(tb + J) * kTile + tid] = (double)sum;
+          for (int q = 0; q < 8; ++q) sum += red[(d * 8 + q) * kTile + c];
+          colpart[(tb + J0 + d) * kTile + c] = (double)sum;
+        }
       }
-      ++consumed;
-      if (tid == 0) issue();
+      consumed += nb;
+      if (tid == 0)
+        for (int d = 0; d < nb; ++d) issue();
     }
     if (failed) break;
 #pragma unroll
@@ -638,21 +663,22 @@ __global__ void k_symv_reduce(const int32_t *__restrict__ vrow_m,
 }
 
 template <typename T> constexpr int symv_stages() { return sizeof(T) == 8 ? 4 : 8; }
+template <typename T> constexpr int symv_batch_tiles() { return sizeof(T) == 8 ? 2 : 4; }
 
 template <typename T>
 void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
                 cudaStream_t s, cudaEvent_t ev_before, cudaEvent_t ev_after) {
-  constexpr int NST = symv_stages<T>();
+  constexpr int NST = symv_stages<T>(), D = symv_batch_tiles<T>();
   const size_t smem = (size_t)NST * kTileElems * sizeof(T) + NST * sizeof(uint64_t) +
-                      8 * kTile * sizeof(typename Acc<T>::type);
+                      (size_t)D * 8 * kTile * sizeof(typename Acc<T>::type);
   static bool attr = false;
   if (!attr) {
-    GENEO_CUDA(cudaFuncSetAttribute(k_symv_strips<T, NST>,
+    GENEO_CUDA(cudaFuncSetAttribute(k_symv_strips<T, NST, D>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   if (ev_before) GENEO_CUDA(cudaEventRecord(ev_before, s));
-  k_symv_strips<T, NST><<<b.sched_ctas, 256, smem, s>>>(
+  k_symv_strips<T, NST, D><<<b.sched_ctas, 256, smem, s>>>(
       data, b.d_toff.p, b.d_voff.p, b.d_strip_m.p, b.d_strip_I.p, b.d_cta_off.p, x, b.rowpart.p,
       b.colpart.p, d_err);
   if (ev_after) GENEO_CUDA(cudaEventRecord(ev_after, s));

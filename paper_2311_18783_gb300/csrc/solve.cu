@@ -62,15 +62,19 @@ __global__ void k_prolong(const int64_t *__restrict__ ptr, const int64_t *__rest
   w[e] = s;
 }
 
-// t[a] = (Z^T r)_a, one column per thread (CSC)
+// t[a] = (Z^T r)_a, one column per warp (CSC): split near-kernel columns
+// have a few entries, GenEO columns one per dof of their subdomain
 __global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zrow,
                      const double *__restrict__ zval, const double *__restrict__ r,
                      double *__restrict__ t, int64_t n0) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int l = threadIdx.x & 31;
   if (a >= n0) return;
   double s = 0;
-  for (int64_t k = zptr[a]; k < zptr[a + 1]; ++k) s = fma(zval[k], r[zrow[k]], s);
-  t[a] = s;
+  for (int64_t k = zptr[a] + l; k < zptr[a + 1]; k += 32) s = fma(zval[k], r[zrow[k]], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (l == 0) t[a] = s;
 }
 
 // y[e] = (Z u)_e, one row per thread (CSR)
@@ -201,7 +205,7 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
   }
   if (c->mf) {
     c->launches += 2 + mf_launches_per_solve(c);
-    k_zt<<<grid_for(c->n0, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
+    k_zt<<<grid_for(c->n0 * 32, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
                                               c->crs_x.p, c->n0);
     if (c->prof) {
       cudaEvent_t e0 = c->ev_take(), e1 = c->ev_take();
@@ -218,7 +222,7 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
     return;
   }
   c->launches += 4;
-  k_zt<<<grid_for(c->n0, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
+  k_zt<<<grid_for(c->n0 * 32, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
                                             c->crs_x.p, c->n0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->prof) {

@@ -137,6 +137,31 @@ def cube32_hole_channels(seed=2):
     return w
 
 
+def cube16_hole_channels(seed=2):
+    """Profiling-size companion of cube32_hole_channels: 16^3 unit cube with
+    a through-hole (central 4x4x16 column removed); mu^-1 log-uniform in
+    [1,1e3] per cell inside 4 random 1x1-cell channels along a random axis,
+    1 elsewhere; eps=1; gamma=1e-4; f uniform in [-1,1]^3 per edge;
+    4x4x4 boxes, overlap 1 (local factors ~0.3 GB in float32)."""
+    n = 16
+    rng = np.random.default_rng(seed)
+    ci, cj, ck = _cell_ijk(n, n, n)
+    ijk = np.stack([ci, cj, ck])
+    active = np.ones(n ** 3, dtype=np.uint8)
+    active[(ci >= 6) & (ci < 10) & (cj >= 6) & (cj < 10)] = 0
+    mu = np.ones(n ** 3)
+    for _ in range(4):
+        axis = int(rng.integers(0, 3))
+        others = [a for a in range(3) if a != axis]
+        p = int(rng.integers(0, n))
+        q = int(rng.integers(0, n))
+        m = (ijk[others[0]] == p) & (ijk[others[1]] == q)
+        mu[m] = 10.0 ** rng.uniform(0.0, 3.0, size=int(m.sum()))
+    f = _uniform_f(rng, (n + 1) ** 3, 1)
+    return Workload("cube16_hole_channels", n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, active, mu,
+                    np.ones(n ** 3), 1e-4, (4, 4, 4), 1, 0.1, f)
+
+
 def beam128_layered(seed=4, nrhs=16):
     """128x16x16 cells (h=1/16), two 4x4-cell through-holes along x
     (y in [3,7) and [9,13), z in [6,10)); mu^-1 alternating 1 and 1e6 every
