@@ -55,6 +55,13 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# DRAM traffic of k_symv_strips<float, 8, 4> per algorithmic byte, from one ncu
+# capture on cube16_hole_channels: (204.36 MB read + 7.14 MB written) / 203.69 MB
+# of stored tiles.  Traffic scales with the stored tiles, so the full launch's
+# traffic is this ratio times its algorithmic bytes.  Set to None when the
+# kernel changes until it is captured again.
+SYMV_F32_TRAFFIC_RATIO = (204.3628 + 7.1421) / 203.6859
+
 # FP64 FMA rate of GB300: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2070 MHz
 # (the recipe's 1.25 TFLOP/s nominal figure at the maximum SM clock)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
@@ -314,7 +321,11 @@ def main():
         peak = peaks["hbm_gbs"]
         roof = {"kernel": "k_symv_strips<float> (local split factors)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"hbm_gbs of {peak_src}", "traffic": None,
+                "peak_source": f"hbm_gbs of {peak_src}",
+                "traffic": (None if SYMV_F32_TRAFFIC_RATIO is None else
+                            SYMV_F32_TRAFFIC_RATIO * prof["local_symv_bytes"]),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum on "
+                                  "cube16_hole_channels, scaled by stored tiles",
                 "algorithmic_bytes_per_launch": prof["local_symv_bytes"],
                 "launch_ms": t_launch * 1e3}
     applies_per_s = (sum(iters) + len(iters)) / (ms * args.steps / 1e3)
