@@ -99,6 +99,8 @@ typedef struct {
                                 1: explicit dense E^-1 (small coarse spaces, testing) */
   int32_t coarse_leaf;       /* sparse factor: nested-dissection regions of at most this
                                 many columns become leaf fronts; 0 selects 256 */
+  int32_t use_graph;         /* 1: every PCG iteration after the first replays one CUDA
+                                graph captured at the first solve; 0: plain launches */
 } geneo_options;
 
 typedef struct {
@@ -125,7 +127,7 @@ typedef struct {
 
 /* Fills `opt` with the defaults: FP64, SNK coarse space, GenEO on,
  * reciprocal tau, LOBPCG block 8, 200 iterations, tolerance 1e-8, seed 1,
- * sparse coarse factor. */
+ * sparse coarse factor, PCG iteration as a CUDA graph. */
 void geneo_default_options(geneo_options *opt);
 
 /* Builds topology, decomposition, A, the local factors, the GenEO

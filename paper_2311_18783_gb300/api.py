@@ -36,7 +36,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("coarse", C.c_int32), ("geneo", C.c_int32),
                 ("tau_convention", C.c_int32), ("lobpcg_block", C.c_int32),
                 ("lobpcg_maxit", C.c_int32), ("lobpcg_tol", C.c_double), ("seed", C.c_uint64),
-                ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32)]
+                ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32),
+                ("use_graph", C.c_int32)]
 
 
 class Sizes(C.Structure):

@@ -31,7 +31,19 @@ int guarded(F &&f) {
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 }  // namespace
 
+void geneo_ctx::drop_graph() {
+  if (pcg_exec) cudaGraphExecDestroy(pcg_exec);
+  pcg_exec = nullptr;
+  pcg_key = -1;
+  for (auto &p : g_ev_local) ev_free.insert(ev_free.end(), {p.first, p.second});
+  for (auto &p : g_ev_coarse) ev_free.insert(ev_free.end(), {p.first, p.second});
+  g_ev_local.clear();
+  g_ev_coarse.clear();
+}
+
 geneo_ctx::~geneo_ctx() {
+  drop_graph();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   for (auto &p : ev_local) ev_free.insert(ev_free.end(), {p.first, p.second});
   for (auto &p : ev_coarse) ev_free.insert(ev_free.end(), {p.first, p.second});
   for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
@@ -63,6 +75,7 @@ void geneo_default_options(geneo_options *o) {
   o->lobpcg_maxit = 200;
   o->lobpcg_tol = 1e-8;
   o->seed = 1;
+  o->use_graph = 1;
 }
 
 int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **out) {
@@ -90,8 +103,9 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
     return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
   if (o.lobpcg_block < 1 || o.lobpcg_block > 16 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
     return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");
-  if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0)
-    return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor options");
+  if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
+      (o.use_graph != 0 && o.use_graph != 1))
+    return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
   return guarded([&]() {
     auto c = new geneo_ctx();
     try {
@@ -115,6 +129,7 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
       GENEO_CUDA(cudaGetDevice(&c->device));
       c->sm_count = geneo::device_sm_count();
       GENEO_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      GENEO_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
       geneo::setup_all(c);
     } catch (...) {
       delete c;
@@ -254,8 +269,12 @@ int geneo_profile_read(geneo_ctx *c, geneo_profile *o) {
       v.clear();
       return k;
     };
-    o->local_symv_launches = sum(c->ev_local, o->local_symv_ms);
-    o->coarse_symv_launches = sum(c->ev_coarse, o->coarse_symv_ms);
+    o->local_symv_launches = sum(c->ev_local, o->local_symv_ms) + c->acc_local_n;
+    o->coarse_symv_launches = sum(c->ev_coarse, o->coarse_symv_ms) + c->acc_coarse_n;
+    o->local_symv_ms += c->acc_local_ms;
+    o->coarse_symv_ms += c->acc_coarse_ms;
+    c->acc_local_ms = c->acc_coarse_ms = 0;
+    c->acc_local_n = c->acc_coarse_n = 0;
     o->local_symv_bytes = c->loc.ntiles * (int64_t)geneo::kTileElems *
                           (c->local_prec == GENEO_PREC_FP32 ? (int64_t)sizeof(float)
                                                             : (int64_t)sizeof(double));

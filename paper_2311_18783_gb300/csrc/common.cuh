@@ -80,6 +80,17 @@ struct DevBuf {
   int64_t bytes() const { return n * (int64_t)sizeof(T); }
 };
 
+// Event record that also works while the stream is being captured into a
+// CUDA graph (it then becomes an event record node fired at every replay).
+inline void record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  GENEO_CUDA(cudaStreamIsCapturing(s, &st));
+  if (st == cudaStreamCaptureStatusActive)
+    GENEO_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+  else
+    GENEO_CUDA(cudaEventRecord(e, s));
+}
+
 inline unsigned grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;

@@ -82,6 +82,20 @@ struct geneo_ctx {
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_local, ev_coarse;
   cudaEvent_t ev_take();
+  // totals harvested from graph replays (the graph owns its event pairs)
+  double acc_local_ms = 0, acc_coarse_ms = 0;
+  int64_t acc_local_n = 0, acc_coarse_n = 0;
+
+  // CUDA graph of one PCG iteration (preconditioner, p update, A p, x/r
+  // update, dots, scalar read-back), rebuilt when the local precision or the
+  // profiling switch changes
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  int pcg_key = -1;
+  int64_t pcg_graph_launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev_local, g_ev_coarse;
+  geneo::DevBuf<double> p_x;
+  void drop_graph();
 
   ~geneo_ctx();
 };

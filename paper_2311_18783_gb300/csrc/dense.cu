@@ -677,11 +677,11 @@ void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  if (ev_before) GENEO_CUDA(cudaEventRecord(ev_before, s));
+  if (ev_before) record_event(ev_before, s);
   k_symv_strips<T, NST, D><<<b.sched_ctas, 256, smem, s>>>(
       data, b.d_toff.p, b.d_voff.p, b.d_strip_m.p, b.d_strip_I.p, b.d_cta_off.p, x, b.rowpart.p,
       b.colpart.p, d_err);
-  if (ev_after) GENEO_CUDA(cudaEventRecord(ev_after, s));
+  if (ev_after) record_event(ev_after, s);
   const int64_t nblocks = b.vlen / kTile;
   k_symv_reduce<<<(unsigned)nblocks, kTile, 0, s>>>(b.d_vrow_m.p, b.d_vrow_I.p, b.d_nt.p,
                                                     b.d_toff.p, b.d_voff.p, b.rowpart.p,

@@ -723,6 +723,7 @@ void setup_all(geneo_ctx *c) {
   c->loc_x.alloc(c->loc.vlen);
   c->loc_y.alloc(c->loc.vlen);
   c->scal.alloc(16);
+  c->p_x.alloc(c->topo.ndofs());
   c->scal.zero(s);
   c->partials.alloc(1024);
   GENEO_CUDA(cudaMallocHost((void **)&c->h_scal, 16 * sizeof(double)));

@@ -210,9 +210,9 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
     if (c->prof) {
       cudaEvent_t e0 = c->ev_take(), e1 = c->ev_take();
       c->ev_coarse.push_back({e0, e1});
-      GENEO_CUDA(cudaEventRecord(e0, s));
+      record_event(e0, s);
       mf_solve(c, c->crs_x.p, c->crs_y.p, s);
-      GENEO_CUDA(cudaEventRecord(e1, s));
+      record_event(e1, s);
     } else {
       mf_solve(c, c->crs_x.p, c->crs_y.p, s);
     }
@@ -253,6 +253,82 @@ void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t
   GENEO_CHECK_LAUNCH();
 }
 
+// second half of a PCG iteration: z = M^-1 r, rz_new = (r, z), p = z + beta p
+static void pcg_precond_half(geneo_ctx *c, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  double *sc = c->scal.p;
+  apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
+  dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s);
+  c->launches += 2;
+  k_update_p<<<grid_for(n, 256), 256, 0, s>>>(sc, c->p_z.p, c->p_p.p, n);
+  k_shift_rz<<<1, 1, 0, s>>>(sc);
+  GENEO_CHECK_LAUNCH();
+}
+
+// first half: q = A p, alpha = rz / (p, q), x += alpha p, r -= alpha q,
+// rr = (r, r), scalars copied to the pinned host mirror
+static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  double *sc = c->scal.p;
+  spmv(c, c->p_p.p, c->p_q.p, s);
+  dot(c, c->p_p.p, c->p_q.p, n, sc + 1, s);
+  c->launches += 1;
+  k_update_xr<<<grid_for(n, 256), 256, 0, s>>>(sc, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
+  dot(c, c->p_r.p, c->p_r.p, n, sc + 2, s);
+  GENEO_CUDA(cudaMemcpyAsync(c->h_scal, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GENEO_CHECK_LAUNCH();
+}
+
+// Captures [second half ; first half] of an iteration on the context's
+// capture stream, with x = p_x; replayed on the caller's stream for every
+// iteration after the first.
+static void ensure_pcg_graph(geneo_ctx *c) {
+  const int key = c->local_prec * 2 + (c->prof ? 1 : 0);
+  if (c->pcg_exec && c->pcg_key == key) return;
+  c->drop_graph();
+  const int64_t l0 = c->launches;
+  const size_t nl = c->ev_local.size(), nc = c->ev_coarse.size();
+  cudaStream_t cs = c->cap_stream;
+  GENEO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t graph = nullptr;
+  try {
+    pcg_precond_half(c, cs);
+    pcg_step_half(c, c->p_x.p, cs);
+  } catch (...) {
+    cudaStreamEndCapture(cs, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    c->launches = l0;
+    throw;
+  }
+  GENEO_CUDA(cudaStreamEndCapture(cs, &graph));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  GENEO_CUDA(e);
+  c->pcg_exec = exec;
+  c->pcg_key = key;
+  c->pcg_graph_launches = c->launches - l0;
+  c->launches = l0;
+  // event pairs recorded by the graph's nodes belong to the graph
+  c->g_ev_local.assign(c->ev_local.begin() + nl, c->ev_local.end());
+  c->ev_local.resize(nl);
+  c->g_ev_coarse.assign(c->ev_coarse.begin() + nc, c->ev_coarse.end());
+  c->ev_coarse.resize(nc);
+}
+
+static void harvest_graph_events(geneo_ctx *c) {
+  auto add = [](std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, double &ms, int64_t &k) {
+    for (auto &p : v) {
+      float t = 0;
+      GENEO_CUDA(cudaEventElapsedTime(&t, p.first, p.second));
+      ms += t;
+      ++k;
+    }
+  };
+  add(c->g_ev_local, c->acc_local_ms, c->acc_local_n);
+  add(c->g_ev_coarse, c->acc_coarse_ms, c->acc_coarse_n);
+}
+
 int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_solve_info *info,
         cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -260,7 +336,9 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
   double *sc = c->scal.p;
   double *hs = c->h_scal;
   const unsigned g = grid_for(n, 256);
-  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  const bool graph = c->opt.use_graph != 0;
+  double *xw = graph ? c->p_x.p : x;  // the graph is built on the context's own x
+  GENEO_CUDA(cudaMemsetAsync(xw, 0, sizeof(double) * n, s));
   c->launches += 2;
   k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
   dot(c, b, b, n, sc + 4, s);
@@ -277,13 +355,19 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
     rel = 0.0;
   } else {
     for (it = 1; it <= maxit; ++it) {
-      spmv(c, c->p_p.p, c->p_q.p, s);
-      dot(c, c->p_p.p, c->p_q.p, n, sc + 1, s);
-      c->launches += 1;
-      k_update_xr<<<g, 256, 0, s>>>(sc, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
-      dot(c, c->p_r.p, c->p_r.p, n, sc + 2, s);
-      GENEO_CUDA(cudaMemcpyAsync(hs, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      const bool replay = graph && it > 1;
+      if (it == 1) {
+        pcg_step_half(c, xw, s);
+      } else if (replay) {
+        ensure_pcg_graph(c);
+        GENEO_CUDA(cudaGraphLaunch(c->pcg_exec, s));
+        c->launches += c->pcg_graph_launches;
+      } else {
+        pcg_precond_half(c, s);
+        pcg_step_half(c, xw, s);
+      }
       GENEO_CUDA(cudaStreamSynchronize(s));
+      if (replay && c->prof) harvest_graph_events(c);
       if (!(hs[1] > 0.0) || !std::isfinite(hs[1]) || !std::isfinite(hs[2])) {
         status = GENEO_ERR_BREAKDOWN;
         break;
@@ -293,14 +377,13 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
         status = GENEO_OK;
         break;
       }
-      apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
-      dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s);
-      c->launches += 2;
-      k_update_p<<<g, 256, 0, s>>>(sc, c->p_z.p, c->p_p.p, n);
-      k_shift_rz<<<1, 1, 0, s>>>(sc);
-      GENEO_CHECK_LAUNCH();
     }
     if (it > maxit) it = maxit;
+  }
+  if (xw != x) {
+    c->launches += 1;
+    k_copy<<<g, 256, 0, s>>>(xw, x, n);
+    GENEO_CHECK_LAUNCH();
   }
   GENEO_CUDA(cudaStreamSynchronize(s));
   check_device_error(c, s);
