@@ -174,6 +174,23 @@ int geneo_solve(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol, 
 int geneo_solve_host(geneo_ctx *ctx, const double *b_host, double *x_host, double tol,
                      int32_t maxit, geneo_solve_info *info, void *stream);
 
+/* Block right-hand sides: nrhs (1..16) columns stored one after another,
+ * R_dev/Z_dev device [nrhs][n].  Z = M^-1_AS,2 R column by column; every
+ * stage runs once for all columns (local factors and coarse factor tiles are
+ * read once per column block where the kernel allows).  Column j equals the
+ * single-column result bit for bit. */
+int geneo_apply_preconditioner_block(geneo_ctx *ctx, const double *R_dev, double *Z_dev,
+                                     int32_t nrhs, void *stream);
+
+/* nrhs independent PCG solves (Sec. 2: A SPD, M^-1_AS,2 symmetric) sharing
+ * the operator, B_dev/X_dev device [nrhs][n].  Each column stops at its own
+ * ||r_j|| <= tol ||b_j|| and is frozen while the others continue; column j
+ * equals geneo_solve on b_j bit for bit.  info (host, may be NULL) holds nrhs
+ * entries.  Returns OK if every column converged, else NOT_CONVERGED or
+ * BREAKDOWN (the worst). */
+int geneo_solve_block(geneo_ctx *ctx, const double *B_dev, double *X_dev, int32_t nrhs,
+                      double tol, int32_t maxit, geneo_solve_info *info, void *stream);
+
 /* Selects the local factors used by later solves when the context holds
  * both: GENEO_PREC_FP64 (explicit float64 inverses) or GENEO_PREC_FP32 (the
  * split C_j + G_j S_j^-1 G_j^T, built when options.precision was FP32; the

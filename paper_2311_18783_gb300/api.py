@@ -84,6 +84,10 @@ _SIGS = {
                               C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                    C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_apply_preconditioner_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
+                                                   C.c_int32, C.c_void_p]),
+    "geneo_solve_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                    C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_export": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64,
                                C.POINTER(C.c_int64)]),
     "geneo_use_precision": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -225,6 +229,21 @@ class Solver:
                                      _stream(stream)))
         return {"status": st, "iters": info.iters, "relres": info.relres,
                 "seconds": info.seconds}
+
+    def apply_preconditioner_block(self, R, Z, stream=None):
+        """R, Z: CUDA float64 tensors [nrhs, n] (contiguous)."""
+        _check(_LIB.geneo_apply_preconditioner_block(self._ctx, _ptr(R), _ptr(Z), R.shape[0],
+                                                     _stream(stream)))
+        return Z
+
+    def solve_block(self, B, X, tol=1e-8, maxit=1000, stream=None):
+        """B, X: CUDA float64 tensors [nrhs, n]; returns the status and one
+        info dict per column."""
+        k = B.shape[0]
+        info = (SolveInfo * k)()
+        st = _check(_LIB.geneo_solve_block(self._ctx, _ptr(B), _ptr(X), k, tol, maxit, info,
+                                           _stream(stream)))
+        return st, [{"iters": i.iters, "relres": i.relres, "seconds": i.seconds} for i in info]
 
     def solve_host(self, b, tol=1e-8, maxit=1000, stream=None, out=None):
         """b: host float64 array [n] (pinned tensors are fastest).  Returns x."""

@@ -29,6 +29,7 @@ int guarded(F &&f) {
 }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+constexpr int kMaxRhs = 16;
 }  // namespace
 
 void geneo_ctx::drop_graph() {
@@ -48,6 +49,7 @@ geneo_ctx::~geneo_ctx() {
   for (auto &p : ev_coarse) ev_free.insert(ev_free.end(), {p.first, p.second});
   for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
   if (h_scal) cudaFreeHost(h_scal);
+  if (h_act) cudaFreeHost(h_act);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -214,6 +216,26 @@ int geneo_solve(geneo_ctx *c, const double *b, double *x, double tol, int32_t ma
   if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded([&]() { return geneo::pcg(c, b, x, tol, maxit, info, as_stream(s)); });
+}
+
+int geneo_apply_preconditioner_block(geneo_ctx *c, const double *r, double *z, int32_t nrhs,
+                                     void *s) {
+  if (!c || !r || !z) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1 || nrhs > kMaxRhs) return fail(GENEO_ERR_INVALID_ARG, "nrhs must be in 1..16");
+  return guarded([&]() {
+    geneo::reserve_rhs(c, nrhs);
+    geneo::apply_preconditioner(c, r, z, as_stream(s), nrhs);
+    return GENEO_OK;
+  });
+}
+
+int geneo_solve_block(geneo_ctx *c, const double *b, double *x, int32_t nrhs, double tol,
+                      int32_t maxit, geneo_solve_info *info, void *s) {
+  if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1 || nrhs > kMaxRhs) return fail(GENEO_ERR_INVALID_ARG, "nrhs must be in 1..16");
+  if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
+  return guarded(
+      [&]() { return geneo::pcg(c, b, x, tol, maxit, info, as_stream(s), nrhs); });
 }
 
 int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int32_t maxit,

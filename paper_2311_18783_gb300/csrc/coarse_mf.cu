@@ -122,10 +122,13 @@ __global__ void k_extend_add(const int32_t *__restrict__ it_child, const int32_t
 __global__ void k_mf_gather(const int32_t *__restrict__ rf, const int32_t *__restrict__ rl,
                             const int64_t *__restrict__ gptr, const int64_t *__restrict__ gidx,
                             const int64_t *__restrict__ first, const int32_t *__restrict__ npiv,
-                            const int64_t *__restrict__ voff, int64_t nrows,
-                            const double *__restrict__ cpos, double *__restrict__ w) {
+                            const int64_t *__restrict__ voff, int64_t nrows, int64_t n0,
+                            int64_t vlen, const double *__restrict__ cpos,
+                            double *__restrict__ w) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= nrows) return;
+  cpos += blockIdx.y * n0;  // right-hand side blockIdx.y
+  w += blockIdx.y * vlen;
   const int f = rf[q], l = rl[q];
   double v = l < npiv[f] ? cpos[first[f] + l] : 0.0;
   for (int64_t k = gptr[q]; k < gptr[q + 1]; ++k) v += w[gidx[k]];
@@ -155,11 +158,25 @@ struct MfArgs {
   const double *T;
   double *wbuf, *ybuf, *tbuf, *xpos, *part;
   int32_t *cnt;
+  // right-hand sides: k columns, column strides of the buffers above
+  int k;
+  int64_t ldv, ldx, ldp, ldc;
 };
 
+// blockIdx.x = task * k + column: the k columns of a task run in adjacent
+// CTAs, so its tiles are read from DRAM once and from L2 for the others
 template <int kMode>
 __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tasks, MfArgs a) {
-  const MfTask tk = tasks[blockIdx.x];
+  const MfTask tk = tasks[blockIdx.x / a.k];
+  {
+    const int64_t col = blockIdx.x % a.k;
+    a.wbuf += col * a.ldv;
+    a.ybuf += col * a.ldv;
+    a.tbuf += col * a.ldv;
+    a.xpos += col * a.ldx;
+    a.part += col * a.ldp;
+    a.cnt += col * a.ldc;
+  }
   const int f = tk.f, O = tk.I;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __shared__ double red[8][kTile];
@@ -254,6 +271,8 @@ __global__ void k_perm(const int64_t *__restrict__ idx, const double *__restrict
                        double *__restrict__ dst, int64_t n, int to_pos) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= n) return;
+  src += blockIdx.y * n;
+  dst += blockIdx.y * n;
   if (to_pos) dst[idx[a]] = src[a];
   else dst[a] = src[idx[a]];
 }
@@ -275,8 +294,9 @@ struct MfLevel {
 struct Multifrontal {
   int nfront = 0;
   TileBatch fb;
-  DevBuf<double> L, Y, dinv, wbuf, ybuf, tbuf, cpos, xpos, part;
+  DevBuf<double> L, Y, dinv, wbuf, ybuf, tbuf, cpos, xpos, part;  // solve buffers: kcap columns
   DevBuf<int32_t> cnt;
+  int kcap = 0, nslot = 0, ncnt = 0;
   DevBuf<int64_t> dtoff, first, nupd, uoff, upos, pos;
   DevBuf<int32_t> npiv, npivp, npivt, parent, nt;
   std::vector<MfLevel> levels;
@@ -578,9 +598,8 @@ void mf_setup(geneo_ctx *c) {
     Lv.gidx.upload(gi, s);
     Lv.nrows = (int64_t)rf.size();
   }
-  M->part.alloc((int64_t)std::max(1, nslot) * kTile);
-  M->cnt.alloc(std::max(1, ncnt));
-  M->cnt.zero(s);
+  M->nslot = std::max(1, nslot);
+  M->ncnt = std::max(1, ncnt);
   // --- numeric factorisation, level by level
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M->levels[lv];
@@ -599,46 +618,61 @@ void mf_setup(geneo_ctx *c) {
   for (int f = 0; f < nf; ++f) maxpt = std::max(maxpt, h_npivt[f]);
   pivot_block_inverse(fb, M->L.p, M->Y.p, M->dinv.p, M->dtoff.p, M->npivt.p, maxpt, s);
   check_device_error(c, s);
-  M->wbuf.alloc(fb.vlen);
-  M->ybuf.alloc(fb.vlen);
-  M->tbuf.alloc(fb.vlen);
-  M->wbuf.zero(s);
-  M->ybuf.zero(s);
-  M->tbuf.zero(s);
-  M->cpos.alloc(n0);
-  M->xpos.alloc(n0);
+  mf_reserve(c, 1);
   M->factor_bytes = M->L.bytes() + M->Y.bytes();
   GENEO_CUDA(cudaStreamSynchronize(s));
 }
 
+// solve buffers for k right-hand-side columns
+void mf_reserve(geneo_ctx *c, int k) {
+  Multifrontal &M = *c->mf;
+  if (k <= M.kcap) return;
+  cudaStream_t s = c->stream;
+  const int64_t vlen = M.fb.vlen, n0 = c->n0;
+  M.wbuf.alloc(vlen * k);
+  M.ybuf.alloc(vlen * k);
+  M.tbuf.alloc(vlen * k);
+  M.wbuf.zero(s);
+  M.ybuf.zero(s);
+  M.tbuf.zero(s);
+  M.cpos.alloc(n0 * k);
+  M.xpos.alloc(n0 * k);
+  M.part.alloc((int64_t)M.nslot * kTile * k);
+  M.cnt.alloc((int64_t)M.ncnt * k);
+  M.cnt.zero(s);
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  M.kcap = k;
+}
+
 int64_t mf_factor_bytes(const geneo_ctx *c) { return c->mf ? c->mf->factor_bytes : 0; }
 
-// y (column order, n0) = E^-1 t
-void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s) {
+// y (column order, n0 per column, k columns) = E^-1 t
+void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {
   Multifrontal &M = *c->mf;
   TileBatch &fb = M.fb;
   const int64_t n0 = c->n0;
-  k_perm<<<grid_for(n0, 256), 256, 0, s>>>(M.pos.p, t, M.cpos.p, n0, 1);
+  if (k > M.kcap) throw Error(GENEO_ERR_STATE, "internal: coarse solve buffers too small");
+  k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, t, M.cpos.p, n0, 1);
   MfArgs al{M.npivt.p, M.npiv.p, M.npivp.p, M.nupd.p, M.first.p, M.uoff.p, M.upos.p,
             fb.d_toff.p, fb.d_voff.p, M.L.p, M.wbuf.p, M.ybuf.p, M.tbuf.p, M.xpos.p,
-            M.part.p, M.cnt.p};
+            M.part.p, M.cnt.p, k, fb.vlen, n0, (int64_t)M.nslot * kTile, M.ncnt};
   MfArgs ay = al;
   ay.T = M.Y.p;
   const int nlev = (int)M.levels.size();
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M.levels[lv];
-    k_mf_gather<<<grid_for(Lv.nrows, 256), 256, 0, s>>>(Lv.rf.p, Lv.rl.p, Lv.gptr.p, Lv.gidx.p,
-                                                         M.first.p, M.npiv.p, fb.d_voff.p,
-                                                         Lv.nrows, M.cpos.p, M.wbuf.p);
-    if (Lv.ntask[0]) k_mf_tiles<0><<<Lv.ntask[0], 256, 0, s>>>(Lv.task[0].p, ay);
-    if (Lv.ntask[1]) k_mf_tiles<1><<<Lv.ntask[1], 256, 0, s>>>(Lv.task[1].p, al);
+    k_mf_gather<<<dim3(grid_for(Lv.nrows, 256), k), 256, 0, s>>>(
+        Lv.rf.p, Lv.rl.p, Lv.gptr.p, Lv.gidx.p, M.first.p, M.npiv.p, fb.d_voff.p, Lv.nrows, n0,
+        fb.vlen, M.cpos.p, M.wbuf.p);
+    if (Lv.ntask[0]) k_mf_tiles<0><<<Lv.ntask[0] * k, 256, 0, s>>>(Lv.task[0].p, ay);
+    if (Lv.ntask[1]) k_mf_tiles<1><<<Lv.ntask[1] * k, 256, 0, s>>>(Lv.task[1].p, al);
   }
   for (int lv = nlev - 1; lv >= 0; --lv) {
     MfLevel &Lv = M.levels[lv];
-    if (Lv.ntask[2]) k_mf_tiles<2><<<Lv.ntask[2], 256, 0, s>>>(Lv.task[2].p, al);
-    if (Lv.ntask[3]) k_mf_tiles<3><<<Lv.ntask[3], 256, 0, s>>>(Lv.task[3].p, ay);
+    if (Lv.ntask[2]) k_mf_tiles<2><<<Lv.ntask[2] * k, 256, 0, s>>>(Lv.task[2].p, al);
+    if (Lv.ntask[3]) k_mf_tiles<3><<<Lv.ntask[3] * k, 256, 0, s>>>(Lv.task[3].p, ay);
   }
-  k_perm<<<grid_for(n0, 256), 256, 0, s>>>(M.pos.p, M.xpos.p, y, n0, 0);
+  k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, M.xpos.p, y, n0, 0);
   GENEO_CHECK_LAUNCH();
 }
 

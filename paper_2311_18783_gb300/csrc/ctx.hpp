@@ -97,5 +97,10 @@ struct geneo_ctx {
   geneo::DevBuf<double> p_x;
   void drop_graph();
 
+  // right-hand-side columns the work buffers hold; PCG column mask
+  int kcap = 0;
+  geneo::DevBuf<int> d_act;
+  int *h_act = nullptr;
+
   ~geneo_ctx();
 };

@@ -1108,15 +1108,18 @@ void build_split_factors(geneo_ctx *c) {
 
 // yl += G_j S_j^-1 G_j^T xl for every subdomain (float64 gradient part of the
 // split local inverse), on padded local vectors
-void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s) {
+void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k) {
   XiOp &op = *c->xi;
-  k_gt<<<grid_for(op.nv, 256), 256, 0, s>>>(op.sptr.p, op.srow.p, op.ssgn.p, op.vslot_sub.p,
-                                            op.xvoff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nv, 1,
-                                            op.vlen, op.vlenS, xl, op.u1.p);
-  symv_batch<double>(op.sb, op.s_inv.p, op.u1.p, op.u2.p, c->d_err.p, s);
-  k_g<<<grid_for(op.nslots, 256), 256, 0, s>>>(op.ghead.p, op.gtail.p, op.slot_sub.p, op.Noff.p,
-                                               c->loc.d_voff.p, op.sb.d_voff.p, op.nslots, 1,
-                                               op.vlen, op.vlenS, op.u2.p, nullptr, yl, 2);
+  k_gt<<<grid_for(op.nv * k, 256), 256, 0, s>>>(op.sptr.p, op.srow.p, op.ssgn.p, op.vslot_sub.p,
+                                                op.xvoff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nv,
+                                                k, op.vlen, op.vlenS, xl, op.u1.p);
+  for (int j = 0; j < k; ++j)
+    symv_batch<double>(op.sb, op.s_inv.p, op.u1.p + j * op.vlenS, op.u2.p + j * op.vlenS,
+                       c->d_err.p, s);
+  k_g<<<grid_for(op.nslots * k, 256), 256, 0, s>>>(op.ghead.p, op.gtail.p, op.slot_sub.p,
+                                                   op.Noff.p, c->loc.d_voff.p, op.sb.d_voff.p,
+                                                   op.nslots, k, op.vlen, op.vlenS, op.u2.p,
+                                                   nullptr, yl, 2);
   GENEO_CHECK_LAUNCH();
 }
 

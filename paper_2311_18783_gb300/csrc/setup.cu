@@ -716,17 +716,9 @@ void setup_all(geneo_ctx *c) {
     c->crs_x.zero(s);
   }
 
-  // --- work vectors
-  for (auto *v : {&c->v_y0, &c->v_s, &c->v_w, &c->v_t, &c->v_c, &c->p_r, &c->p_z, &c->p_p, &c->p_q,
-                  &c->h_b, &c->h_x})
-    v->alloc(n);
-  c->loc_x.alloc(c->loc.vlen);
-  c->loc_y.alloc(c->loc.vlen);
-  c->scal.alloc(16);
-  c->p_x.alloc(c->topo.ndofs());
-  c->scal.zero(s);
-  c->partials.alloc(1024);
-  GENEO_CUDA(cudaMallocHost((void **)&c->h_scal, 16 * sizeof(double)));
+  // --- work vectors (one right-hand side; grown on demand)
+  for (auto *v : {&c->h_b, &c->h_x}) v->alloc(n);
+  reserve_rhs(c, 1);
   check_device_error(c, s);
   c->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -52,19 +52,23 @@ void build_xi_operator(geneo_ctx *c, XiOp &op, cudaStream_t s);
 // float32 C_j = (I - xi_j) A_j^-1 of every subdomain (needs the float64 inverse)
 void build_split_factors(geneo_ctx *c);
 // yl += G_j S_j^-1 G_j^T xl, float64 gradient part of the split local solve
-void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s);
+void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k = 1);
 
 // multifrontal coarse factor: set-up, solve y = E^-1 t (column order), sizes
 void mf_setup(geneo_ctx *c);
-void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s);
+void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k = 1);
+void mf_reserve(geneo_ctx *c, int k);
 int mf_launches_per_solve(const geneo_ctx *c);
 int64_t mf_factor_bytes(const geneo_ctx *c);
 
-void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s);
-void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s);
-void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s);
-void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s);
+// Solve path; k right-hand sides stored as k consecutive columns of length n
+// (local vectors: columns of loc.vlen).
+void reserve_rhs(geneo_ctx *c, int k);
+void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k = 1);
+void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k = 1);
+void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k = 1);
+void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k = 1);
 int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_solve_info *info,
-        cudaStream_t s);
+        cudaStream_t s, int k = 1);
 
 }  // namespace geneo

@@ -15,6 +15,8 @@ namespace geneo {
 __global__ void k_spmv(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                        const double *__restrict__ val, const double *__restrict__ x,
                        double *__restrict__ y, int64_t n) {
+  x += blockIdx.y * n;  // right-hand side blockIdx.y (columns of length n)
+  y += blockIdx.y * n;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt >> 3;
   const int lane = threadIdx.x & 7;
@@ -31,6 +33,9 @@ __global__ void k_spmv(const int32_t *__restrict__ rowptr, const int32_t *__rest
 __global__ void k_residual(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ x,
                            const double *__restrict__ b, double *__restrict__ y, int64_t n) {
+  x += blockIdx.y * n;
+  b += blockIdx.y * n;
+  y += blockIdx.y * n;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt >> 3;
   const int lane = threadIdx.x & 7;
@@ -45,18 +50,23 @@ __global__ void k_residual(const int32_t *__restrict__ rowptr, const int32_t *__
 
 // padded local vector x_loc[p] = s[l2g[p]] (0 on padding)
 __global__ void k_restrict(const int32_t *__restrict__ l2g, const double *__restrict__ s,
-                           double *__restrict__ xl, int64_t len) {
+                           double *__restrict__ xl, int64_t len, int64_t n) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= len) return;
+  s += blockIdx.y * n;
+  xl += blockIdx.y * len;
   const int32_t g = l2g[p];
   xl[p] = g >= 0 ? s[g] : 0.0;
 }
 
 // w[e] = sum over the local slots holding e (deterministic gather-sum)
 __global__ void k_prolong(const int64_t *__restrict__ ptr, const int64_t *__restrict__ slot,
-                          const double *__restrict__ yl, double *__restrict__ w, int64_t n) {
+                          const double *__restrict__ yl, double *__restrict__ w, int64_t n,
+                          int64_t len) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
+  yl += blockIdx.y * len;
+  w += blockIdx.y * n;
   double s = 0;
   for (int64_t k = ptr[e]; k < ptr[e + 1]; ++k) s += yl[slot[k]];
   w[e] = s;
@@ -66,10 +76,12 @@ __global__ void k_prolong(const int64_t *__restrict__ ptr, const int64_t *__rest
 // have a few entries, GenEO columns one per dof of their subdomain
 __global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zrow,
                      const double *__restrict__ zval, const double *__restrict__ r,
-                     double *__restrict__ t, int64_t n0) {
+                     double *__restrict__ t, int64_t n0, int64_t n) {
   const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int l = threadIdx.x & 31;
   if (a >= n0) return;
+  r += blockIdx.y * n;
+  t += blockIdx.y * n0;
   double s = 0;
   for (int64_t k = zptr[a] + l; k < zptr[a + 1]; k += 32) s = fma(zval[k], r[zrow[k]], s);
 #pragma unroll
@@ -80,9 +92,11 @@ __global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict
 // y[e] = (Z u)_e, one row per thread (CSR)
 __global__ void k_z(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zcol,
                     const double *__restrict__ zval, const double *__restrict__ u,
-                    double *__restrict__ y, int64_t n) {
+                    double *__restrict__ y, int64_t n, int64_t n0) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
+  u += blockIdx.y * n0;
+  y += blockIdx.y * n;
   double s = 0;
   for (int64_t k = zptr[e]; k < zptr[e + 1]; ++k) s = fma(zval[k], u[zcol[k]], s);
   y[e] = s;
@@ -92,17 +106,22 @@ __global__ void k_z(const int64_t *__restrict__ zptr, const int32_t *__restrict_
 __global__ void k_combine(const double *__restrict__ y0, const double *__restrict__ w,
                           const double *__restrict__ c, double *__restrict__ z, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) z[i] = (y0[i] + w[i]) - c[i];
+  const int64_t o = blockIdx.y * n;
+  if (i < n) z[o + i] = (y0[o + i] + w[o + i]) - c[o + i];
 }
 
 // ---------------------------------------------------------------------------
 // deterministic dot products: fixed grid, block partials, one final block
 
 constexpr int kDotBlocks = 512;
+constexpr int kScal = 8;  // PCG scalars per right-hand side
 
 __global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
                               double *__restrict__ part) {
   __shared__ double sh[256];
+  a += blockIdx.y * n;
+  b += blockIdx.y * n;
+  part += blockIdx.y * gridDim.x;
   double s = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -117,8 +136,11 @@ __global__ void k_dot_partial(const double *__restrict__ a, const double *__rest
   }
 }
 
+// one block per column; out[column * kScal]
 __global__ void k_dot_final(const double *__restrict__ part, int np, double *__restrict__ out) {
   __shared__ double sh[32];
+  part += blockIdx.x * np;
+  out += blockIdx.x * kScal;
   double s = 0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -132,158 +154,209 @@ __global__ void k_dot_final(const double *__restrict__ part, int np, double *__r
 }
 
 static void dot(geneo_ctx *c, const double *a, const double *b, int64_t n, double *out,
-                cudaStream_t s) {
+                cudaStream_t s, int k = 1) {
   c->launches += 2;
-  k_dot_partial<<<kDotBlocks, 256, 0, s>>>(a, b, n, c->partials.p);
-  k_dot_final<<<1, 256, 0, s>>>(c->partials.p, kDotBlocks, out);
+  k_dot_partial<<<dim3(kDotBlocks, k), 256, 0, s>>>(a, b, n, c->partials.p);
+  k_dot_final<<<k, 256, 0, s>>>(c->partials.p, kDotBlocks, out);
 }
-
-// scalars: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 bb
+// scalars per column c at sc[c * kScal]: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 bb;
+// act[c] = 0 freezes a converged column
 // x += alpha p ; r -= alpha q  with alpha = rz / pq
-__global__ void k_update_xr(const double *__restrict__ sc, const double *__restrict__ p,
-                            const double *__restrict__ q, double *__restrict__ x,
-                            double *__restrict__ r, int64_t n) {
+__global__ void k_update_xr(const double *__restrict__ sc, const int *__restrict__ act,
+                            const double *__restrict__ p, const double *__restrict__ q,
+                            double *__restrict__ x, double *__restrict__ r, int64_t n) {
+  if (!act[blockIdx.y]) return;
+  sc += blockIdx.y * kScal;
+  const int64_t o = blockIdx.y * n;
   const double alpha = sc[0] / sc[1];
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
-    x[i] = fma(alpha, p[i], x[i]);
-    r[i] = fma(-alpha, q[i], r[i]);
+    x[o + i] = fma(alpha, p[o + i], x[o + i]);
+    r[o + i] = fma(-alpha, q[o + i], r[o + i]);
   }
 }
 
-// p = z + beta p with beta = rz_new / rz; then rz = rz_new
-__global__ void k_update_p(double *__restrict__ sc, const double *__restrict__ z,
-                           double *__restrict__ p, int64_t n) {
+// p = z + beta p with beta = rz_new / rz
+__global__ void k_update_p(const double *__restrict__ sc, const int *__restrict__ act,
+                           const double *__restrict__ z, double *__restrict__ p, int64_t n) {
+  if (!act[blockIdx.y]) return;
+  sc += blockIdx.y * kScal;
+  const int64_t o = blockIdx.y * n;
   const double beta = sc[3] / sc[0];
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = fma(beta, p[i], z[i]);
+  if (i < n) p[o + i] = fma(beta, p[o + i], z[o + i]);
 }
 
-__global__ void k_shift_rz(double *sc) { sc[0] = sc[3]; }
+// rz = rz_new, one thread per column
+__global__ void k_shift_rz(double *sc, int k) {
+  const int c = threadIdx.x;
+  if (c < k) sc[c * kScal] = sc[c * kScal + 3];
+}
 
 __global__ void k_copy(const double *__restrict__ a, double *__restrict__ b, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = a[i];
+  const int64_t o = blockIdx.y * n;
+  if (i < n) b[o + i] = a[o + i];
 }
 
 // ---------------------------------------------------------------------------
+// Work buffers for k right-hand-side columns (column c of a vector of length
+// len at offset c * len).  Growing them invalidates the captured graph.
 
-void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s) {
+void reserve_rhs(geneo_ctx *c, int k) {
+  if (k <= c->kcap) return;
+  c->drop_graph();
+  cudaStream_t s = c->stream;
+  const int64_t n = c->topo.ndofs();
+  for (auto *v : {&c->v_y0, &c->v_s, &c->v_w, &c->v_t, &c->v_c, &c->p_r, &c->p_z, &c->p_p,
+                  &c->p_q, &c->p_x})
+    v->alloc(n * k);
+  c->loc_x.alloc(c->loc.vlen * k);
+  c->loc_y.alloc(c->loc.vlen * k);
+  if (c->n0 > 0) {
+    const int64_t len = c->mf ? c->n0 : c->crs.vlen;
+    c->crs_x.alloc(len * k);
+    c->crs_y.alloc(len * k);
+    c->crs_x.zero(s);
+    if (c->mf) mf_reserve(c, k);
+  }
+  if (c->xi) {
+    c->xi->u1.alloc(c->xi->vlenS * k);
+    c->xi->u2.alloc(c->xi->vlenS * k);
+    c->xi->u1.zero(s);
+    c->xi->u2.zero(s);
+  }
+  c->scal.alloc((int64_t)kScal * k);
+  c->scal.zero(s);
+  c->partials.alloc((int64_t)kDotBlocks * k);
+  c->d_act.alloc(k);
+  if (c->h_scal) GENEO_CUDA(cudaFreeHost(c->h_scal));
+  c->h_scal = nullptr;
+  GENEO_CUDA(cudaMallocHost((void **)&c->h_scal, sizeof(double) * kScal * k));
+  if (c->h_act) GENEO_CUDA(cudaFreeHost(c->h_act));
+  c->h_act = nullptr;
+  GENEO_CUDA(cudaMallocHost((void **)&c->h_act, sizeof(int) * k));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  c->kcap = k;
+}
+
+void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k) {
   const int64_t n = c->topo.ndofs();
   c->launches += 1;
-  k_spmv<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x, y, n);
+  k_spmv<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x,
+                                                       y, n);
   GENEO_CHECK_LAUNCH();
 }
 
-void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s) {
-  const int64_t n = c->topo.ndofs();
-  c->launches += 4;
-  k_restrict<<<grid_for(c->loc.vlen, 256), 256, 0, s>>>(c->d_l2g.p, r, c->loc_x.p, c->loc.vlen);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->prof) {
-    e0 = c->ev_take();
-    e1 = c->ev_take();
-    c->ev_local.push_back({e0, e1});
+void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k) {
+  const int64_t n = c->topo.ndofs(), vlen = c->loc.vlen;
+  c->launches += 2;
+  k_restrict<<<dim3(grid_for(vlen, 256), k), 256, 0, s>>>(c->d_l2g.p, r, c->loc_x.p, vlen, n);
+  for (int j = 0; j < k; ++j) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+      e0 = c->ev_take();
+      e1 = c->ev_take();
+      c->ev_local.push_back({e0, e1});
+    }
+    const double *xj = c->loc_x.p + j * vlen;
+    double *yj = c->loc_y.p + j * vlen;
+    c->launches += 2;
+    if (c->local_prec == GENEO_PREC_FP32)
+      symv_batch<float>(c->loc, c->loc_f32.p, xj, yj, c->d_err.p, s, e0, e1);
+    else
+      symv_batch<double>(c->loc, c->loc_f64.p, xj, yj, c->d_err.p, s, e0, e1);
   }
   if (c->local_prec == GENEO_PREC_FP32) {
     // split inverse: float32 C_j r_j plus the float64 gradient part
-    symv_batch<float>(c->loc, c->loc_f32.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s, e0, e1);
-    split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s);
-    c->launches += 4;
-  } else {
-    symv_batch<double>(c->loc, c->loc_f64.p, c->loc_x.p, c->loc_y.p, c->d_err.p, s, e0, e1);
+    split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s, k);
+    c->launches += 2 + 2 * k;
   }
-  k_prolong<<<grid_for(n, 256), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w, n);
+  k_prolong<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w,
+                                                      n, vlen);
   GENEO_CHECK_LAUNCH();
 }
 
-void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s) {
-  const int64_t n = c->topo.ndofs();
-  if (c->n0 == 0) {
-    GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, s));
+void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k) {
+  const int64_t n = c->topo.ndofs(), n0 = c->n0;
+  if (n0 == 0) {
+    GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n * k, s));
     return;
   }
-  if (c->mf) {
-    c->launches += 2 + mf_launches_per_solve(c);
-    k_zt<<<grid_for(c->n0 * 32, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
-                                              c->crs_x.p, c->n0);
-    if (c->prof) {
-      cudaEvent_t e0 = c->ev_take(), e1 = c->ev_take();
-      c->ev_coarse.push_back({e0, e1});
-      record_event(e0, s);
-      mf_solve(c, c->crs_x.p, c->crs_y.p, s);
-      record_event(e1, s);
-    } else {
-      mf_solve(c, c->crs_x.p, c->crs_y.p, s);
-    }
-    k_z<<<grid_for(n, 256), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p, c->crs_y.p,
-                                         y, n);
-    GENEO_CHECK_LAUNCH();
-    return;
-  }
-  c->launches += 4;
-  k_zt<<<grid_for(c->n0 * 32, 256), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p, c->d_zc_val.p, r,
-                                            c->crs_x.p, c->n0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->prof) {
     e0 = c->ev_take();
     e1 = c->ev_take();
     c->ev_coarse.push_back({e0, e1});
   }
-  symv_batch<double>(c->crs, c->crs_f64.p, c->crs_x.p, c->crs_y.p, c->d_err.p, s, e0, e1);
-  k_z<<<grid_for(n, 256), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p, c->crs_y.p,
-                                       y, n);
+  c->launches += 2;
+  k_zt<<<dim3(grid_for(n0 * 32, 256), k), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p,
+                                                       c->d_zc_val.p, r, c->crs_x.p, n0, n);
+  if (c->mf) {
+    c->launches += mf_launches_per_solve(c);
+    if (e0) record_event(e0, s);
+    mf_solve(c, c->crs_x.p, c->crs_y.p, s, k);
+    if (e1) record_event(e1, s);
+  } else {
+    // explicit dense E^-1, one SYMV per column
+    if (k != 1) throw Error(GENEO_ERR_STATE, "the dense coarse inverse solves one column at a time");
+    c->launches += 2;
+    symv_batch<double>(c->crs, c->crs_f64.p, c->crs_x.p, c->crs_y.p, c->d_err.p, s, e0, e1);
+  }
+  k_z<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p,
+                                                c->crs_y.p, y, n, n0);
   GENEO_CHECK_LAUNCH();
 }
 
-void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s) {
+void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k) {
   const int64_t n = c->topo.ndofs();
   if (c->n0 == 0) {
-    local_solve(c, r, z, s);
+    local_solve(c, r, z, s, k);
     return;
   }
   c->launches += 2;
-  coarse_solve(c, r, c->v_y0.p, s);
-  k_residual<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
-                                                  c->v_y0.p, r, c->v_s.p, n);
-  local_solve(c, c->v_s.p, c->v_w.p, s);
-  spmv(c, c->v_w.p, c->v_t.p, s);
-  coarse_solve(c, c->v_t.p, c->v_c.p, s);
-  k_combine<<<grid_for(n, 256), 256, 0, s>>>(c->v_y0.p, c->v_w.p, c->v_c.p, z, n);
+  coarse_solve(c, r, c->v_y0.p, s, k);
+  k_residual<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
+                                                           c->v_y0.p, r, c->v_s.p, n);
+  local_solve(c, c->v_s.p, c->v_w.p, s, k);
+  spmv(c, c->v_w.p, c->v_t.p, s, k);
+  coarse_solve(c, c->v_t.p, c->v_c.p, s, k);
+  k_combine<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->v_y0.p, c->v_w.p, c->v_c.p, z, n);
   GENEO_CHECK_LAUNCH();
 }
 
 // second half of a PCG iteration: z = M^-1 r, rz_new = (r, z), p = z + beta p
-static void pcg_precond_half(geneo_ctx *c, cudaStream_t s) {
+static void pcg_precond_half(geneo_ctx *c, cudaStream_t s, int k) {
   const int64_t n = c->topo.ndofs();
   double *sc = c->scal.p;
-  apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
-  dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s);
+  apply_preconditioner(c, c->p_r.p, c->p_z.p, s, k);
+  dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s, k);
   c->launches += 2;
-  k_update_p<<<grid_for(n, 256), 256, 0, s>>>(sc, c->p_z.p, c->p_p.p, n);
-  k_shift_rz<<<1, 1, 0, s>>>(sc);
+  k_update_p<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(sc, c->d_act.p, c->p_z.p, c->p_p.p, n);
+  k_shift_rz<<<1, 32, 0, s>>>(sc, k);
   GENEO_CHECK_LAUNCH();
 }
 
 // first half: q = A p, alpha = rz / (p, q), x += alpha p, r -= alpha q,
 // rr = (r, r), scalars copied to the pinned host mirror
-static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s) {
+static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s, int k) {
   const int64_t n = c->topo.ndofs();
   double *sc = c->scal.p;
-  spmv(c, c->p_p.p, c->p_q.p, s);
-  dot(c, c->p_p.p, c->p_q.p, n, sc + 1, s);
+  spmv(c, c->p_p.p, c->p_q.p, s, k);
+  dot(c, c->p_p.p, c->p_q.p, n, sc + 1, s, k);
   c->launches += 1;
-  k_update_xr<<<grid_for(n, 256), 256, 0, s>>>(sc, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
-  dot(c, c->p_r.p, c->p_r.p, n, sc + 2, s);
-  GENEO_CUDA(cudaMemcpyAsync(c->h_scal, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  k_update_xr<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(sc, c->d_act.p, c->p_p.p, c->p_q.p, x,
+                                                         c->p_r.p, n);
+  dot(c, c->p_r.p, c->p_r.p, n, sc + 2, s, k);
+  GENEO_CUDA(cudaMemcpyAsync(c->h_scal, sc, sizeof(double) * kScal * k, cudaMemcpyDeviceToHost, s));
   GENEO_CHECK_LAUNCH();
 }
 
-// Captures [second half ; first half] of an iteration on the context's
-// capture stream, with x = p_x; replayed on the caller's stream for every
-// iteration after the first.
-static void ensure_pcg_graph(geneo_ctx *c) {
-  const int key = c->local_prec * 2 + (c->prof ? 1 : 0);
+// Captures [second half ; first half] of an iteration for k columns on the
+// context's capture stream, with x = p_x; replayed on the caller's stream for
+// every iteration after the first.
+static void ensure_pcg_graph(geneo_ctx *c, int k) {
+  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) << 8) + k;
   if (c->pcg_exec && c->pcg_key == key) return;
   c->drop_graph();
   const int64_t l0 = c->launches;
@@ -292,8 +365,8 @@ static void ensure_pcg_graph(geneo_ctx *c) {
   GENEO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaGraph_t graph = nullptr;
   try {
-    pcg_precond_half(c, cs);
-    pcg_step_half(c, c->p_x.p, cs);
+    pcg_precond_half(c, cs, k);
+    pcg_step_half(c, c->p_x.p, cs, k);
   } catch (...) {
     cudaStreamEndCapture(cs, &graph);
     if (graph) cudaGraphDestroy(graph);
@@ -329,56 +402,74 @@ static void harvest_graph_events(geneo_ctx *c) {
   add(c->g_ev_coarse, c->acc_coarse_ms, c->acc_coarse_n);
 }
 
+// k independent preconditioned CG iterations sharing the operator; a column
+// stops (is frozen) at its own convergence.  info[c] per column.
 int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_solve_info *info,
-        cudaStream_t s) {
+        cudaStream_t s, int k) {
   const auto t0 = std::chrono::steady_clock::now();
+  reserve_rhs(c, k);
   const int64_t n = c->topo.ndofs();
   double *sc = c->scal.p;
   double *hs = c->h_scal;
-  const unsigned g = grid_for(n, 256);
+  int *ha = c->h_act;
+  const dim3 g(grid_for(n, 256), k);
   const bool graph = c->opt.use_graph != 0;
   double *xw = graph ? c->p_x.p : x;  // the graph is built on the context's own x
-  GENEO_CUDA(cudaMemsetAsync(xw, 0, sizeof(double) * n, s));
+  GENEO_CUDA(cudaMemsetAsync(xw, 0, sizeof(double) * n * k, s));
   c->launches += 2;
   k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
-  dot(c, b, b, n, sc + 4, s);
-  apply_preconditioner(c, c->p_r.p, c->p_z.p, s);
+  dot(c, b, b, n, sc + 4, s, k);
+  apply_preconditioner(c, c->p_r.p, c->p_z.p, s, k);
   k_copy<<<g, 256, 0, s>>>(c->p_z.p, c->p_p.p, n);
-  dot(c, c->p_r.p, c->p_z.p, n, sc + 0, s);
-  GENEO_CUDA(cudaMemcpyAsync(hs, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  dot(c, c->p_r.p, c->p_z.p, n, sc + 0, s, k);
+  GENEO_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * kScal * k, cudaMemcpyDeviceToHost, s));
   GENEO_CUDA(cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(hs[4]);
-  int status = GENEO_NOT_CONVERGED, it = 0;
-  double rel = 1.0;
-  if (bnorm == 0.0) {
-    status = GENEO_OK;
-    rel = 0.0;
-  } else {
-    for (it = 1; it <= maxit; ++it) {
-      const bool replay = graph && it > 1;
-      if (it == 1) {
-        pcg_step_half(c, xw, s);
-      } else if (replay) {
-        ensure_pcg_graph(c);
-        GENEO_CUDA(cudaGraphLaunch(c->pcg_exec, s));
-        c->launches += c->pcg_graph_launches;
+  std::vector<double> bnorm(k), rel(k, 1.0);
+  std::vector<int> st(k, GENEO_NOT_CONVERGED), its(k, 0);
+  int nact = 0;
+  for (int j = 0; j < k; ++j) {
+    bnorm[j] = std::sqrt(hs[j * kScal + 4]);
+    ha[j] = bnorm[j] > 0.0;
+    if (!ha[j]) {
+      st[j] = GENEO_OK;
+      rel[j] = 0.0;
+    }
+    nact += ha[j];
+  }
+  GENEO_CUDA(cudaMemcpyAsync(c->d_act.p, ha, sizeof(int) * k, cudaMemcpyHostToDevice, s));
+  for (int it = 1; it <= maxit && nact > 0; ++it) {
+    const bool replay = graph && it > 1;
+    if (it == 1) {
+      pcg_step_half(c, xw, s, k);
+    } else if (replay) {
+      ensure_pcg_graph(c, k);
+      GENEO_CUDA(cudaGraphLaunch(c->pcg_exec, s));
+      c->launches += c->pcg_graph_launches;
+    } else {
+      pcg_precond_half(c, s, k);
+      pcg_step_half(c, xw, s, k);
+    }
+    GENEO_CUDA(cudaStreamSynchronize(s));
+    if (replay && c->prof) harvest_graph_events(c);
+    bool changed = false;
+    for (int j = 0; j < k; ++j) {
+      if (!ha[j]) continue;
+      its[j] = it;
+      const double *h = hs + j * kScal;
+      if (!(h[1] > 0.0) || !std::isfinite(h[1]) || !std::isfinite(h[2])) {
+        st[j] = GENEO_ERR_BREAKDOWN;
       } else {
-        pcg_precond_half(c, s);
-        pcg_step_half(c, xw, s);
+        rel[j] = std::sqrt(h[2]) / bnorm[j];
+        if (rel[j] <= tol) st[j] = GENEO_OK;
       }
-      GENEO_CUDA(cudaStreamSynchronize(s));
-      if (replay && c->prof) harvest_graph_events(c);
-      if (!(hs[1] > 0.0) || !std::isfinite(hs[1]) || !std::isfinite(hs[2])) {
-        status = GENEO_ERR_BREAKDOWN;
-        break;
-      }
-      rel = std::sqrt(hs[2]) / bnorm;
-      if (rel <= tol) {
-        status = GENEO_OK;
-        break;
+      if (st[j] != GENEO_NOT_CONVERGED) {
+        ha[j] = 0;
+        --nact;
+        changed = true;
       }
     }
-    if (it > maxit) it = maxit;
+    if (changed && nact > 0)
+      GENEO_CUDA(cudaMemcpyAsync(c->d_act.p, ha, sizeof(int) * k, cudaMemcpyHostToDevice, s));
   }
   if (xw != x) {
     c->launches += 1;
@@ -387,10 +478,16 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
   }
   GENEO_CUDA(cudaStreamSynchronize(s));
   check_device_error(c, s);
-  if (info) {
-    info->iters = it;
-    info->relres = rel;
-    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int status = GENEO_OK;
+  for (int j = 0; j < k; ++j) {
+    if (info) {
+      info[j].iters = its[j];
+      info[j].relres = rel[j];
+      info[j].seconds = secs;
+    }
+    if (st[j] == GENEO_ERR_BREAKDOWN) status = GENEO_ERR_BREAKDOWN;
+    else if (st[j] == GENEO_NOT_CONVERGED && status == GENEO_OK) status = GENEO_NOT_CONVERGED;
   }
   return status;
 }
