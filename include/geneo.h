@@ -63,6 +63,10 @@ extern "C" {
 #define GENEO_PREC_FP64 0          /* local factors stored and applied in float64 */
 #define GENEO_PREC_FP32 1          /* split factors (Sec. 2, eq. "inverseBw"): A_j^-1 =
                                       G S^-1 G^T (float64) + (I - xi) A_j^-1 (float32) */
+#define GENEO_PREC_BF16 2          /* the same split with (I - xi) A_j^-1 in bfloat16, applied on
+                                      the tensor cores with float32 accumulation to blocks of up
+                                      to 16 right-hand sides (x rounded to bfloat16); needs
+                                      n_j <= 2048 in every subdomain (else INVALID_ARG) */
 
 #define GENEO_COARSE_NONE 0        /* one-level additive Schwarz (eq. "AS") */
 #define GENEO_COARSE_SNK 1         /* split near-kernel space (definition "near-kernelCS") */
@@ -192,7 +196,8 @@ int geneo_solve_block(geneo_ctx *ctx, const double *B_dev, double *X_dev, int32_
                       double tol, int32_t maxit, geneo_solve_info *info, void *stream);
 
 /* Selects the local factors used by later solves when the context holds
- * both: GENEO_PREC_FP64 (explicit float64 inverses) or GENEO_PREC_FP32 (the
+ * several: GENEO_PREC_FP64 (explicit float64 inverses), GENEO_PREC_BF16 (built
+ * when options.precision was BF16, together with the float32 split) or GENEO_PREC_FP32 (the
  * split C_j + G_j S_j^-1 G_j^T, built when options.precision was FP32; the
  * float64 inverses are kept as well).  Returns STATE if they were not built. */
 int geneo_use_precision(geneo_ctx *ctx, int32_t precision);

@@ -7,7 +7,7 @@ loads the library and raises if it has not been built: there is no CPU
 fallback.
 """
 from .api import (GeneoError, Options, Solver, load_library, PREC_FP64, PREC_FP32,
-                  COARSE_NONE, COARSE_SNK, TAU_RECIPROCAL, TAU_PAPER)
+                  PREC_BF16, COARSE_NONE, COARSE_SNK, TAU_RECIPROCAL, TAU_PAPER)
 
-__all__ = ["GeneoError", "Options", "Solver", "load_library", "PREC_FP64", "PREC_FP32",
+__all__ = ["GeneoError", "Options", "Solver", "load_library", "PREC_FP64", "PREC_FP32", "PREC_BF16",
            "COARSE_NONE", "COARSE_SNK", "TAU_RECIPROCAL", "TAU_PAPER"]

@@ -11,7 +11,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgeneo.so")
 
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 COARSE_NONE, COARSE_SNK = 0, 1
 TAU_RECIPROCAL, TAU_PAPER = 0, 1
 NOT_CONVERGED = 1
@@ -105,6 +105,7 @@ _EXPORT_DTYPES = {
     "N_idx": np.int32, "owner": np.int32, "snk_sub": np.int32, "snk_vert": np.int32,
     "geneo_sub": np.int32, "geneo_lambda": np.float64, "geneo_found": np.int32,
     "Zcol_ptr": np.int64, "Zcol_row": np.int32, "Zcol_val": np.float64, "k0k1": np.int32,
+    "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
 }
 
 

@@ -99,7 +99,8 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
   geneo_options o;
   geneo_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32)
+  if (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32 &&
+      o.precision != GENEO_PREC_BF16)
     return fail(GENEO_ERR_INVALID_ARG, "unknown precision");
   if (o.coarse != GENEO_COARSE_NONE && o.coarse != GENEO_COARSE_SNK)
     return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
@@ -165,7 +166,7 @@ int geneo_query(const geneo_ctx *c, geneo_sizes *o) {
   o->n0 = c->n0;
   o->n0_snk = c->n0_snk;
   o->n0_geneo = c->n0_geneo;
-  o->local_factor_bytes = c->loc_f64.bytes() + c->loc_f32.bytes();
+  o->local_factor_bytes = c->loc_f64.bytes() + c->loc_f32.bytes() + geneo::tc_factor_bytes(c);
   o->coarse_factor_bytes = c->mf ? geneo::mf_factor_bytes(c) : c->crs_f64.bytes();
   o->setup_seconds = c->setup_seconds;
   return GENEO_OK;
@@ -264,6 +265,10 @@ int geneo_use_precision(geneo_ctx *c, int32_t precision) {
     c->local_prec = GENEO_PREC_FP32;
     return GENEO_OK;
   }
+  if (precision == GENEO_PREC_BF16 && c->tc) {
+    c->local_prec = GENEO_PREC_BF16;
+    return GENEO_OK;
+  }
   return fail(GENEO_ERR_STATE, "the requested local factors were not built");
 }
 
@@ -297,9 +302,11 @@ int geneo_profile_read(geneo_ctx *c, geneo_profile *o) {
     o->coarse_symv_ms += c->acc_coarse_ms;
     c->acc_local_ms = c->acc_coarse_ms = 0;
     c->acc_local_n = c->acc_coarse_n = 0;
-    o->local_symv_bytes = c->loc.ntiles * (int64_t)geneo::kTileElems *
-                          (c->local_prec == GENEO_PREC_FP32 ? (int64_t)sizeof(float)
-                                                            : (int64_t)sizeof(double));
+    o->local_symv_bytes = c->local_prec == GENEO_PREC_BF16
+                              ? geneo::tc_factor_bytes(c)
+                              : c->loc.ntiles * (int64_t)geneo::kTileElems *
+                                    (c->local_prec == GENEO_PREC_FP32 ? (int64_t)sizeof(float)
+                                                                      : (int64_t)sizeof(double));
     int64_t fl = 0;
     for (int i = 0; i < c->dec.nsub; ++i) fl += 2 * c->dec.ni(i) * c->dec.ni(i);
     o->local_symv_flops = fl;
@@ -337,6 +344,12 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
     else if (nm == "Zcol_ptr") put(c->zc_ptr.data(), c->zc_ptr.size() * 8);
     else if (nm == "Zcol_row") put(c->zc_row.data(), c->zc_row.size() * 4);
     else if (nm == "Zcol_val") put(c->zc_val.data(), c->zc_val.size() * 8);
+    else if (nm == "loc_f32") {
+      auto v = c->loc_f32.download(c->stream);
+      put(v.data(), v.size() * 4);
+    } else if (nm == "loc_nt") put(c->loc.nt.data(), c->loc.nt.size() * 4);
+    else if (nm == "loc_toff") put(c->loc.toff.data(), c->loc.toff.size() * 8);
+    else if (nm == "loc_voff") put(c->loc.voff.data(), c->loc.voff.size() * 8);
     else if (nm == "k0k1") {
       int32_t k[2] = {c->dec.k0, c->dec.k1};
       put(k, 8);

@@ -108,5 +108,6 @@ enum DevErr : int {
 
 constexpr int kTile = 64;             // tile edge of the packed symmetric matrices
 constexpr int kTileElems = kTile * kTile;
+constexpr int kTcMaxBlocks = 16;      // tensor-core local solves: n_i <= 16 * 128
 
 }  // namespace geneo

@@ -12,6 +12,10 @@ struct Multifrontal;
 struct MfDeleter {
   void operator()(Multifrontal *m) const;
 };
+struct TcFactors;
+struct TcDeleter {
+  void operator()(TcFactors *t) const;
+};
 }  // namespace geneo
 
 struct geneo_ctx {
@@ -68,6 +72,8 @@ struct geneo_ctx {
   // local operators (xi, S_j^-1, element data) for GenEO and the split solve
   std::unique_ptr<geneo::XiOp> xi;
   int local_prec = GENEO_PREC_FP64;  // precision used by the local solves
+  // bfloat16 super-tiles of C_j for the tensor-core local solves
+  std::unique_ptr<geneo::TcFactors, geneo::TcDeleter> tc;
 
   // work vectors
   geneo::DevBuf<double> v_y0, v_s, v_w, v_t, v_c, loc_x, loc_y, crs_x, crs_y;

@@ -672,9 +672,13 @@ void setup_all(geneo_ctx *c) {
     c->d_g2l_ptr.upload(c->ls.g2l_ptr, s);
     c->d_g2l.upload(g2l, s);
   }
-  if (c->opt.precision == GENEO_PREC_FP32) {
+  if (c->opt.precision == GENEO_PREC_FP32 || c->opt.precision == GENEO_PREC_BF16) {
     build_split_factors(c);
     c->local_prec = GENEO_PREC_FP32;
+  }
+  if (c->opt.precision == GENEO_PREC_BF16) {
+    build_bf16_factors(c);
+    c->local_prec = GENEO_PREC_BF16;
   }
 
   // --- coarse space

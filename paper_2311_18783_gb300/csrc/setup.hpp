@@ -64,6 +64,12 @@ int64_t mf_factor_bytes(const geneo_ctx *c);
 // Solve path; k right-hand sides stored as k consecutive columns of length n
 // (local vectors: columns of loc.vlen).
 void reserve_rhs(geneo_ctx *c, int k);
+// bfloat16 local factors on the tensor cores (block right-hand sides)
+bool tc_supported(const geneo_ctx *c);
+void build_bf16_factors(geneo_ctx *c);
+int64_t tc_factor_bytes(const geneo_ctx *c);
+void tc_symm(geneo_ctx *c, const double *xl, double *yl, int k, cudaStream_t s, cudaEvent_t e0,
+             cudaEvent_t e1);
 void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k = 1);
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k = 1);
 void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k = 1);

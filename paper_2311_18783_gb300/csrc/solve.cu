@@ -252,6 +252,22 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k
   const int64_t n = c->topo.ndofs(), vlen = c->loc.vlen;
   c->launches += 2;
   k_restrict<<<dim3(grid_for(vlen, 256), k), 256, 0, s>>>(c->d_l2g.p, r, c->loc_x.p, vlen, n);
+  if (c->local_prec == GENEO_PREC_BF16) {
+    // tensor cores: every column in one pass over the bfloat16 factors
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+      e0 = c->ev_take();
+      e1 = c->ev_take();
+      c->ev_local.push_back({e0, e1});
+    }
+    c->launches += 1 + 2 + 2 * k;
+    tc_symm(c, c->loc_x.p, c->loc_y.p, k, s, e0, e1);
+    split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s, k);
+    k_prolong<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w,
+                                                        n, vlen);
+    GENEO_CHECK_LAUNCH();
+    return;
+  }
   for (int j = 0; j < k; ++j) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof) {
