@@ -105,6 +105,9 @@ typedef struct {
                                 many columns become leaf fronts; 0 selects 256 */
   int32_t use_graph;         /* 1: every PCG iteration after the first replays one CUDA
                                 graph captured at the first solve; 0: plain launches */
+  int32_t gradient_shift;    /* 1: invert A~_j = A_j + rho_j A_j G_j S_j^-1 G_j^T A_j instead of
+                                A_j (same C_j and A_j^-1 exactly, see Sec. 2 eq. "inverseBw";
+                                needed when gamma makes A_j numerically singular); 0: off */
 } geneo_options;
 
 typedef struct {

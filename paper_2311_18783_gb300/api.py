@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("tau_convention", C.c_int32), ("lobpcg_block", C.c_int32),
                 ("lobpcg_maxit", C.c_int32), ("lobpcg_tol", C.c_double), ("seed", C.c_uint64),
                 ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("gradient_shift", C.c_int32)]
 
 
 class Sizes(C.Structure):

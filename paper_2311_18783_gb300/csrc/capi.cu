@@ -107,7 +107,7 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
   if (o.lobpcg_block < 1 || o.lobpcg_block > 16 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
     return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
-      (o.use_graph != 0 && o.use_graph != 1))
+      (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
   return guarded([&]() {
     auto c = new geneo_ctx();

@@ -76,7 +76,7 @@ struct geneo_ctx {
   std::unique_ptr<geneo::TcFactors, geneo::TcDeleter> tc;
 
   // work vectors
-  geneo::DevBuf<double> v_y0, v_s, v_w, v_t, v_c, loc_x, loc_y, crs_x, crs_y;
+  geneo::DevBuf<double> v_y0, v_s, v_w, v_t, v_c, loc_x, loc_y, loc_xp, crs_x, crs_y;
   geneo::DevBuf<double> p_r, p_z, p_p, p_q, scal, partials;
   geneo::DevBuf<double> h_b, h_x;  // device copies used by geneo_solve_host
   geneo::DevBuf<int> d_err;

@@ -1,6 +1,6 @@
-// Batched tile-packed symmetric matrices: explicit inversion by a symmetric
-// Gauss-Jordan sweep (float64) and a streaming SYMV whose 64x64 tiles are
-// staged in shared memory by cp.async.bulk copies completed on mbarriers.
+// Batched tile-packed symmetric matrices: explicit inversion by tiled
+// Cholesky (float64) and a streaming SYMV whose 64x64 tiles are staged in
+// shared memory by cp.async.bulk copies completed on mbarriers.
 //
 // The local solves A_i^-1 of Sec. 2, eq. "AS", are applied as explicit
 // inverses: every tile is read once per application and the work of all
@@ -90,19 +90,11 @@ void TileBatch::schedule(int nctas, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // tile helpers
 
-__device__ __forceinline__ void tile_I_J(int64_t q, int &I, int &J) {
-  int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
-  while ((int64_t)i * (i + 1) / 2 > q) --i;
-  I = i;
-  J = (int)(q - (int64_t)i * (i + 1) / 2);
-}
 
 __device__ __forceinline__ int64_t tidx(int64_t toff, int I, int J) {
   return toff + (int64_t)I * (I + 1) / 2 + J;
 }
 
-constexpr int kLd = kTile + 1;  // padded shared-memory leading dimension
 
 // dst[r][c] = src[r][c] (transpose = false) or src[c][r] (transpose = true)
 __device__ __forceinline__ void load_tile_smem(double *dst, const double *__restrict__ src,
@@ -115,22 +107,6 @@ __device__ __forceinline__ void load_tile_smem(double *dst, const double *__rest
   }
 }
 
-// acc[i][j] += sum_t As[ri][t] * Bs[cj][t], rows ri = 4*tr + i, cols cj = tc + 16 j
-__device__ __forceinline__ void gemm_abt(const double *As, const double *Bs, double acc[4][4]) {
-  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-#pragma unroll 4
-  for (int t = 0; t < kTile; ++t) {
-    double a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = As[(4 * tr + i) * kLd + t];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = Bs[(tc + 16 * j) * kLd + t];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Explicit SPD inverse by tiled Cholesky.  A = L L^T (POTRF on the diagonal

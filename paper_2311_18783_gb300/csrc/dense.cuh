@@ -1,17 +1,47 @@
 // Batched dense symmetric matrices in tile-packed storage, their explicit
-// inversion by a symmetric Gauss-Jordan sweep, and the streaming SYMV that
-// applies them.
+// inversion by tiled Cholesky, and the streaming SYMV that applies them.
 //
 // Storage: matrix m of dimension dim[m] is padded to nt[m] = ceil(dim/64)
 // tiles per side; only tiles (I, J) with J <= I are stored, each a full 64x64
 // row-major block, at tile index toff[m] + I(I+1)/2 + J.  Diagonal tiles hold
 // both triangles.  Padding rows/columns carry an identity diagonal, so the
-// sweep leaves them decoupled.  Vectors use the padded layout: matrix m owns
+// factorisation leaves them decoupled.  Vectors use the padded layout: matrix m owns
 // elements [voff[m], voff[m] + 64 nt[m]).
 #pragma once
 #include "common.cuh"
 
 namespace geneo {
+
+// ---- 64x64 tile helpers shared by the dense kernels
+
+// (I, J) of the q-th lower tile in row-major packed order
+__device__ __forceinline__ void tile_I_J(int64_t q, int &I, int &J) {
+  int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
+  while ((int64_t)i * (i + 1) / 2 > q) --i;
+  I = i;
+  J = (int)(q - (int64_t)i * (i + 1) / 2);
+}
+
+constexpr int kLd = kTile + 1;  // padded shared-memory leading dimension
+
+// acc[i][j] += sum_t As[ri][t] * Bs[cj][t], rows ri = 4*tr + i, cols cj = tc + 16 j
+__device__ __forceinline__ void gemm_abt(const double *As, const double *Bs, double acc[4][4]) {
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll 4
+  for (int t = 0; t < kTile; ++t) {
+    double a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[(4 * tr + i) * kLd + t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Bs[(tc + 16 * j) * kLd + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
 
 struct TileBatch {
   int nmat = 0;

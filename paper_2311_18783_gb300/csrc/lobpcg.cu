@@ -175,7 +175,7 @@ __global__ void k_g(const int32_t *__restrict__ ghead, const int32_t *__restrict
                     const int64_t *__restrict__ voff, const int64_t *__restrict__ voffS,
                     int64_t nslots, int k, int64_t vlen, int64_t vlenS,
                     const double *__restrict__ u, const double *__restrict__ x,
-                    double *__restrict__ out, int mode) {
+                    double *__restrict__ out, int mode, const double *__restrict__ scale) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= nslots * k) return;
   const int64_t slot = q % nslots;
@@ -186,7 +186,7 @@ __global__ void k_g(const int32_t *__restrict__ ghead, const int32_t *__restrict
   if (ghead[slot] >= 0) g += u[ub + ghead[slot]];
   if (gtail[slot] >= 0) g -= u[ub + gtail[slot]];
   const int64_t p = voff[m] + (slot - Noff[m]) + (int64_t)c * vlen;
-  if (mode == 2) out[p] += g;
+  if (mode == 2) out[p] += scale ? scale[m] * g : g;
   else out[p] = mode ? x[p] - g : g;
 }
 
@@ -207,7 +207,7 @@ __global__ void k_split_cast(const double *__restrict__ ainv, const int32_t *__r
                              const int64_t *__restrict__ toff, const int64_t *__restrict__ Noff,
                              const int32_t *__restrict__ ghead, const int32_t *__restrict__ gtail,
                              const double *__restrict__ sinv, const int64_t *__restrict__ toffS,
-                             float *__restrict__ out) {
+                             const double *__restrict__ gfac, float *__restrict__ out) {
   const int m = blockIdx.y;
   const int64_t ntm = nt[m];
   const int64_t q = blockIdx.x;
@@ -229,7 +229,7 @@ __global__ void k_split_cast(const double *__restrict__ ainv, const int32_t *__r
       if (hr >= 0 && tc >= 0) g -= sinv_at(sinv, toffS[m], hr, tc);
       if (tr >= 0 && hc >= 0) g -= sinv_at(sinv, toffS[m], tr, hc);
       if (tr >= 0 && tc >= 0) g += sinv_at(sinv, toffS[m], tr, tc);
-      v -= g;
+      v -= gfac ? gfac[m] * g : g;
     }
     out[tb + e] = (float)v;
   }
@@ -493,7 +493,7 @@ static void xi_apply(Lobpcg &L, const double *x, double *out, int k, int mode) {
   if (mode == 1) {
     k_g<<<grid_for(L.op.nslots * k, 256), 256, 0, L.s>>>(L.op.ghead.p, L.op.gtail.p, L.op.slot_sub.p, L.op.Noff.p,
                                                       L.c->loc.d_voff.p, L.op.sb.d_voff.p, L.op.nslots, k,
-                                                      L.vlen, L.op.vlenS, L.U2.p, x, out, 1);
+                                                      L.vlen, L.op.vlenS, L.U2.p, x, out, 1, nullptr);
   } else {
     k_agw<<<grid_for(L.op.nslots * k, 128), 128, 0, L.s>>>(
         L.op.rptr.p, L.op.rtet.p, L.op.rpos.p, L.op.rlidx.p, L.op.rvidx.p, L.op.tcurl.p, L.op.tmass.p, L.op.slot_sub.p,
@@ -513,7 +513,7 @@ static void project_gradients_B(Lobpcg &L, double *Y, int k) {
                        L.U2.p + (int64_t)col * L.op.vlenS, L.c->d_err.p, L.s);
   k_g<<<grid_for(L.op.nslots * k, 256), 256, 0, L.s>>>(L.op.ghead.p, L.op.gtail.p, L.op.slot_sub.p, L.op.Noff.p,
                                                     L.c->loc.d_voff.p, L.op.sb.d_voff.p, L.op.nslots, k,
-                                                    L.vlen, L.op.vlenS, L.U2.p, Y, Y, 1);
+                                                    L.vlen, L.op.vlenS, L.U2.p, Y, Y, 1, nullptr);
 }
 
 // LY = (I - xi)^T D A D (I - xi) Y  for a block of k columns
@@ -1097,7 +1097,7 @@ void build_split_factors(geneo_ctx *c) {
   const int64_t maxT = (int64_t)c->loc.maxnt * (c->loc.maxnt + 1) / 2;
   k_split_cast<<<dim3((unsigned)maxT, c->loc.nmat), 256, 0, s>>>(
       c->loc_f64.p, c->loc.d_nt.p, c->loc.d_toff.p, op.Noff.p, op.ghead.p, op.gtail.p,
-      op.s_inv.p, op.sb.d_toff.p, c->loc_f32.p);
+      op.s_inv.p, op.sb.d_toff.p, op.shifted ? op.gfac.p : nullptr, c->loc_f32.p);
   GENEO_CHECK_LAUNCH();
   op.u1.alloc(op.vlenS);
   op.u2.alloc(op.vlenS);
@@ -1108,7 +1108,8 @@ void build_split_factors(geneo_ctx *c) {
 
 // yl += G_j S_j^-1 G_j^T xl for every subdomain (float64 gradient part of the
 // split local inverse), on padded local vectors
-void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k) {
+void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k,
+                          const double *scale) {
   XiOp &op = *c->xi;
   k_gt<<<grid_for(op.nv * k, 256), 256, 0, s>>>(op.sptr.p, op.srow.p, op.ssgn.p, op.vslot_sub.p,
                                                 op.xvoff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nv,
@@ -1119,8 +1120,236 @@ void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream
   k_g<<<grid_for(op.nslots * k, 256), 256, 0, s>>>(op.ghead.p, op.gtail.p, op.slot_sub.p,
                                                    op.Noff.p, c->loc.d_voff.p, op.sb.d_voff.p,
                                                    op.nslots, k, op.vlen, op.vlenS, op.u2.p,
-                                                   nullptr, yl, 2);
+                                                   nullptr, yl, 2, scale);
   GENEO_CHECK_LAUNCH();
+}
+
+// bfloat16 split local solve on the tensor cores in the two-sided form
+// C_j = (I - xi_j) A_j^-1 (I - xi_j)^T (equal to (I - xi_j) A_j^-1, since
+// (I - xi_j) A_j^-1 = A_j^-1 (I - xi_j)^T and the projection is idempotent):
+//   u = S_j^-1 G_j^T x,   x' = x - A_j G_j u = (I - xi_j)^T x,
+//   v = C_j x' (bfloat16, tensor cores),
+//   y = v - G_j S_j^-1 G_j^T A_j v + G_j u.
+// The bfloat16 C_j never sees the gradient-type part of the residual, and
+// its rounding error is removed from the gradient directions of the output,
+// so the perturbation stays in the complement where A_j is not small.
+void split_tc_apply(geneo_ctx *c, const double *xl, double *yl, double *xp, cudaStream_t s, int k,
+                    cudaEvent_t e0, cudaEvent_t e1) {
+  XiOp &op = *c->xi;
+  k_gt<<<grid_for(op.nv * k, 256), 256, 0, s>>>(op.sptr.p, op.srow.p, op.ssgn.p, op.vslot_sub.p,
+                                                op.xvoff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nv,
+                                                k, op.vlen, op.vlenS, xl, op.u1.p);
+  for (int j = 0; j < k; ++j)
+    symv_batch<double>(op.sb, op.s_inv.p, op.u1.p + j * op.vlenS, op.u2.p + j * op.vlenS,
+                       c->d_err.p, s);
+  k_agw<<<grid_for(op.nslots * k, 256), 256, 0, s>>>(
+      op.rptr.p, op.rtet.p, op.rpos.p, op.rlidx.p, op.rvidx.p, op.tcurl.p, op.tmass.p,
+      op.slot_sub.p, op.Noff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nslots, k, op.vlen, op.vlenS,
+      op.u2.p, xl, xp);
+  tc_symm(c, xp, yl, k, s, e0, e1);
+  k_gtA_curl<<<grid_for(op.nv * k, 128), 128, 0, s>>>(
+      op.ctp_d.p, op.ctt_d.p, op.ct_d.p, op.lidx_d.p, op.tcurl.p, op.tmass.p, op.col_sub.p,
+      op.col_out.p, c->loc.d_voff.p, op.nv, k, op.vlen, op.vlenS, yl, op.u1.p);
+  for (int j = 0; j < k; ++j)
+    symv_batch<double>(op.sb, op.s_inv.p, op.u1.p + j * op.vlenS, op.u3.p + j * op.vlenS,
+                       c->d_err.p, s);
+  k_sub<<<grid_for(op.vlenS * k, 256), 256, 0, s>>>(op.u2.p, op.u3.p, op.u3.p, op.vlenS * k);
+  k_g<<<grid_for(op.nslots * k, 256), 256, 0, s>>>(op.ghead.p, op.gtail.p, op.slot_sub.p,
+                                                   op.Noff.p, c->loc.d_voff.p, op.sb.d_voff.p,
+                                                   op.nslots, k, op.vlen, op.vlenS, op.u3.p,
+                                                   nullptr, yl, 2, nullptr);
+  GENEO_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// Gradient shift of the local matrices.  For tiny gamma the gradients of
+// Omega_j make A_j numerically singular (kappa ~ 1/(gamma u) and beyond), so
+// no float64 factorisation of A_j is meaningful.  With xi_j = G S^-1 G^T A_j
+// (Sec. 2, lemma with eq. "inverseBw") and any rho > 0,
+//   A~_j = A_j + rho A_j G S^-1 G^T A_j = A_j (I + rho xi_j),
+//   A~_j^-1 = (I + rho xi_j)^-1 A_j^-1 = A_j^-1 - rho/(1+rho) G S^-1 G^T,
+// since xi_j is a projection.  A~_j lifts only the gradient modes (by 1 + rho),
+// so it is factored instead, and exactly
+//   C_j = (I - xi_j) A_j^-1 = A~_j^-1 - 1/(1+rho) G S^-1 G^T,
+//   A_j^-1 = A~_j^-1 + rho/(1+rho) G S^-1 G^T.
+// rho_j puts the mean Rayleigh quotient of the lifted gradient columns at the
+// mean diagonal of A_j: rho = (tr A_j / n_j) / (tr H_j / nv_j), H = A G S^-1 G^T A.
+
+namespace {
+
+// w[c][voffS[m] + c] = 1 for the nv_m kept vertices of subdomain m
+__global__ void k_ident_cols(const int64_t *__restrict__ xvoff, const int64_t *__restrict__ voffS,
+                             int64_t vlenS, double *__restrict__ w) {
+  const int m = blockIdx.x;
+  const int64_t nv = xvoff[m + 1] - xvoff[m];
+  for (int64_t c = threadIdx.x; c < nv; c += blockDim.x) w[c * vlenS + voffS[m] + c] = 1.0;
+}
+
+// T[v][rows of tile I] = sum_u AG[u][rows] S^-1(u, v), 64 x 64 output tile
+// (I, V) of subdomain m per CTA; columns of length vlen per vertex
+__global__ void __launch_bounds__(256) k_ag_sinv(const double *__restrict__ AG,
+                                                 const double *__restrict__ sinv,
+                                                 const int32_t *__restrict__ nt,
+                                                 const int64_t *__restrict__ voff,
+                                                 const int32_t *__restrict__ ntS,
+                                                 const int64_t *__restrict__ toffS, int64_t vlen,
+                                                 double *__restrict__ T) {
+  __shared__ double As[kTile * kLd], Bs[kTile * kLd];
+  const int m = blockIdx.z, I = blockIdx.x, V = blockIdx.y;
+  if (I >= nt[m] || V >= ntS[m]) return;
+  const int64_t rb = voff[m] + (int64_t)I * kTile;
+  double acc[4][4] = {};
+  for (int U = 0; U < ntS[m]; ++U) {
+    for (int e = threadIdx.x; e < kTileElems; e += blockDim.x) {
+      const int uu = e >> 6, r = e & 63;  // coalesced over rows
+      As[r * kLd + uu] = AG[((int64_t)U * kTile + uu) * vlen + rb + r];
+      const int a = e >> 6, b = e & 63;   // S^-1(U*64 + a, V*64 + b) -> Bs[b][a]
+      double v;
+      if (U >= V)
+        v = sinv[(toffS[m] + (int64_t)U * (U + 1) / 2 + V) * kTileElems + a * kTile + b];
+      else
+        v = sinv[(toffS[m] + (int64_t)V * (V + 1) / 2 + U) * kTileElems + b * kTile + a];
+      Bs[b * kLd + a] = v;
+    }
+    __syncthreads();
+    gemm_abt(As, Bs, acc);
+    __syncthreads();
+  }
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      T[((int64_t)V * kTile + tc + 16 * j) * vlen + rb + 4 * tr + i] = acc[i][j];
+}
+
+// per subdomain (one CTA): tr A_m over its n_m rows and tr H_m = sum_v T[v] . AG[v]
+__global__ void k_shift_rho(const double *__restrict__ ainv, const int64_t *__restrict__ toff,
+                            const int64_t *__restrict__ Noff, const int64_t *__restrict__ voff,
+                            const int64_t *__restrict__ xvoff, const double *__restrict__ AG,
+                            const double *__restrict__ T, int64_t vlen, double *__restrict__ rho,
+                            double *__restrict__ gfac, double *__restrict__ gsc) {
+  __shared__ double sa[256], sh[256];
+  const int m = blockIdx.x;
+  const int64_t n = Noff[m + 1] - Noff[m], nv = xvoff[m + 1] - xvoff[m];
+  double ta = 0, th = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const int64_t I = r / kTile;
+    ta += ainv[(toff[m] + I * (I + 1) / 2 + I) * kTileElems + (r % kTile) * (kTile + 1)];
+    for (int64_t v = 0; v < nv; ++v) th = fma(T[v * vlen + voff[m] + r], AG[v * vlen + voff[m] + r], th);
+  }
+  sa[threadIdx.x] = ta;
+  sh[threadIdx.x] = th;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sh[threadIdx.x] += sh[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double r = (nv > 0 && sh[0] > 0) ? (sa[0] / (double)n) / (sh[0] / (double)nv) : 0.0;
+    rho[m] = r;
+    gfac[m] = 1.0 / (1.0 + r);
+    gsc[m] = r / (1.0 + r);
+  }
+}
+
+// A~(I, J) += rho_m sum_v T[v][rows I] AG[v][rows J], J <= I
+__global__ void __launch_bounds__(256) k_shift_update(const double *__restrict__ T,
+                                                      const double *__restrict__ AG,
+                                                      const int32_t *__restrict__ nt,
+                                                      const int64_t *__restrict__ toff,
+                                                      const int64_t *__restrict__ voff,
+                                                      const int32_t *__restrict__ ntS,
+                                                      const double *__restrict__ rho,
+                                                      int64_t vlen, double *__restrict__ A) {
+  __shared__ double As[kTile * kLd], Bs[kTile * kLd];
+  const int m = blockIdx.y;
+  const int64_t ntm = nt[m];
+  const int64_t q = blockIdx.x;
+  if (q >= ntm * (ntm + 1) / 2) return;
+  int I, J;
+  tile_I_J(q, I, J);
+  const int64_t ri = voff[m] + (int64_t)I * kTile, rj = voff[m] + (int64_t)J * kTile;
+  double acc[4][4] = {};
+  for (int V = 0; V < ntS[m]; ++V) {
+    for (int e = threadIdx.x; e < kTileElems; e += blockDim.x) {
+      const int vv = e >> 6, r = e & 63;
+      const int64_t col = ((int64_t)V * kTile + vv) * vlen;
+      As[r * kLd + vv] = T[col + ri + r];
+      Bs[r * kLd + vv] = AG[col + rj + r];
+    }
+    __syncthreads();
+    gemm_abt(As, Bs, acc);
+    __syncthreads();
+  }
+  const double rh = rho[m];
+  double *dst = A + (toff[m] + q) * kTileElems;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[(4 * tr + i) * kTile + tc + 16 * j] += rh * acc[i][j];
+}
+
+}  // namespace
+
+void apply_gradient_shift(geneo_ctx *c) {
+  cudaStream_t s = c->stream;
+  if (!c->xi) {
+    c->xi.reset(new XiOp());
+    build_xi_operator(c, *c->xi, s);
+  }
+  XiOp &op = *c->xi;
+  const int nsub = c->dec.nsub;
+  const std::vector<int64_t> &xv = c->ls.xv_off;
+  int64_t nvmax = 0;
+  for (int m = 0; m < nsub; ++m) nvmax = std::max(nvmax, xv[m + 1] - xv[m]);
+  op.rho.alloc(nsub);
+  op.gfac.alloc(nsub);
+  op.gsc64.alloc(nsub);
+  op.shifted = true;
+  if (nvmax == 0) {
+    op.rho.zero(s);
+    std::vector<double> one(nsub, 1.0);
+    op.gfac.upload(one, s);
+    op.gsc64.zero(s);
+    return;
+  }
+  const int64_t kv = (nvmax + kTile - 1) / kTile * kTile;  // vertex columns, tile padded
+  const int64_t vlen = c->loc.vlen, vlenS = op.vlenS;
+  DevBuf<double> W, AG, T;
+  W.alloc(kv * vlenS);
+  W.zero(s);
+  k_ident_cols<<<nsub, 128, 0, s>>>(op.xvoff.p, op.sb.d_voff.p, vlenS, W.p);
+  // -A_j G e_v for every kept vertex v (curl route; y = 0 in out = y - A G w)
+  AG.alloc(kv * vlen);
+  AG.zero(s);
+  k_agw<<<grid_for(op.nslots * kv, 256), 256, 0, s>>>(
+      op.rptr.p, op.rtet.p, op.rpos.p, op.rlidx.p, op.rvidx.p, op.tcurl.p, op.tmass.p,
+      op.slot_sub.p, op.Noff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nslots, (int)kv, vlen, vlenS,
+      W.p, AG.p, AG.p);
+  GENEO_CHECK_LAUNCH();
+  W.release();
+  T.alloc(kv * vlen);
+  T.zero(s);
+  const int maxntS = op.sb.maxnt;
+  k_ag_sinv<<<dim3(c->loc.maxnt, maxntS, nsub), 256, 0, s>>>(AG.p, op.s_inv.p, c->loc.d_nt.p,
+                                                             c->loc.d_voff.p, op.sb.d_nt.p,
+                                                             op.sb.d_toff.p, vlen, T.p);
+  GENEO_CHECK_LAUNCH();
+  k_shift_rho<<<nsub, 256, 0, s>>>(c->loc_f64.p, c->loc.d_toff.p, op.Noff.p, c->loc.d_voff.p,
+                                   op.xvoff.p, AG.p, T.p, vlen, op.rho.p, op.gfac.p, op.gsc64.p);
+  GENEO_CHECK_LAUNCH();
+  const int64_t maxT = (int64_t)c->loc.maxnt * (c->loc.maxnt + 1) / 2;
+  k_shift_update<<<dim3((unsigned)maxT, nsub), 256, 0, s>>>(T.p, AG.p, c->loc.d_nt.p,
+                                                           c->loc.d_toff.p, c->loc.d_voff.p,
+                                                           op.sb.d_nt.p, op.rho.p, vlen,
+                                                           c->loc_f64.p);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace geneo

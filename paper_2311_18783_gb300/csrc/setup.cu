@@ -652,10 +652,6 @@ void setup_all(geneo_ctx *c) {
     k_extract_local<<<dim3(64, d.nsub), 256, 0, s>>>(noff.p, lrp.p, lcol.p, lpos.p, c->d_val.p,
                                                      c->loc.d_toff.p, c->loc_f64.p);
     GENEO_CHECK_LAUNCH();
-    DevBuf<double> ws;
-    ws.alloc(spd_workspace_elems(c->loc));
-    spd_invert(c->loc, c->loc_f64.p, ws.p, c->d_err.p, s);
-    check_device_error(c, s);
   }
   c->loc.schedule(c->sm_count, s);
   {
@@ -671,6 +667,14 @@ void setup_all(geneo_ctx *c) {
     c->d_l2g.upload(l2g, s);
     c->d_g2l_ptr.upload(c->ls.g2l_ptr, s);
     c->d_g2l.upload(g2l, s);
+  }
+  // optional gradient shift A_j -> A_j (I + rho xi_j), then the explicit inverses
+  if (c->opt.gradient_shift) apply_gradient_shift(c);
+  {
+    DevBuf<double> ws;
+    ws.alloc(spd_workspace_elems(c->loc));
+    spd_invert(c->loc, c->loc_f64.p, ws.p, c->d_err.p, s);
+    check_device_error(c, s);
   }
   if (c->opt.precision == GENEO_PREC_FP32 || c->opt.precision == GENEO_PREC_BF16) {
     build_split_factors(c);

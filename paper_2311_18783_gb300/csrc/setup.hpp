@@ -52,7 +52,11 @@ void build_xi_operator(geneo_ctx *c, XiOp &op, cudaStream_t s);
 // float32 C_j = (I - xi_j) A_j^-1 of every subdomain (needs the float64 inverse)
 void build_split_factors(geneo_ctx *c);
 // yl += G_j S_j^-1 G_j^T xl, float64 gradient part of the split local solve
-void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k = 1);
+void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k = 1,
+                          const double *scale = nullptr);
+void apply_gradient_shift(geneo_ctx *c);
+void split_tc_apply(geneo_ctx *c, const double *xl, double *yl, double *xp, cudaStream_t s, int k,
+                    cudaEvent_t e0, cudaEvent_t e1);
 
 // multifrontal coarse factor: set-up, solve y = E^-1 t (column order), sizes
 void mf_setup(geneo_ctx *c);

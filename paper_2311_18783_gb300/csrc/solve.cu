@@ -213,6 +213,10 @@ void reserve_rhs(geneo_ctx *c, int k) {
     v->alloc(n * k);
   c->loc_x.alloc(c->loc.vlen * k);
   c->loc_y.alloc(c->loc.vlen * k);
+  if (c->tc) {
+    c->loc_xp.alloc(c->loc.vlen * k);
+    c->loc_xp.zero(s);  // padding rows stay zero
+  }
   if (c->n0 > 0) {
     const int64_t len = c->mf ? c->n0 : c->crs.vlen;
     c->crs_x.alloc(len * k);
@@ -221,10 +225,10 @@ void reserve_rhs(geneo_ctx *c, int k) {
     if (c->mf) mf_reserve(c, k);
   }
   if (c->xi) {
-    c->xi->u1.alloc(c->xi->vlenS * k);
-    c->xi->u2.alloc(c->xi->vlenS * k);
-    c->xi->u1.zero(s);
-    c->xi->u2.zero(s);
+    for (auto *u : {&c->xi->u1, &c->xi->u2, &c->xi->u3}) {
+      u->alloc(c->xi->vlenS * k);
+      u->zero(s);
+    }
   }
   c->scal.alloc((int64_t)kScal * k);
   c->scal.zero(s);
@@ -260,9 +264,8 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k
       e1 = c->ev_take();
       c->ev_local.push_back({e0, e1});
     }
-    c->launches += 1 + 2 + 2 * k;
-    tc_symm(c, c->loc_x.p, c->loc_y.p, k, s, e0, e1);
-    split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s, k);
+    c->launches += 6 + 4 * k;
+    split_tc_apply(c, c->loc_x.p, c->loc_y.p, c->loc_xp.p, s, k, e0, e1);
     k_prolong<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w,
                                                         n, vlen);
     GENEO_CHECK_LAUNCH();
@@ -286,6 +289,10 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k
   if (c->local_prec == GENEO_PREC_FP32) {
     // split inverse: float32 C_j r_j plus the float64 gradient part
     split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s, k);
+    c->launches += 2 + 2 * k;
+  } else if (c->xi && c->xi->shifted) {
+    // shifted float64 inverse: A_j^-1 = A~_j^-1 + rho/(1+rho) G S^-1 G^T
+    split_gradient_apply(c, c->loc_x.p, c->loc_y.p, s, k, c->xi->gsc64.p);
     c->launches += 2 + 2 * k;
   }
   k_prolong<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->d_g2l_ptr.p, c->d_g2l.p, c->loc_y.p, w,

@@ -29,7 +29,11 @@ struct XiOp {
   DevBuf<int64_t> rptr;
   DevBuf<int32_t> rtet, rlidx, rvidx;
   DevBuf<int8_t> rpos;
-  DevBuf<double> u1, u2;  // vertex vectors of the split local solve
+  DevBuf<double> u1, u2, u3;  // vertex vectors of the split local solves
+  // gradient shift (A_j replaced by A_j + rho_j A_j G_j S_j^-1 G_j^T A_j before
+  // inversion): rho_j, 1 / (1 + rho_j) and rho_j / (1 + rho_j) per subdomain
+  bool shifted = false;
+  DevBuf<double> rho, gfac, gsc64;
 };
 
 }  // namespace geneo

@@ -2,12 +2,14 @@
 in bfloat16 (Sec. 2, eq. "inverseBw"), applied by tcgen05 MMAs to blocks of
 right-hand sides with float32 accumulation.
 
-* Exactness of the kernel: y_bf16 - y_fp32 (the gradient parts, identical
-  float64 code on both paths, cancel) against the same difference emulated in
-  float64 from the library's own float32 C_j rounded to bfloat16 and the
-  restricted residual rounded to bfloat16.  The remaining gap is float32
-  accumulation (<= n_j 2^-24 |C||x| per entry): bound 1e-5 ||C||x|| + 5% of the
-  difference itself.  A misplaced or mis-transposed tile gives an O(1) error.
+* Exactness of the kernel: y_bf16 - y_fp32 (the float64 gradient parts cancel)
+  against the same difference emulated in float64 from the library's own
+  float32 C_j rounded to bfloat16, applied in the two-sided form
+  (I - xi_j) C_j (I - xi_j)^T x (equal to C_j x in exact arithmetic) to the
+  residual rounded to bfloat16 after the right projection.  The remaining
+  gap is float32 accumulation (<= n_j 2^-24 |C||x| per entry): bound
+  1e-5 ||C||x|| + 5% of the difference itself.  A misplaced or mis-transposed
+  tile gives an O(1) error.
 * Precision: ||y_bf16 - y_fp32|| <= 2^-6 ||y_fp32||.
 * Columns are independent: a block of 16 equals the single-column results.
 * Block PCG with bfloat16 local factors converges to 1e-8; the solution is
@@ -63,14 +65,26 @@ def test_tc_local_solve_exact(tcs):
     s.local_solve(rd, y32)
     s.use_precision(pkg.PREC_BF16)
     d = (y16 - y32).cpu().numpy()
+    from oracle.mesh import build_mesh
+    from oracle.fem import assemble_A
+    from oracle.dd import decompose
+    from oracle.coarse import local_gradient, xi_projector
+    mesh = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    A = assemble_A(mesh, w).tocsr()
+    dec = decompose(mesh, w.parts, w.overlap)
     noff, nidx = s.export("N_off"), s.export("N_idx")
     dref = np.zeros(s.n)
     cx = np.zeros(s.n)
     for i in range(len(noff) - 1):
         idx = nidx[noff[i]:noff[i + 1]]
+        assert np.array_equal(idx, dec.N[i])
         C = _dense_C(s, i)[:len(idx), :len(idx)].astype(np.float64)
         x = r[idx]
-        e = _bf16(C) @ _bf16(x) - C @ x
+        Gi, _ = local_gradient(mesh, dec, i)
+        xi = xi_projector(A[idx][:, idx].toarray(), Gi)
+        xp = x - xi.T @ x
+        v = _bf16(C) @ _bf16(xp)
+        e = (v - xi @ v) - C @ x
         np.add.at(dref, idx, e)
         np.add.at(cx, idx, np.abs(C) @ np.abs(x))
     err = np.linalg.norm(d - dref)

@@ -162,21 +162,34 @@ def cube16_hole_channels(seed=2):
                     np.ones(n ** 3), 1e-4, (4, 4, 4), 1, 0.1, f)
 
 
-def beam128_layered(seed=4, nrhs=16):
+def beam128_layered(seed=4, nrhs=16, nx=128, name="beam128_layered", gamma=1e-6,
+                    contrast=1e6):
     """128x16x16 cells (h=1/16), two 4x4-cell through-holes along x
     (y in [3,7) and [9,13), z in [6,10)); mu^-1 alternating 1 and 1e6 every
     8 cells in x; eps=1; gamma=1e-6; 16 seeded uniform right-hand sides;
-    32x4x4 boxes, overlap 1."""
-    nx, ny, nz = 128, 16, 16
+    32x4x4 boxes (one box per 4 cells along x), overlap 1."""
+    ny, nz = 16, 16
     rng = np.random.default_rng(seed)
     ci, cj, ck = _cell_ijk(nx, ny, nz)
     active = np.ones(nx * ny * nz, dtype=np.uint8)
     for j0, j1 in ((3, 7), (9, 13)):
         active[(cj >= j0) & (cj < j1) & (ck >= 6) & (ck < 10)] = 0
-    mu = np.where((ci // 8) % 2 == 0, 1.0, 1e6)
+    mu = np.where((ci // 8) % 2 == 0, 1.0, contrast)
     f = _uniform_f(rng, (nx + 1) * (ny + 1) * (nz + 1), nrhs)
-    return Workload("beam128_layered", nx, ny, nz, 1 / 16, 1 / 16, 1 / 16, active, mu,
-                    np.ones(nx * ny * nz), 1e-6, (32, 4, 4), 1, 0.1, f)
+    return Workload(name, nx, ny, nz, 1 / 16, 1 / 16, 1 / 16, active, mu,
+                    np.ones(nx * ny * nz), gamma, (nx // 4, 4, 4), 1, 0.1, f)
+
+
+def beam128_mild(seed=4, nrhs=16):
+    """beam128_layered with gamma = 1e-3 and a 1e3 jump of mu^-1, where the
+    float32 and bfloat16 split local factors stay definite."""
+    return beam128_layered(seed, nrhs, name="beam128_mild", gamma=1e-3, contrast=1e3)
+
+
+def beam64_layered(seed=4, nrhs=16):
+    """Profiling-size companion of beam128_layered: the same beam cut to
+    64 cells along x (16x4x4 boxes)."""
+    return beam128_layered(seed, nrhs, nx=64, name="beam64_layered")
 
 
 def cube48_blocks(seed=5):
