@@ -76,6 +76,7 @@ extern "C" {
 
 /* Opaque context: owns every device allocation of one set-up problem. */
 typedef struct geneo_ctx geneo_ctx;
+typedef struct geneo_mlp geneo_mlp;  /* warm-start network (see the end of this header) */
 
 /* Problem description; arrays are host memory, copied during geneo_setup. */
 typedef struct {
@@ -108,6 +109,11 @@ typedef struct {
   int32_t gradient_shift;    /* 1: invert A~_j = A_j + rho_j A_j G_j S_j^-1 G_j^T A_j instead of
                                 A_j (same C_j and A_j^-1 exactly, see Sec. 2 eq. "inverseBw";
                                 needed when gamma makes A_j numerically singular); 0: off */
+  int32_t keep_eigvecs;      /* 1: keep the first 8 locked eigenvectors of every subdomain and
+                                the edge features (training data of the warm-start network) */
+  const struct geneo_mlp *warm_start;  /* non-NULL: the first LOBPCG block of every subdomain
+                                is this network's output on the edge features (needs
+                                lobpcg_block == 8); NULL: seeded random block */
 } geneo_options;
 
 typedef struct {
@@ -133,7 +139,11 @@ typedef struct {
 } geneo_solve_info;
 
 /* Fills `opt` with the defaults: FP64, SNK coarse space, GenEO on,
- * reciprocal tau, LOBPCG block 8, 200 iterations, tolerance 1e-8, seed 1,
+ * reciprocal tau, LOBPCG block 8, 200 iterations, tolerance 1e-8 (a block
+ * whose relative residual has stopped decreasing for 10 iterations is
+ * accepted below 1e-4: under a 1e6 contrast of mu^-1 the local residuals
+ * stall near 1e-6, where the eigenvalues are already accurate to ~1e-10),
+ * seed 1,
  * sparse coarse factor, PCG iteration as a CUDA graph. */
 void geneo_default_options(geneo_options *opt);
 
@@ -266,6 +276,36 @@ int geneo_export(const geneo_ctx *ctx, const char *name, void *dst, int64_t capa
  * dim outside [1, 4096]), TIMEOUT (a bounded device wait gave up), CUDA. */
 int geneo_symv_packed_noalloc(const double *tiles_dev, int32_t dim, const double *x_dev,
                               double *y_dev, void *stream);
+
+/* ---- Learned warm start of the local eigensolves (the GEVPs of Sec. 3.2,
+ * GEVP "tauthresholdAS").  The paper solves them directly; this network
+ * (5 -> 128 -> 128 -> 8, ReLU, bfloat16 weights, float32 accumulation) maps
+ * per-edge features (log10 mu^-1 of the edge's tetrahedra / 6, hop distance
+ * to the subdomain's artificial boundary / 8, |unit edge direction|) to the
+ * first LOBPCG block.  It is trained on eigenvectors the exact set-up
+ * produced (options.keep_eigvecs = 1) with the subspace loss
+ *   L_j = ||(I - V V^T B) X||^2 / ||X||^2 + 0.1 ||X^T B X - I||^2
+ * averaged over subdomains with eigenvectors (B = A_j^Neu, V the locked
+ * eigenvectors, X the network's block).  The network lives on the device that
+ * was current at creation. */
+int geneo_mlp_create(uint64_t seed, geneo_mlp **out);  /* He-normal weights, zero biases */
+void geneo_mlp_destroy(geneo_mlp *mlp);
+int64_t geneo_mlp_param_count(void);                   /* 18312 */
+/* float32 master parameters, layout W1[128][5] b1[128] W2[128][128] b2[128]
+ * W3[8][128] b3[8]; host arrays of geneo_mlp_param_count() floats */
+int geneo_mlp_get_params(const geneo_mlp *mlp, float *host);
+int geneo_mlp_set_params(geneo_mlp *mlp, const float *host);  /* also resets Adam */
+/* loss on ctx's kept eigenvectors and its parameter gradient (host, may be
+ * NULL), with the network's current bfloat16 weights */
+int geneo_mlp_loss_grad(geneo_mlp *mlp, geneo_ctx *ctx, double *loss, float *grad_host,
+                        void *stream);
+/* `steps` full-batch Adam steps (learning rate lr) on ctx's kept
+ * eigenvectors; loss_host[steps] (may be NULL) receives the loss before each */
+int geneo_mlp_train(geneo_mlp *mlp, geneo_ctx *ctx, int32_t steps, double lr, double *loss_host,
+                    void *stream);
+/* X_dev (device, 8 x loc_vlen doubles, loc_vlen from geneo_export("loc_vlen"))
+ * = the network's block on ctx's padded local rows (needs ctx features) */
+int geneo_mlp_infer(const geneo_mlp *mlp, geneo_ctx *ctx, double *X_dev, void *stream);
 
 /* Message of the last error of this thread. */
 const char *geneo_last_error(void);

@@ -37,7 +37,8 @@ class Options(C.Structure):
                 ("tau_convention", C.c_int32), ("lobpcg_block", C.c_int32),
                 ("lobpcg_maxit", C.c_int32), ("lobpcg_tol", C.c_double), ("seed", C.c_uint64),
                 ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32),
-                ("use_graph", C.c_int32), ("gradient_shift", C.c_int32)]
+                ("use_graph", C.c_int32), ("gradient_shift", C.c_int32),
+                ("keep_eigvecs", C.c_int32), ("warm_start", C.c_void_p)]
 
 
 class Sizes(C.Structure):
@@ -95,6 +96,16 @@ _SIGS = {
     "geneo_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "geneo_symv_packed_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                             C.c_void_p]),
+    "geneo_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
+    "geneo_mlp_destroy": (None, [C.c_void_p]),
+    "geneo_mlp_param_count": (C.c_int64, []),
+    "geneo_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "geneo_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "geneo_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                      C.c_void_p, C.c_void_p]),
+    "geneo_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                                  C.c_void_p]),
+    "geneo_mlp_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "geneo_last_error": (C.c_char_p, []),
     "geneo_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -106,6 +117,8 @@ _EXPORT_DTYPES = {
     "geneo_sub": np.int32, "geneo_lambda": np.float64, "geneo_found": np.int32,
     "Zcol_ptr": np.int64, "Zcol_row": np.int32, "Zcol_val": np.float64, "k0k1": np.int32,
     "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
+    "loc_vlen": np.int64, "mlp_features": np.float32, "eig_V": np.float64, "eig_nq": np.int32,
+    "lobpcg_iters": np.int32,
 }
 
 
@@ -277,3 +290,58 @@ class Solver:
         _check(_LIB.geneo_export(self._ctx, name.encode(), out.ctypes.data_as(C.c_void_p),
                                  size.value, C.byref(size)))
         return out
+
+
+class Mlp:
+    """Warm-start network of the local eigensolves (5 -> 128 -> 128 -> 8),
+    on the current CUDA device."""
+
+    def __init__(self, seed=0):
+        lib = load_library()
+        h = C.c_void_p()
+        _check(lib.geneo_mlp_create(seed, C.byref(h)))
+        self._h = h
+        self.nparam = lib.geneo_mlp_param_count()
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(_LIB.geneo_mlp_get_params(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparam
+        _check(_LIB.geneo_mlp_set_params(self._h, p.ctypes.data_as(C.c_void_p)))
+
+    def loss_grad(self, solver, stream=None):
+        loss = C.c_double()
+        g = np.empty(self.nparam, dtype=np.float32)
+        _check(_LIB.geneo_mlp_loss_grad(self._h, solver._ctx, C.byref(loss),
+                                        g.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return loss.value, g
+
+    def train(self, solver, steps, lr=1e-3, stream=None):
+        losses = np.empty(steps, dtype=np.float64)
+        _check(_LIB.geneo_mlp_train(self._h, solver._ctx, steps, lr,
+                                    losses.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return losses
+
+    def infer(self, solver, X, stream=None):
+        """X: CUDA float64 tensor of 8 * loc_vlen (padded local rows)."""
+        _check(_LIB.geneo_mlp_infer(self._h, solver._ctx, _ptr(X), _stream(stream)))
+        return X
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _LIB.geneo_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

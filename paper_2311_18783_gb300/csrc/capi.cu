@@ -106,6 +106,10 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
     return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
   if (o.lobpcg_block < 1 || o.lobpcg_block > 16 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
     return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");
+  if (o.warm_start && o.lobpcg_block != 8)
+    return fail(GENEO_ERR_INVALID_ARG, "a warm start needs lobpcg_block = 8");
+  if (o.keep_eigvecs != 0 && o.keep_eigvecs != 1)
+    return fail(GENEO_ERR_INVALID_ARG, "keep_eigvecs must be 0 or 1");
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
       (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
@@ -350,6 +354,17 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
     } else if (nm == "loc_nt") put(c->loc.nt.data(), c->loc.nt.size() * 4);
     else if (nm == "loc_toff") put(c->loc.toff.data(), c->loc.toff.size() * 8);
     else if (nm == "loc_voff") put(c->loc.voff.data(), c->loc.voff.size() * 8);
+    else if (nm == "loc_vlen") {
+      const int64_t v = c->loc.vlen;
+      put(&v, 8);
+    } else if (nm == "mlp_features") {
+      auto v = c->d_feat.download(c->stream);
+      put(v.data(), v.size() * 4);
+    } else if (nm == "eig_V") {
+      auto v = c->eigV.download(c->stream);
+      put(v.data(), v.size() * 8);
+    } else if (nm == "eig_nq") put(c->eig_nq.data(), c->eig_nq.size() * 4);
+    else if (nm == "lobpcg_iters") put(c->lobpcg_iters.data(), c->lobpcg_iters.size() * 4);
     else if (nm == "k0k1") {
       int32_t k[2] = {c->dec.k0, c->dec.k1};
       put(k, 8);
@@ -360,6 +375,83 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
       if (cap < (int64_t)buf.size()) return fail(GENEO_ERR_INVALID_ARG, "buffer too small");
       if (!buf.empty()) std::memcpy(dst, buf.data(), buf.size());
     }
+    return GENEO_OK;
+  });
+}
+
+int geneo_mlp_create(uint64_t seed, geneo_mlp **out) {
+  if (!out) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  return guarded([&]() {
+    auto h = new geneo_mlp();
+    try {
+      h->m = geneo::mlp_create(seed);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return GENEO_OK;
+  });
+}
+
+void geneo_mlp_destroy(geneo_mlp *mlp) {
+  if (!mlp) return;
+  geneo::mlp_destroy(mlp->m);
+  delete mlp;
+}
+
+int64_t geneo_mlp_param_count(void) { return geneo::mlp_param_count(); }
+
+int geneo_mlp_get_params(const geneo_mlp *mlp, float *host) {
+  if (!mlp || !host) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    auto w = geneo::mlp_get(mlp->m);
+    std::memcpy(host, w.data(), w.size() * sizeof(float));
+    return GENEO_OK;
+  });
+}
+
+int geneo_mlp_set_params(geneo_mlp *mlp, const float *host) {
+  if (!mlp || !host) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::mlp_set(mlp->m, std::vector<float>(host, host + geneo::mlp_param_count()));
+    return GENEO_OK;
+  });
+}
+
+int geneo_mlp_loss_grad(geneo_mlp *mlp, geneo_ctx *c, double *loss, float *grad_host, void *s) {
+  if (!mlp || !c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    const double l = geneo::mlp_loss_grad(mlp->m, c, as_stream(s));
+    if (loss) *loss = l;
+    if (grad_host) {
+      auto g = geneo::mlp_grad_host(mlp->m, as_stream(s));
+      std::memcpy(grad_host, g.data(), g.size() * sizeof(float));
+    }
+    return GENEO_OK;
+  });
+}
+
+int geneo_mlp_train(geneo_mlp *mlp, geneo_ctx *c, int32_t steps, double lr, double *loss_host,
+                    void *s) {
+  if (!mlp || !c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (steps < 0 || !(lr > 0)) return fail(GENEO_ERR_INVALID_ARG, "steps >= 0, lr > 0");
+  return guarded([&]() {
+    for (int i = 0; i < steps; ++i) {
+      const double l = geneo::mlp_loss_grad(mlp->m, c, as_stream(s));
+      if (loss_host) loss_host[i] = l;
+      geneo::mlp_adam(mlp->m, lr, as_stream(s));
+    }
+    GENEO_CUDA(cudaStreamSynchronize(as_stream(s)));
+    return GENEO_OK;
+  });
+}
+
+int geneo_mlp_infer(const geneo_mlp *mlp, geneo_ctx *c, double *X, void *s) {
+  if (!mlp || !c || !X) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::mlp_infer(mlp->m, c, X, as_stream(s));
     return GENEO_OK;
   });
 }

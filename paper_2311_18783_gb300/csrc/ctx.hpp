@@ -16,7 +16,13 @@ struct TcFactors;
 struct TcDeleter {
   void operator()(TcFactors *t) const;
 };
+struct Mlp;
 }  // namespace geneo
+
+// public handle of a warm-start network
+struct geneo_mlp {
+  geneo::Mlp *m = nullptr;
+};
 
 struct geneo_ctx {
   // problem copy
@@ -72,6 +78,11 @@ struct geneo_ctx {
   // local operators (xi, S_j^-1, element data) for GenEO and the split solve
   std::unique_ptr<geneo::XiOp> xi;
   int local_prec = GENEO_PREC_FP64;  // precision used by the local solves
+  // warm start of the local eigensolves: edge features [loc.vlen][5]; the
+  // locked eigenvectors (first 8 per subdomain, and B times them) when kept
+  geneo::DevBuf<float> d_feat;
+  geneo::DevBuf<double> eigV, eigBV;
+  std::vector<int32_t> eig_nq, lobpcg_iters;
   // bfloat16 super-tiles of C_j for the tensor-core local solves
   std::unique_ptr<geneo::TcFactors, geneo::TcDeleter> tc;
 

@@ -840,14 +840,19 @@ void geneo_eigenvectors(geneo_ctx *c) {
   const double tau = c->tau_p, tol = c->opt.lobpcg_tol;
   std::vector<uint8_t> done(L.nsub, 0);
   std::vector<std::vector<double>> lam_locked(L.nsub);
+  c->lobpcg_iters.assign(L.nsub, 0);
   const int ld = L.ld;
   for (int round = 0;; ++round) {
     bool any = false;
     for (int m = 0; m < L.nsub; ++m) any |= !done[m];
     if (!any) break;
-    // fresh block, B-orthogonal to the locked vectors, B-orthonormal
-    k_rand_block<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.X.p, k, L.vlen, c->d_l2g.p, c->opt.seed,
-                                                       (uint64_t)round);
+    // fresh block, B-orthogonal to the locked vectors, B-orthonormal; the
+    // first block comes from the warm-start network when one is given
+    if (round == 0 && c->opt.warm_start)
+      mlp_infer(c->opt.warm_start->m, c, L.X.p, s);
+    else
+      k_rand_block<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.X.p, k, L.vlen, c->d_l2g.p,
+                                                         c->opt.seed, (uint64_t)round);
     project_gradients_B(L, L.X.p, k);
     apply_B(L, L.X.p, L.BX.p, k);
     b_orthogonalize(L, L.X, nullptr, nullptr, 0, true, k);
@@ -865,6 +870,10 @@ void geneo_eigenvectors(geneo_ctx *c) {
     std::swap(L.BX.p, L.T1.p);
     bool have_p = false;
     std::vector<uint8_t> finished(L.nsub, 0);
+    // stall detection: best largest relative residual of the block so far
+    // and the iterations since it last dropped by 10%
+    std::vector<double> best(L.nsub, 1e300);
+    std::vector<int> stall(L.nsub, 0);
     for (int m = 0; m < L.nsub; ++m) finished[m] = done[m];
     for (int it = 0; it < c->opt.lobpcg_maxit; ++it) {
       k_resid<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.LX.p, L.BX.p, L.theta.p, k, L.op.pos_sub.p,
@@ -889,18 +898,33 @@ void geneo_eigenvectors(geneo_ctx *c) {
           std::fprintf(stderr, "\n");
         }
       }
+      for (int m = 0; m < L.nsub; ++m) c->lobpcg_iters[m] += !finished[m];
       // lock / finish decisions
       std::vector<int32_t> srcc((size_t)L.nsub * k, -1), dstc((size_t)L.nsub * k, -1);
       bool moves = false;
       int need = 0;
       for (int m = 0; m < L.nsub; ++m) {
         if (finished[m]) continue;
+        double worst = 0.0;
+        for (int j = 0; j < k; ++j) {
+          const double rn = std::sqrt(std::max(gr[(size_t)m * ld * ld + j * ld + j], 0.0));
+          const double bn = std::sqrt(std::max(gb[(size_t)m * ld * ld + j * ld + j], 0.0));
+          const double sc = std::max(std::fabs(th[m * k + j]), tau) * bn;
+          if (bn > 0.0) worst = std::max(worst, rn / sc);
+        }
+        if (worst < 0.9 * best[m]) {
+          best[m] = worst;
+          stall[m] = 0;
+        } else {
+          ++stall[m];
+        }
+        const double tol_m = stall[m] >= 10 ? std::max(tol, 1e-4) : tol;
         int lead = 0;
         for (int j = 0; j < k; ++j) {
           const double rn = std::sqrt(std::max(gr[(size_t)m * ld * ld + j * ld + j], 0.0));
           const double bn = std::sqrt(std::max(gb[(size_t)m * ld * ld + j * ld + j], 0.0));
           const double sc = std::max(std::fabs(th[m * k + j]), tau) * bn;
-          if (rn <= tol * sc || bn == 0.0) ++lead;
+          if (rn <= tol_m * sc || bn == 0.0) ++lead;
           else break;
         }
         bool fin = false, stop = false;
@@ -1033,10 +1057,12 @@ void geneo_eigenvectors(geneo_ctx *c) {
         std::swap(L.LP.p, L.T2.p);
         std::swap(L.BP.p, L.T3.p);
         combine(L, cat(lx, lw, lp), L.tmat.p, k, L.T1.p);  // LX_new
-        combine(L, cat(bx, bw, bp), L.tmat.p, k, L.T2.p);  // BX_new
         std::swap(L.X.p, L.R.p);
-        std::swap(L.LX.p, L.T1.p);
-        std::swap(L.BX.p, L.T2.p);
+        // L X and B X recomputed from X: the combined images carry the
+        // rounding of ||L|| ||W|| (large for high-contrast mu^-1), which
+        // stalls the residual far above the tolerance
+        apply_L(L, L.X.p, L.LX.p, k);
+        apply_B(L, L.X.p, L.BX.p, k);
         have_p = true;
       }
       check_device_error(c, s);
@@ -1048,6 +1074,24 @@ void geneo_eigenvectors(geneo_ctx *c) {
   for (int v : L.nq) maxq = std::max(maxq, v);
   c->geneo_found.assign(L.nsub, 0);
   for (int m = 0; m < L.nsub; ++m) c->geneo_found[m] = L.nq[m];
+  if (c->opt.keep_eigvecs) {
+    // training targets of the warm-start network: the first 8 locked
+    // eigenvectors of every subdomain (B-orthonormal) and B times them
+    const int qc = std::min(maxq, 8);
+    c->eigV.alloc(8 * L.vlen);
+    c->eigBV.alloc(8 * L.vlen);
+    c->eigV.zero(s);
+    c->eigBV.zero(s);
+    if (qc > 0) {
+      GENEO_CUDA(cudaMemcpyAsync(c->eigV.p, L.Q.p, sizeof(double) * L.vlen * qc,
+                                 cudaMemcpyDeviceToDevice, s));
+      GENEO_CUDA(cudaMemcpyAsync(c->eigBV.p, L.BQ.p, sizeof(double) * L.vlen * qc,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    c->eig_nq.assign(L.nsub, 0);
+    for (int m = 0; m < L.nsub; ++m) c->eig_nq[m] = std::min(L.nq[m], 8);
+    GENEO_CUDA(cudaStreamSynchronize(s));
+  }
   if (maxq == 0) return;
   DevBuf<double> V;
   V.alloc(L.vlen * maxq);
@@ -1108,6 +1152,15 @@ void build_split_factors(geneo_ctx *c) {
 
 // yl += G_j S_j^-1 G_j^T xl for every subdomain (float64 gradient part of the
 // split local inverse), on padded local vectors
+void apply_neumann(geneo_ctx *c, const double *x, double *y, int k, cudaStream_t s) {
+  XiOp &op = *c->xi;
+  k_local_csr<<<grid_for(op.nslots * k, 256), 256, 0, s>>>(op.lrp.p, op.lcol.p, op.nval.p,
+                                                           op.slot_sub.p, op.Noff.p,
+                                                           c->loc.d_voff.p, op.nslots, k,
+                                                           c->loc.vlen, x, y);
+  GENEO_CHECK_LAUNCH();
+}
+
 void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k,
                           const double *scale) {
   XiOp &op = *c->xi;

@@ -14,6 +14,7 @@
 
 #include "ctx.hpp"
 #include "setup.hpp"
+#include "xi.hpp"
 
 namespace geneo {
 
@@ -698,6 +699,13 @@ void setup_all(geneo_ctx *c) {
   }
   if (c->zc_ptr.empty()) c->zc_ptr.push_back(0);
   if (c->opt.geneo) {
+    if (c->opt.warm_start || c->opt.keep_eigvecs) {
+      if (!c->xi) {
+        c->xi.reset(new XiOp());
+        build_xi_operator(c, *c->xi, s);
+      }
+      build_mlp_features(c);
+    }
     geneo_eigenvectors(c);  // appends GenEO candidates to zc_* and sets n0_geneo
     if (c->n0_geneo > 0) geneo_filter(c);
   }

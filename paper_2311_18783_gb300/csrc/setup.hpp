@@ -55,6 +55,22 @@ void build_split_factors(geneo_ctx *c);
 void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream_t s, int k = 1,
                           const double *scale = nullptr);
 void apply_gradient_shift(geneo_ctx *c);
+// y = A_j^Neu x for k columns of local vectors (the right-hand operator B of
+// the local generalised eigenproblems)
+void apply_neumann(geneo_ctx *c, const double *x, double *y, int k, cudaStream_t s);
+
+// learned warm start (mlp.cu)
+struct Mlp;
+int mlp_param_count();
+Mlp *mlp_create(uint64_t seed);
+void mlp_destroy(Mlp *M);
+std::vector<float> mlp_get(const Mlp *M);
+void mlp_set(Mlp *M, const std::vector<float> &w);
+void mlp_infer(const Mlp *M, geneo_ctx *c, double *X, cudaStream_t s);
+double mlp_loss_grad(Mlp *M, geneo_ctx *c, cudaStream_t s);
+void mlp_adam(Mlp *M, double lr, cudaStream_t s);
+std::vector<float> mlp_grad_host(const Mlp *M, cudaStream_t s);
+void build_mlp_features(geneo_ctx *c);
 void split_tc_apply(geneo_ctx *c, const double *xl, double *yl, double *xp, cudaStream_t s, int k,
                     cudaEvent_t e0, cudaEvent_t e1);
 

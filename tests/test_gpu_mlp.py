@@ -1,0 +1,122 @@
+"""Learned warm start of the local eigensolves, against the float64 oracle
+(oracle/mlp.py) and against the method without it.
+
+* Edge features of every subdomain equal the oracle's (float32 rounding).
+* Loss and parameter gradient of the network's bfloat16 weights equal the
+  oracle's float64 loss and backward pass evaluated with the same weights,
+  the same (library-computed) eigenvectors and the oracle's own A_j^Neu:
+  relative 1e-3 (the network runs in float32).
+* Full-batch Adam on the GPU reduces the loss.
+* Gain: on a held-out coefficient draw, the trained network's block keeps a
+  smaller part outside the exact eigenspace than the untrained one, and the
+  warm-started set-up finds the same GenEO space (same counts per subdomain)
+  while the LOBPCG iteration counts are reported for both starts.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _blocks(seed, n=12, parts=(2, 2, 2)):
+    """n^3 unit cube, mu^-1 log-uniform in [1, 1e6] on 3x3x3-cell blocks,
+    gamma 1e-3 (the layout of the 48^3 warm-start workload, smaller); the
+    eigenproblems keep lambda > 3 (paper convention), so that most
+    subdomains have several eigenvectors to learn from."""
+    rng = np.random.default_rng(seed)
+    nb = (n + 2) // 3
+    blk = 10.0 ** rng.uniform(0, 6, nb ** 3)
+    c = np.arange(n ** 3)
+    i, j, k = c % n, (c // n) % n, c // (n * n)
+    mu = blk[(i // 3) + nb * ((j // 3) + nb * (k // 3))]
+    return W.box(n, n, n, parts=parts, overlap=1, gamma=1e-3, mu_inv=mu, f='random', seed=seed,
+                 tau=3.0)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    import paper_2311_18783_gb300 as pkg
+    w = _blocks(100)
+    s = pkg.Solver.from_workload(w, keep_eigvecs=1, tau_convention=pkg.TAU_PAPER)
+    net = pkg.Mlp(seed=7)
+    yield pkg, w, s, net
+    net.close()
+    s.close()
+
+
+def test_features_match_oracle(trained):
+    from oracle.mesh import build_mesh
+    from oracle.dd import decompose
+    from oracle.mlp import edge_features
+    pkg, w, s, net = trained
+    F = s.export("mlp_features").reshape(-1, 5)
+    voff = s.export("loc_voff")
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    dec = decompose(m, w.parts, w.overlap)
+    for j in range(dec.nsub):
+        ref = edge_features(m, w, dec, j)
+        got = F[voff[j]:voff[j] + len(dec.N[j])]
+        assert np.abs(got - ref).max() <= 1e-6
+
+
+def test_loss_and_gradient_match_oracle(trained):
+    from oracle import mlp as om
+    from oracle.mesh import build_mesh
+    from oracle.fem import local_element_A
+    from oracle.dd import decompose, local_neumann
+    pkg, w, s, net = trained
+    theta = net.params()
+    # the library evaluates with bfloat16 weights: the oracle gets the same
+    tb = torch.as_tensor(theta).to(torch.bfloat16).to(torch.float64).numpy()
+    loss, grad = net.loss_grad(s)
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    dec = decompose(m, w.parts, w.overlap)
+    AT = local_element_A(m, w)
+    F = s.export("mlp_features").reshape(-1, 5).astype(np.float64)
+    voff = s.export("loc_voff")
+    vlen = int(s.export("loc_vlen")[0])
+    V = s.export("eig_V").reshape(8, vlen)
+    nq = s.export("eig_nq")
+    assert nq.max() > 0
+    Fl, Vl, Bl = [], [], []
+    for j in range(dec.nsub):
+        n = len(dec.N[j])
+        Fl.append(F[voff[j]:voff[j] + n])
+        Vl.append(V[:nq[j], voff[j]:voff[j] + n].T.copy())
+        Bl.append(np.asarray(local_neumann(m, AT, dec, j)))
+    ref_loss, ref_grad = om.loss_and_grad(tb, Fl, Vl, Bl)
+    assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss)
+    assert np.linalg.norm(grad - ref_grad) <= 1e-3 * np.linalg.norm(ref_grad)
+
+
+def test_training_reduces_loss(trained):
+    pkg, w, s, net = trained
+    losses = net.train(s, 300, lr=2e-3)
+    print(f"loss {losses[0]:.4f} -> {losses[-1]:.4f}")
+    assert losses[-1] < 0.8 * losses[0]
+
+
+def test_warm_start_gain(trained):
+    pkg, w, s, net = trained
+    # held-out draw of the same family
+    w2 = _blocks(101)
+    s_cold = pkg.Solver.from_workload(w2, keep_eigvecs=1, tau_convention=pkg.TAU_PAPER)
+    untrained = pkg.Mlp(seed=7)
+    l_trained, _ = net.loss_grad(s_cold)
+    l_untrained, _ = untrained.loss_grad(s_cold)
+    s_warm = pkg.Solver.from_workload(w2, keep_eigvecs=1, tau_convention=pkg.TAU_PAPER,
+                                      warm_start=net.handle)
+    it_cold = s_cold.export("lobpcg_iters")
+    it_warm = s_warm.export("lobpcg_iters")
+    print(f"held-out subspace loss: trained {l_trained:.4f}, untrained {l_untrained:.4f}; "
+          f"LOBPCG iterations cold {it_cold.sum()} (max {it_cold.max()}), "
+          f"warm {it_warm.sum()} (max {it_warm.max()})")
+    assert l_trained < l_untrained
+    assert list(s_warm.export("geneo_found")) == list(s_cold.export("geneo_found"))
+    assert s_warm.sizes["n0"] == s_cold.sizes["n0"]
+    untrained.close()
+    s_cold.close()
+    s_warm.close()
