@@ -31,6 +31,7 @@ METRIC = "PCG time-to-1e-8 (s)"
 TOL = 1e-8
 WORKLOAD = "cube32_hole_channels"
 BLOCK_WORKLOAD = "beam128_layered"
+WARM_WORKLOAD = "cube24_blocks"
 
 
 def parse():
@@ -44,7 +45,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "cube16_hole_channels", BLOCK_WORKLOAD, "beam128_mild",
-                            "beam64_layered"],
+                            "beam64_layered", WARM_WORKLOAD],
                    help="cube16_hole_channels: the profiling-size companion (ncu captures); "
                         f"{BLOCK_WORKLOAD}: 16 right-hand sides as a block, bfloat16 local "
                         "factors on the tensor cores")
@@ -347,6 +348,62 @@ def run_block(args):
         dist.destroy_process_group()
 
 
+def run_warm(args):
+    """Learned warm start on cube24_blocks (64 subdomains of the 48^3 blocks
+    workload's size, mu^-1 in [1, 1e6] on 3^3-cell blocks): the network is
+    trained on the eigenvectors the exact set-up produces for 4 coefficient
+    draws (4 x 64 local eigenproblems), then the held-out draw of the
+    workload is set up cold and warm.  Reports
+    GenEO set-up time, LOBPCG iterations (first block and all) and the GenEO
+    counts of both starts (the method's result must not change)."""
+    import torch
+    import numpy as np
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import workloads as W
+    import paper_2311_18783_gb300 as pkg
+    net = pkg.Mlp(seed=7)
+    t_train, losses = 0.0, []
+    for seed in (100, 101, 102, 103):
+        s = pkg.Solver.from_workload(W.cube24_blocks(seed), keep_eigvecs=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ls = net.train(s, 150, lr=2e-3)
+        torch.cuda.synchronize()
+        t_train += time.perf_counter() - t0
+        losses.append([float(ls[0]), float(ls[-1])])
+        s.close()
+    w = W.cube24_blocks()
+    out = {}
+    for name, kw in (("cold", {}), ("warm", {"warm_start": net.handle})):
+        t0 = time.perf_counter()
+        s = pkg.Solver.from_workload(w, keep_eigvecs=1, **kw)
+        setup = time.perf_counter() - t0
+        loss, _ = net.loss_grad(s)
+        b = torch.empty(s.n, dtype=torch.float64, device="cuda")
+        s.assemble_rhs(w.f_slot[0], b)
+        x = torch.zeros_like(b)
+        info = s.solve(b, x, tol=TOL, maxit=1000)
+        out[name] = {"setup_s": setup, "lobpcg_iters_first_block": int(s.export("lobpcg_iters_first").sum()),
+                     "lobpcg_iters_all": int(s.export("lobpcg_iters").sum()),
+                     "geneo_found": int(s.export("geneo_found").sum()),
+                     "n0_geneo": s.sizes["n0_geneo"], "pcg_iters": info["iters"],
+                     "trained_net_subspace_loss": loss}
+        found = s.export("geneo_found")
+        out[name]["_found"] = found
+        s.close()
+    same = bool(np.array_equal(out["cold"].pop("_found"), out["warm"].pop("_found")))
+    line = {"metric": "GenEO set-up time with the learned warm start (s)",
+            "value": out["warm"]["setup_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": False, "vs_baseline": None, "dtype": "f64 (network bf16)",
+            "data": "synthetic",
+            "config": {"workload": WARM_WORKLOAD, "train_draws": [100, 101, 102, 103],
+                       "train_steps_per_draw": 150, "train_seconds": t_train,
+                       "train_loss_first_last": losses, "held_out_seed": 5},
+            "cold": out["cold"], "warm": out["warm"], "same_geneo_counts": same}
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -354,6 +411,9 @@ def main():
         return
     if args.workload in (BLOCK_WORKLOAD, "beam128_mild", "beam64_layered"):
         run_block(args)
+        return
+    if args.workload == WARM_WORKLOAD:
+        run_warm(args)
         return
     import torch
     import torch.distributed as dist

@@ -118,7 +118,7 @@ _EXPORT_DTYPES = {
     "Zcol_ptr": np.int64, "Zcol_row": np.int32, "Zcol_val": np.float64, "k0k1": np.int32,
     "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
     "loc_vlen": np.int64, "mlp_features": np.float32, "eig_V": np.float64, "eig_nq": np.int32,
-    "lobpcg_iters": np.int32,
+    "lobpcg_iters": np.int32, "lobpcg_iters_first": np.int32,
 }
 
 

@@ -365,6 +365,7 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
       put(v.data(), v.size() * 8);
     } else if (nm == "eig_nq") put(c->eig_nq.data(), c->eig_nq.size() * 4);
     else if (nm == "lobpcg_iters") put(c->lobpcg_iters.data(), c->lobpcg_iters.size() * 4);
+    else if (nm == "lobpcg_iters_first") put(c->lobpcg_iters0.data(), c->lobpcg_iters0.size() * 4);
     else if (nm == "k0k1") {
       int32_t k[2] = {c->dec.k0, c->dec.k1};
       put(k, 8);

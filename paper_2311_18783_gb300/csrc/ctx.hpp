@@ -82,7 +82,7 @@ struct geneo_ctx {
   // locked eigenvectors (first 8 per subdomain, and B times them) when kept
   geneo::DevBuf<float> d_feat;
   geneo::DevBuf<double> eigV, eigBV;
-  std::vector<int32_t> eig_nq, lobpcg_iters;
+  std::vector<int32_t> eig_nq, lobpcg_iters, lobpcg_iters0;  // iterations: all rounds, first round
   // bfloat16 super-tiles of C_j for the tensor-core local solves
   std::unique_ptr<geneo::TcFactors, geneo::TcDeleter> tc;
 

@@ -841,6 +841,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
   std::vector<uint8_t> done(L.nsub, 0);
   std::vector<std::vector<double>> lam_locked(L.nsub);
   c->lobpcg_iters.assign(L.nsub, 0);
+  c->lobpcg_iters0.assign(L.nsub, 0);
   const int ld = L.ld;
   for (int round = 0;; ++round) {
     bool any = false;
@@ -898,7 +899,10 @@ void geneo_eigenvectors(geneo_ctx *c) {
           std::fprintf(stderr, "\n");
         }
       }
-      for (int m = 0; m < L.nsub; ++m) c->lobpcg_iters[m] += !finished[m];
+      for (int m = 0; m < L.nsub; ++m) {
+        c->lobpcg_iters[m] += !finished[m];
+        if (round == 0) c->lobpcg_iters0[m] += !finished[m];
+      }
       // lock / finish decisions
       std::vector<int32_t> srcc((size_t)L.nsub * k, -1), dstc((size_t)L.nsub * k, -1);
       bool moves = false;

@@ -111,8 +111,11 @@ def test_warm_start_gain(trained):
                                       warm_start=net.handle)
     it_cold = s_cold.export("lobpcg_iters")
     it_warm = s_warm.export("lobpcg_iters")
+    f_cold = s_cold.export("lobpcg_iters_first")
+    f_warm = s_warm.export("lobpcg_iters_first")
     print(f"held-out subspace loss: trained {l_trained:.4f}, untrained {l_untrained:.4f}; "
-          f"LOBPCG iterations cold {it_cold.sum()} (max {it_cold.max()}), "
+          f"LOBPCG iterations, first block: cold {f_cold.sum()} warm {f_warm.sum()}; "
+          f"all blocks: cold {it_cold.sum()} (max {it_cold.max()}), "
           f"warm {it_warm.sum()} (max {it_warm.max()})")
     assert l_trained < l_untrained
     assert list(s_warm.export("geneo_found")) == list(s_cold.export("geneo_found"))

@@ -192,17 +192,23 @@ def beam64_layered(seed=4, nrhs=16):
     return beam128_layered(seed, nrhs, nx=64, name="beam64_layered")
 
 
-def cube48_blocks(seed=5):
+def cube48_blocks(seed=5, n=48, parts=8, name="cube48_blocks"):
     """48^3 unit cube, mu^-1 log-uniform in [1,1e6] on 3x3x3-cell blocks,
     gamma=1e-3, 8x8x8 boxes, overlap 1, f=(1,1,1)."""
-    n = 48
     rng = np.random.default_rng(seed)
     ci, cj, ck = _cell_ijk(n, n, n)
-    blk = 10.0 ** rng.uniform(0.0, 6.0, size=(16, 16, 16))
+    nb = (n + 2) // 3
+    blk = 10.0 ** rng.uniform(0.0, 6.0, size=(nb, nb, nb))
     mu = blk[ck // 3, cj // 3, ci // 3]
-    return Workload("cube48_blocks", n, n, n, 1 / n, 1 / n, 1 / n,
+    return Workload(name, n, n, n, 1 / n, 1 / n, 1 / n,
                     np.ones(n ** 3, dtype=np.uint8), mu, np.ones(n ** 3), 1e-3,
-                    (8, 8, 8), 1, 0.1, _const_f((n + 1) ** 3))
+                    (parts, parts, parts), 1, 0.1, _const_f((n + 1) ** 3))
+
+
+def cube24_blocks(seed=5):
+    """cube48_blocks at 24^3 with 4x4x4 boxes (same subdomain size, 64
+    subdomains)."""
+    return cube48_blocks(seed, n=24, parts=4, name="cube24_blocks")
 
 
 def paper_beam(nsub=8, *, gamma=1e-3, tau=0.1):
