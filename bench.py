@@ -72,6 +72,23 @@ SYMV_F32_TRAFFIC_RATIO = (204.3628 + 7.1421) / 203.6859
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 
 
+def max_over_ranks(value, world, device):
+    """Largest value over the ranks: a timed region ends when the slowest rank
+    ends (each rank solves its own replica)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, seconds, world):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -290,11 +307,9 @@ def run_block(args):
     prec_of = {"fp64": pkg.PREC_FP64, "fp32_split": pkg.PREC_FP32,
                "bf16_tensor_cores": pkg.PREC_BF16}
     # headline variant, max over ranks
-    t = torch.tensor([variants[head]["ms"]], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(variants[head]["ms"], world, "cuda")
     s.use_precision(prec_of[head])
     s.solve_block(B, X, tol=TOL, maxit=maxit)
     diff = max((torch.linalg.norm(X[j] - X64[j]) / torch.linalg.norm(X64[j])).item()
@@ -486,11 +501,7 @@ def main():
         dist.barrier()
     prof = s.profile_read()
     s.profile(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     clk = clocks.stop()
     # end to end through the host-buffer entry point (copies inside)
     bh = b.cpu().pin_memory()
@@ -527,7 +538,7 @@ def main():
                                   "cube16_hole_channels, scaled by stored tiles",
                 "algorithmic_bytes_per_launch": prof["local_symv_bytes"],
                 "launch_ms": t_launch * 1e3}
-    applies_per_s = (sum(iters) + len(iters)) / (ms * args.steps / 1e3)
+    applies_per_s = aggregate_rate(sum(iters) + len(iters), ms * args.steps / 1e3, world)
     line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
