@@ -305,7 +305,7 @@ struct Multifrontal {
 
 void MfDeleter::operator()(Multifrontal *m) const { delete m; }
 
-void mf_setup(geneo_ctx *c) {
+void mf_setup(geneo_ctx *c, MfSchur *schur) {
   cudaStream_t s = c->stream;
   const int64_t n0 = c->n0;
   const Topology &t = c->topo;
@@ -465,6 +465,16 @@ void mf_setup(geneo_ctx *c) {
     k_scatter<<<grid_for(nq, 256), 256, 0, s>>>(vals.p, d1.p, d2.p, nq, M->L.p);
     GENEO_CHECK_LAUNCH();
     GENEO_CUDA(cudaStreamSynchronize(s));
+    if (schur) {
+      // diagonal of E on the GenEO columns (pattern entry (a, a))
+      const std::vector<double> hv = vals.download(s);
+      const int64_t ns = c->n0_snk;
+      schur->nh = n0 - ns;
+      schur->diag.assign(schur->nh, 0.0);
+      for (int64_t a = ns; a < n0; ++a)
+        for (int64_t q = P.pptr[a]; q < P.pptr[a + 1]; ++q)
+          if (P.pcol[q] == a) schur->diag[a - ns] = hv[q];
+    }
   }
   // --- per-front metadata on the device
   std::vector<int32_t> h_npiv(nf), h_npivp(nf), h_npivt(nf), h_parent(nf);
@@ -608,9 +618,33 @@ void mf_setup(geneo_ctx *c) {
         k_extend_add<<<Lv.ea_n[sl], 256, 0, s>>>(Lv.ea_child[sl].p, Lv.ea_I[sl].p, Lv.ea_J[sl].p,
                                                   M->parent.p, M->npivp.p, M->nupd.p, d_mapoff.p,
                                                   d_map.p, fb.d_toff.p, M->L.p);
+    if (schur && lv == nlev - 1) break;  // the root (GenEO columns) stays unfactored
     if (Lv.max_npivt > 0)
       chol_factor(fb, M->L.p, Lv.npiv_lvl.p, Lv.max_npivt, M->dinv.p, M->dtoff.p, c->d_err.p, s);
     check_device_error(c, s);
+  }
+  if (schur) {
+    // the root front holds exactly the GenEO columns, in order, at the top level
+    const int r = nf - 1;
+    const int64_t nh = schur->nh;
+    if (F[r].npiv != nh || F[r].level != nlev - 1 || !F[r].upd.empty())
+      throw Error(GENEO_ERR_CUDA, "internal: GenEO root front");
+    check_device_error(c, s);
+    const int64_t ntr = fb.nt[r];
+    std::vector<double> tiles((size_t)(ntr * (ntr + 1) / 2) * kTileElems);
+    GENEO_CUDA(cudaMemcpyAsync(tiles.data(), M->L.p + fb.toff[r] * kTileElems,
+                               sizeof(double) * tiles.size(), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaStreamSynchronize(s));
+    schur->S.assign((size_t)(nh * nh), 0.0);
+    for (int64_t i = 0; i < nh; ++i)
+      for (int64_t j = 0; j <= i; ++j) {
+        const int64_t I = i / kTile, J = j / kTile;
+        const double v =
+            tiles[(size_t)((I * (I + 1) / 2 + J) * kTileElems + (i % kTile) * kTile + j % kTile)];
+        schur->S[i * nh + j] = schur->S[j * nh + i] = v;
+      }
+    c->mf.reset();
+    return;
   }
   // --- inverses of the pivot blocks
   M->Y.alloc(tile_elems(fb));

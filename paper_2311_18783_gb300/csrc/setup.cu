@@ -524,6 +524,19 @@ static Columns coarse_columns(const geneo_ctx *c, int64_t gap_after_snk) {
 // complement E_hh - E_hg E_gg^-1 E_gh is below kDepTol times their diagonal.
 constexpr double kDepTol = 1e-8;
 
+static std::vector<int64_t> ordered_drop(const std::vector<double> &S,
+                                         const std::vector<double> &diag, int64_t nh);
+static void apply_geneo_keep(geneo_ctx *c, const std::vector<int64_t> &keep);
+
+// The same filter through the multifrontal: the root front holds the GenEO
+// columns, so after the fronts below it are factored its pivot block is the
+// Schur complement, without a dense matrix over the split near-kernel.
+static void geneo_filter_mf(geneo_ctx *c) {
+  MfSchur sc;
+  mf_setup(c, &sc);
+  apply_geneo_keep(c, ordered_drop(sc.S, sc.diag, sc.nh));
+}
+
 static void geneo_filter(geneo_ctx *c) {
   cudaStream_t s = c->stream;
   const int64_t ns = c->n0_snk, nh = c->n0_geneo;
@@ -555,9 +568,18 @@ static void geneo_filter(geneo_ctx *c) {
     check_device_error(c, s);
     host = tiles.download(s);
   }
-  std::vector<double> S(nh * nh), Lm(nh * nh, 0.0);
+  std::vector<double> S(nh * nh);
   for (int64_t i = 0; i < nh; ++i)
     for (int64_t j = 0; j <= i; ++j) S[i * nh + j] = S[j * nh + i] = host[get(off + i, off + j)];
+  apply_geneo_keep(c, ordered_drop(S, diag, nh));
+}
+
+// Ordered Cholesky of the GenEO Schur complement S (nh x nh, row-major)
+// keeping the columns whose pivot stays at or above kDepTol times their
+// diagonal in E (Sec. 3.2 needs a full-rank Z)
+static std::vector<int64_t> ordered_drop(const std::vector<double> &S,
+                                         const std::vector<double> &diag, int64_t nh) {
+  std::vector<double> Lm(nh * nh, 0.0);
   std::vector<int64_t> keep;
   for (int64_t kk = 0; kk < nh; ++kk) {
     double piv = S[kk * nh + kk];
@@ -572,6 +594,12 @@ static void geneo_filter(geneo_ctx *c) {
     }
     keep.push_back(kk);
   }
+  return keep;
+}
+
+// Z without the dropped GenEO columns
+static void apply_geneo_keep(geneo_ctx *c, const std::vector<int64_t> &keep) {
+  const int64_t ns = c->n0_snk, nh = c->n0_geneo;
   if ((int64_t)keep.size() == nh) return;
   std::vector<int64_t> ptr(c->zc_ptr.begin(), c->zc_ptr.begin() + ns + 1);
   std::vector<int32_t> row(c->zc_row.begin(), c->zc_row.begin() + c->zc_ptr[ns]);
@@ -707,7 +735,10 @@ void setup_all(geneo_ctx *c) {
       build_mlp_features(c);
     }
     geneo_eigenvectors(c);  // appends GenEO candidates to zc_* and sets n0_geneo
-    if (c->n0_geneo > 0) geneo_filter(c);
+    if (c->n0_geneo > 0) {
+      if (c->opt.coarse_dense) geneo_filter(c);
+      else geneo_filter_mf(c);
+    }
   }
   if (c->n0 > 0 && !c->opt.coarse_dense) {
     build_z_csr(c);

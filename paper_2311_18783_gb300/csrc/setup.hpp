@@ -74,8 +74,16 @@ void build_mlp_features(geneo_ctx *c);
 void split_tc_apply(geneo_ctx *c, const double *xl, double *yl, double *xp, cudaStream_t s, int k,
                     cudaEvent_t e0, cudaEvent_t e1);
 
-// multifrontal coarse factor: set-up, solve y = E^-1 t (column order), sizes
-void mf_setup(geneo_ctx *c);
+// multifrontal coarse factor: set-up, solve y = E^-1 t (column order), sizes.
+// With `schur`, only the fronts below the root are factored and the root's
+// pivot block after the extend-adds, E_hh - E_hg E_gg^-1 E_gh on the GenEO
+// columns h (dense, row-major), is returned with the diagonal of E_hh; the
+// context keeps no factor.
+struct MfSchur {
+  int64_t nh = 0;
+  std::vector<double> S, diag;
+};
+void mf_setup(geneo_ctx *c, MfSchur *schur = nullptr);
 void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k = 1);
 void mf_reserve(geneo_ctx *c, int k);
 int mf_launches_per_solve(const geneo_ctx *c);
