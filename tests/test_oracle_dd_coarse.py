@@ -147,6 +147,40 @@ def test_xi_projector_properties():
         assert np.abs(Ai @ u - y).max() < 1e-8 * np.abs(y).max()
 
 
+def test_split_inverse_identities():
+    """Identities the library's split local solves rest on (Sec. 2, eq.
+    "inverseBw", with xi_i = G S^-1 G^T A_i a projection):
+    * C = (I - xi) A_i^-1 = A_i^-1 - G S^-1 G^T, and C = (I - xi) C (I - xi)^T
+      (the two-sided form applied to bfloat16 factors);
+    * for any rho > 0, A~ = A_i (I + rho xi) = A_i + rho A_i G S^-1 G^T A_i is
+      symmetric and A~^-1 = A_i^-1 - rho/(1+rho) G S^-1 G^T, so that
+      C = A~^-1 - G S^-1 G^T / (1 + rho) (the gradient shift)."""
+    w = small(n=(6, 5, 4), parts=(2, 2, 1), overlap=1)
+    m, A, AT, dec = setup(w)
+    for i in range(dec.nsub):
+        Ai = local_dirichlet(A, dec, i)
+        Gi, _ = local_gradient(m, dec, i)
+        n = len(Ai)
+        S = Gi.T @ Ai @ Gi
+        GSG = Gi @ np.linalg.solve(S, Gi.T)
+        xi = GSG @ Ai
+        Ainv = np.linalg.inv(Ai)
+        P = np.eye(n) - xi
+        C = P @ Ainv
+        sc = np.abs(Ainv).max()
+        assert np.abs(C - (Ainv - GSG)).max() < 1e-9 * sc
+        assert np.abs(C - P @ C @ P.T).max() < 1e-9 * sc
+        assert np.abs(C @ Ai @ Gi).max() < 1e-9 * sc * np.abs(Ai).max()
+        for rho in (0.5, 1e3):
+            At = Ai + rho * Ai @ GSG @ Ai
+            # rounding of the triple product: relative u kappa(S) rho
+            assert np.abs(At - At.T).max() < 1e-8 * np.abs(At).max()
+            assert np.abs(At - Ai @ (np.eye(n) + rho * xi)).max() < 1e-8 * np.abs(At).max()
+            Atinv = np.linalg.inv(At)
+            assert np.abs(Atinv - (Ainv - rho / (1 + rho) * GSG)).max() < 1e-6 * sc
+            assert np.abs(C - (Atinv - GSG / (1 + rho))).max() < 1e-6 * sc
+
+
 def test_gevp_count_by_inertia():
     """#{lambda > tau} of eq. "eigAtildeBAS" equals the number of positive
     eigenvalues of L - tau B (Sylvester), computed by an LDL^T inertia count
