@@ -89,6 +89,10 @@ typedef struct {
   int32_t px, py, pz;        /* boxes per axis; cell (i,j,k) is in box (i*px/nx, j*py/ny, k*pz/nz) */
   int32_t overlap;           /* layers of cells added around each box (vertex neighbours), >= 1 */
   double tau;                /* GenEO threshold, > 0, read with options.tau_convention */
+  const int32_t *cell_part;  /* NULL: the boxes above; else [nx*ny*nz] subdomain id >= 0 of
+                                every active cell (px, py, pz ignored).  Independent problems
+                                placed in one grid, separated by inactive cells and stacked
+                                along z, are solved together by geneo_solve_segments. */
 } geneo_problem;
 
 typedef struct {
@@ -207,6 +211,18 @@ int geneo_apply_preconditioner_block(geneo_ctx *ctx, const double *R_dev, double
  * BREAKDOWN (the worst). */
 int geneo_solve_block(geneo_ctx *ctx, const double *B_dev, double *X_dev, int32_t nrhs,
                       double tol, int32_t maxit, geneo_solve_info *info, void *stream);
+
+/* Independent problems in one context: the connected components of the
+ * active cells (vertex neighbours) are independent systems (A, Z and M^-1_AS,2
+ * are block diagonal over them).  When their unknowns are contiguous (the
+ * problems are stacked along z), this runs one PCG per component in the same
+ * launches: per-component scalars, each component stopping at its own
+ * ||r_c|| <= tol ||b_c||.  b_dev, x_dev device [n]; info (host, may be NULL)
+ * holds one entry per component (geneo_export("seg_off") gives their unknown
+ * ranges).  Returns OK, NOT_CONVERGED or BREAKDOWN (the worst); STATE if the
+ * components are not contiguous. */
+int geneo_solve_segments(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol,
+                         int32_t maxit, geneo_solve_info *info, void *stream);
 
 /* Selects the local factors used by later solves when the context holds
  * several: GENEO_PREC_FP64 (explicit float64 inverses), GENEO_PREC_BF16 (built

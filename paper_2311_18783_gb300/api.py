@@ -29,7 +29,8 @@ class Problem(C.Structure):
                 ("active", C.POINTER(C.c_uint8)), ("mu_inv", C.POINTER(C.c_double)),
                 ("eps", C.POINTER(C.c_double)), ("gamma", C.c_double),
                 ("px", C.c_int32), ("py", C.c_int32), ("pz", C.c_int32),
-                ("overlap", C.c_int32), ("tau", C.c_double)]
+                ("overlap", C.c_int32), ("tau", C.c_double),
+                ("cell_part", C.POINTER(C.c_int32))]
 
 
 class Options(C.Structure):
@@ -85,6 +86,8 @@ _SIGS = {
                               C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                    C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_solve_segments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_apply_preconditioner_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
                                                    C.c_int32, C.c_void_p]),
     "geneo_solve_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
@@ -118,7 +121,7 @@ _EXPORT_DTYPES = {
     "Zcol_ptr": np.int64, "Zcol_row": np.int32, "Zcol_val": np.float64, "k0k1": np.int32,
     "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
     "loc_vlen": np.int64, "mlp_features": np.float32, "eig_V": np.float64, "eig_nq": np.int32,
-    "lobpcg_iters": np.int32, "lobpcg_iters_first": np.int32,
+    "lobpcg_iters": np.int32, "lobpcg_iters_first": np.int32, "seg_off": np.int64,
 }
 
 
@@ -174,17 +177,21 @@ class Solver:
     """One set-up problem on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, h, active, mu_inv, eps, gamma, parts, overlap, tau,
-                 options=None, **opt_kw):
+                 options=None, cell_part=None, **opt_kw):
         lib = load_library()
         self._keep = [np.ascontiguousarray(active, dtype=np.uint8),
                       np.ascontiguousarray(mu_inv, dtype=np.float64),
                       np.ascontiguousarray(eps, dtype=np.float64)]
+        cp = None
+        if cell_part is not None:
+            self._keep.append(np.ascontiguousarray(cell_part, dtype=np.int32))
+            cp = self._keep[-1].ctypes.data_as(C.POINTER(C.c_int32))
         hx, hy, hz = (h, h, h) if np.isscalar(h) else h
         p = Problem(nx, ny, nz, hx, hy, hz,
                     self._keep[0].ctypes.data_as(C.POINTER(C.c_uint8)),
                     self._keep[1].ctypes.data_as(C.POINTER(C.c_double)),
                     self._keep[2].ctypes.data_as(C.POINTER(C.c_double)),
-                    gamma, parts[0], parts[1], parts[2], overlap, tau)
+                    gamma, parts[0], parts[1], parts[2], overlap, tau, cp)
         o = options if options is not None else default_options(**opt_kw)
         ctx = C.c_void_p()
         _check(lib.geneo_setup(C.byref(p), C.byref(o), C.byref(ctx)))
@@ -196,7 +203,7 @@ class Solver:
     @classmethod
     def from_workload(cls, w, **kw):
         return cls(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active, w.mu_inv, w.eps, w.gamma,
-                   w.parts, w.overlap, w.tau, **kw)
+                   w.parts, w.overlap, w.tau, cell_part=getattr(w, "cell_part", None), **kw)
 
     def close(self):
         if getattr(self, "_ctx", None):
@@ -258,6 +265,16 @@ class Solver:
         st = _check(_LIB.geneo_solve_block(self._ctx, _ptr(B), _ptr(X), k, tol, maxit, info,
                                            _stream(stream)))
         return st, [{"iters": i.iters, "relres": i.relres, "seconds": i.seconds} for i in info]
+
+    def solve_segments(self, b, x, tol=1e-8, maxit=1000, stream=None):
+        """One PCG per independent component; returns the status and one info
+        dict per component (unknown ranges: export("seg_off"))."""
+        k = len(self.export("seg_off")) - 1
+        info = (SolveInfo * max(k, 1))()
+        st = _check(_LIB.geneo_solve_segments(self._ctx, _ptr(b), _ptr(x), tol, maxit, info,
+                                              _stream(stream)))
+        return st, [{"iters": i.iters, "relres": i.relres, "seconds": i.seconds}
+                    for i in info[:k]]
 
     def solve_host(self, b, tol=1e-8, maxit=1000, stream=None, out=None):
         """b: host float64 array [n] (pinned tensors are fastest).  Returns x."""

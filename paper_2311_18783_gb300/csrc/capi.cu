@@ -88,7 +88,8 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
   if (!p->active || !p->mu_inv || !p->eps) return fail(GENEO_ERR_INVALID_ARG, "null array");
   if (!(p->gamma > 0)) return fail(GENEO_ERR_INVALID_ARG, "gamma must be > 0");
   if (p->overlap < 1) return fail(GENEO_ERR_INVALID_ARG, "overlap must be >= 1");
-  if (p->px < 1 || p->py < 1 || p->pz < 1 || p->px > p->nx || p->py > p->ny || p->pz > p->nz)
+  if (!p->cell_part &&
+      (p->px < 1 || p->py < 1 || p->pz < 1 || p->px > p->nx || p->py > p->ny || p->pz > p->nz))
     return fail(GENEO_ERR_INVALID_ARG, "box counts must lie in [1, cells per axis]");
   if (!(p->tau > 0)) return fail(GENEO_ERR_INVALID_ARG, "tau must be > 0");
   const int64_t nc = (int64_t)p->nx * p->ny * p->nz;
@@ -96,6 +97,10 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
   for (int64_t c = 0; c < nc; ++c)
     if (p->active[c] && (!(p->mu_inv[c] > 0) || !(p->eps[c] > 0)))
       return fail(GENEO_ERR_INVALID_ARG, "mu^-1 and eps must be > 0 on active cells");
+  if (p->cell_part)
+    for (int64_t c = 0; c < nc; ++c)
+      if (p->active[c] && (p->cell_part[c] < 0 || p->cell_part[c] >= (1 << 24)))
+        return fail(GENEO_ERR_INVALID_ARG, "cell_part must lie in [0, 2^24) on active cells");
   geneo_options o;
   geneo_default_options(&o);
   if (opt) o = *opt;
@@ -132,6 +137,7 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
       c->active.assign(p->active, p->active + nc);
       c->mu_inv.assign(p->mu_inv, p->mu_inv + nc);
       c->eps.assign(p->eps, p->eps + nc);
+      if (p->cell_part) c->cell_part.assign(p->cell_part, p->cell_part + nc);
       c->opt = o;
       GENEO_CUDA(cudaGetDevice(&c->device));
       c->sm_count = geneo::device_sm_count();
@@ -241,6 +247,13 @@ int geneo_solve_block(geneo_ctx *c, const double *b, double *x, int32_t nrhs, do
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded(
       [&]() { return geneo::pcg(c, b, x, tol, maxit, info, as_stream(s), nrhs); });
+}
+
+int geneo_solve_segments(geneo_ctx *c, const double *b, double *x, double tol, int32_t maxit,
+                         geneo_solve_info *info, void *s) {
+  if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
+  return guarded([&]() { return geneo::pcg_segments(c, b, x, tol, maxit, info, as_stream(s)); });
 }
 
 int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int32_t maxit,
@@ -354,6 +367,7 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
     } else if (nm == "loc_nt") put(c->loc.nt.data(), c->loc.nt.size() * 4);
     else if (nm == "loc_toff") put(c->loc.toff.data(), c->loc.toff.size() * 8);
     else if (nm == "loc_voff") put(c->loc.voff.data(), c->loc.voff.size() * 8);
+    else if (nm == "seg_off") put(c->seg_off.data(), c->seg_off.size() * 8);
     else if (nm == "loc_vlen") {
       const int64_t v = c->loc.vlen;
       put(&v, 8);

@@ -32,6 +32,17 @@ struct geneo_ctx {
   int px = 0, py = 0, pz = 0, overlap = 0;
   std::vector<uint8_t> active;
   std::vector<double> mu_inv, eps;
+  std::vector<int32_t> cell_part;  // explicit partition, empty for boxes
+  // independent components (vertex-connected active cells): unknown ranges
+  // [seg_off[s], seg_off[s+1]) when contiguous (seg_ok), per-unknown component
+  std::vector<int64_t> seg_off;
+  bool seg_ok = false;
+  geneo::DevBuf<int32_t> d_seg_of;
+  geneo::DevBuf<int64_t> d_seg_off;
+  geneo::DevBuf<double> seg_sc;     // per-component PCG scalars
+  geneo::DevBuf<int> seg_act;
+  std::vector<double> seg_hs;
+  std::vector<int> seg_ha;
   geneo_options opt{};
   int device = 0;
   int sm_count = 0;

@@ -630,6 +630,19 @@ __global__ void k_pos_tables(const int32_t *__restrict__ l2g, const int32_t *__r
   dmask[p] = (g >= 0 && owner[g] == m) ? 1.0 : 0.0;
 }
 
+// A subdomain whose edges all join boundary vertices (a thin box between a
+// hole and the outer boundary) has no gradient column: its S_j is empty and
+// is stored as one padded 1x1 block, which gets the unit pivot here so that
+// the batched inverse stays defined (no vector entry ever reaches it).
+static void unit_empty_gradient_blocks(const TileBatch &b, const LocalStructure &ls, int nsub,
+                                       double *data, cudaStream_t s) {
+  static const double one = 1.0;
+  for (int m = 0; m < nsub; ++m)
+    if (ls.xv_off[m + 1] == ls.xv_off[m])
+      GENEO_CUDA(cudaMemcpyAsync(data + b.toff[m] * kTileElems, &one, sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+}
+
 // local operators of every subdomain: A_j and A_j^Neu values on the local
 // CSR, the Boolean D_j, the gradient structure of xi_j and the inverses of
 // S_j = G_j^T A_j G_j (Galerkin per tetrahedron, tiled Cholesky inverse)
@@ -701,6 +714,7 @@ void build_xi_operator(geneo_ctx *c, XiOp &L, cudaStream_t s) {
   L.s_inv.alloc(tile_elems(L.sb));
   tiles_init_padding(L.sb, L.s_inv.p, s);
   galerkin_tiles(c, X, L.sb, L.s_inv.p, s);
+  unit_empty_gradient_blocks(L.sb, ls, d.nsub, L.s_inv.p, s);
   DevBuf<double> ws;
   ws.alloc(spd_workspace_elems(L.sb));
   spd_invert(L.sb, L.s_inv.p, ws.p, c->d_err.p, s);
@@ -805,6 +819,7 @@ void build_xi_operator(geneo_ctx *c, XiOp &L, cudaStream_t s) {
   L.sn_inv.alloc(tile_elems(L.sb));
   tiles_init_padding(L.sb, L.sn_inv.p, s);
   galerkin_tiles(c, X, L.sb, L.sn_inv.p, s);
+  unit_empty_gradient_blocks(L.sb, ls, d.nsub, L.sn_inv.p, s);
   spd_invert(L.sb, L.sn_inv.p, ws.p, c->d_err.p, s);
   check_device_error(c, s);
   L.sb.schedule(c->sm_count, s);

@@ -11,6 +11,7 @@
 // E = Z^T A Z).
 #include <algorithm>
 #include <chrono>
+#include <functional>
 
 #include "ctx.hpp"
 #include "setup.hpp"
@@ -623,13 +624,64 @@ static void apply_geneo_keep(geneo_ctx *c, const std::vector<int64_t> &keep) {
   c->n0 = ns + c->n0_geneo;
 }
 
+// Independent components: union-find over active cells sharing a vertex;
+// an unknown belongs to the component of its lowest containing cell.
+static void build_components(geneo_ctx *c) {
+  const Topology &t = c->topo;
+  const int nx = t.nx, ny = t.ny, nz = t.nz;
+  std::vector<int32_t> par(t.ncells, -1);
+  for (int32_t cl : t.cells) par[cl] = cl;
+  std::function<int32_t(int32_t)> find = [&](int32_t a) {
+    while (par[a] != a) {
+      par[a] = par[par[a]];
+      a = par[a];
+    }
+    return a;
+  };
+  for (int32_t cl : t.cells) {
+    const int i = cl % nx, j = (cl / nx) % ny, k = cl / (nx * ny);
+    for (int dk = 0; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          if (dk == 0 && (dj < 0 || (dj == 0 && di <= 0))) continue;  // each pair once
+          const int a = i + di, b = j + dj, d = k + dk;
+          if (a < 0 || b < 0 || a >= nx || b >= ny || d >= nz) continue;
+          const int32_t o = a + nx * (b + ny * d);
+          if (par[o] < 0) continue;
+          const int32_t ra = find(cl), rb = find(o);
+          if (ra != rb) par[std::max(ra, rb)] = std::min(ra, rb);
+        }
+  }
+  const int64_t n = t.ndofs();
+  std::vector<int32_t> comp_id(t.ncells, -1), seg(n);
+  int32_t ncomp = 0;
+  c->seg_ok = true;
+  for (int64_t e = 0; e < n; ++e) {
+    const int32_t r = find(t.first_cell[t.dof_edge[e]]);
+    if (comp_id[r] < 0) comp_id[r] = ncomp++;
+    seg[e] = comp_id[r];
+    if (e > 0 && seg[e] < seg[e - 1]) c->seg_ok = false;
+  }
+  c->seg_off.assign(1, 0);
+  if (c->seg_ok) {
+    for (int64_t e = 1; e <= n; ++e)
+      if (e == n || seg[e] != seg[e - 1]) c->seg_off.push_back(e);
+    if ((int64_t)c->seg_off.size() != ncomp + 1) c->seg_ok = false;
+  }
+  if (!c->seg_ok) c->seg_off.clear();
+  c->d_seg_of.upload(seg, c->stream);
+  if (c->seg_ok) c->d_seg_off.upload(c->seg_off, c->stream);
+}
+
 void setup_all(geneo_ctx *c) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c->stream;
   Topology &t = c->topo;
   build_topology(c->nx, c->ny, c->nz, c->h, c->active.data(), t);
   if (t.ndofs() == 0) throw Error(GENEO_ERR_INVALID_ARG, "the mesh has no interior edge");
-  build_decomposition(t, c->px, c->py, c->pz, c->overlap, c->dec);
+  build_decomposition(t, c->px, c->py, c->pz, c->overlap, c->dec,
+                      c->cell_part.empty() ? nullptr : c->cell_part.data());
+  build_components(c);
   build_local_structure(t, c->dec, c->ls);
   c->d_err.alloc(1);
   c->d_err.zero(s);

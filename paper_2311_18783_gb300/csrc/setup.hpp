@@ -104,5 +104,8 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int 
 void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k = 1);
 int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_solve_info *info,
         cudaStream_t s, int k = 1);
+// one PCG per independent component (contiguous unknown ranges), same launches
+int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit,
+                 geneo_solve_info *info, cudaStream_t s);
 
 }  // namespace geneo

@@ -515,4 +515,157 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Independent components (block-diagonal A, Z and M^-1): one PCG per
+// component in the same launches, scalars per component.
+
+namespace {
+
+// out[s * kScal] = (a, b) over component s's unknowns (one CTA per component)
+__global__ void k_seg_dot(const double *__restrict__ a, const double *__restrict__ b,
+                          const int64_t *__restrict__ off, double *__restrict__ out) {
+  __shared__ double sh[256];
+  const int sg = blockIdx.x;
+  double v = 0;
+  for (int64_t i = off[sg] + threadIdx.x; i < off[sg + 1]; i += blockDim.x) v = fma(a[i], b[i], v);
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(int64_t)sg * kScal] = sh[0];
+}
+
+__global__ void k_seg_update_xr(const double *__restrict__ sc, const int *__restrict__ act,
+                                const int32_t *__restrict__ seg, const double *__restrict__ p,
+                                const double *__restrict__ q, double *__restrict__ x,
+                                double *__restrict__ r, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int g = seg[i];
+  if (!act[g]) return;
+  const double alpha = sc[g * kScal] / sc[g * kScal + 1];
+  x[i] = fma(alpha, p[i], x[i]);
+  r[i] = fma(-alpha, q[i], r[i]);
+}
+
+__global__ void k_seg_update_p(const double *__restrict__ sc, const int *__restrict__ act,
+                               const int32_t *__restrict__ seg, const double *__restrict__ z,
+                               double *__restrict__ p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int g = seg[i];
+  if (!act[g]) return;
+  p[i] = fma(sc[g * kScal + 3] / sc[g * kScal], p[i], z[i]);
+}
+
+__global__ void k_seg_shift(double *sc, int nseg) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < nseg) sc[g * kScal] = sc[g * kScal + 3];
+}
+
+}  // namespace
+
+int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit,
+                 geneo_solve_info *info, cudaStream_t s) {
+  if (!c->seg_ok)
+    throw Error(GENEO_ERR_STATE,
+                "the independent components are not contiguous in the unknown numbering "
+                "(stack the problems along z)");
+  const auto t0 = std::chrono::steady_clock::now();
+  reserve_rhs(c, 1);
+  const int64_t n = c->topo.ndofs();
+  const int nseg = (int)c->seg_off.size() - 1;
+  if (c->seg_sc.n < (int64_t)kScal * nseg) {
+    c->seg_sc.alloc((int64_t)kScal * nseg);
+    c->seg_act.alloc(nseg);
+  }
+  c->seg_sc.zero(s);
+  c->seg_hs.assign((size_t)kScal * nseg, 0.0);
+  c->seg_ha.assign(nseg, 0);
+  double *sc = c->seg_sc.p;
+  const int64_t *off = c->d_seg_off.p;
+  const int32_t *seg = c->d_seg_of.p;
+  const unsigned g = grid_for(n, 256);
+  auto read_back = [&]() {
+    GENEO_CUDA(cudaMemcpyAsync(c->seg_hs.data(), sc, sizeof(double) * kScal * nseg,
+                               cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA(cudaStreamSynchronize(s));
+  };
+  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  c->launches += 5;
+  k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
+  k_seg_dot<<<nseg, 256, 0, s>>>(b, b, off, sc + 4);
+  apply_preconditioner(c, c->p_r.p, c->p_z.p, s, 1);
+  k_copy<<<g, 256, 0, s>>>(c->p_z.p, c->p_p.p, n);
+  k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, off, sc + 0);
+  GENEO_CHECK_LAUNCH();
+  read_back();
+  std::vector<double> bnorm(nseg), rel(nseg, 1.0);
+  std::vector<int> st(nseg, GENEO_NOT_CONVERGED), its(nseg, 0);
+  int nact = 0;
+  for (int j = 0; j < nseg; ++j) {
+    bnorm[j] = std::sqrt(c->seg_hs[(size_t)j * kScal + 4]);
+    c->seg_ha[j] = bnorm[j] > 0.0;
+    if (!c->seg_ha[j]) {
+      st[j] = GENEO_OK;
+      rel[j] = 0.0;
+    }
+    nact += c->seg_ha[j];
+  }
+  GENEO_CUDA(cudaMemcpyAsync(c->seg_act.p, c->seg_ha.data(), sizeof(int) * nseg,
+                             cudaMemcpyHostToDevice, s));
+  for (int it = 1; it <= maxit && nact > 0; ++it) {
+    if (it > 1) {
+      apply_preconditioner(c, c->p_r.p, c->p_z.p, s, 1);
+      c->launches += 3;
+      k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, off, sc + 3);
+      k_seg_update_p<<<g, 256, 0, s>>>(sc, c->seg_act.p, seg, c->p_z.p, c->p_p.p, n);
+      k_seg_shift<<<grid_for(nseg, 256), 256, 0, s>>>(sc, nseg);
+    }
+    spmv(c, c->p_p.p, c->p_q.p, s, 1);
+    c->launches += 3;
+    k_seg_dot<<<nseg, 256, 0, s>>>(c->p_p.p, c->p_q.p, off, sc + 1);
+    k_seg_update_xr<<<g, 256, 0, s>>>(sc, c->seg_act.p, seg, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
+    k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_r.p, off, sc + 2);
+    GENEO_CHECK_LAUNCH();
+    read_back();
+    bool changed = false;
+    for (int j = 0; j < nseg; ++j) {
+      if (!c->seg_ha[j]) continue;
+      its[j] = it;
+      const double *h = c->seg_hs.data() + (size_t)j * kScal;
+      if (!(h[1] > 0.0) || !std::isfinite(h[1]) || !std::isfinite(h[2])) {
+        st[j] = GENEO_ERR_BREAKDOWN;
+      } else {
+        rel[j] = std::sqrt(h[2]) / bnorm[j];
+        if (rel[j] <= tol) st[j] = GENEO_OK;
+      }
+      if (st[j] != GENEO_NOT_CONVERGED) {
+        c->seg_ha[j] = 0;
+        --nact;
+        changed = true;
+      }
+    }
+    if (changed && nact > 0)
+      GENEO_CUDA(cudaMemcpyAsync(c->seg_act.p, c->seg_ha.data(), sizeof(int) * nseg,
+                                 cudaMemcpyHostToDevice, s));
+  }
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  check_device_error(c, s);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int status = GENEO_OK;
+  for (int j = 0; j < nseg; ++j) {
+    if (info) {
+      info[j].iters = its[j];
+      info[j].relres = rel[j];
+      info[j].seconds = secs;
+    }
+    if (st[j] == GENEO_ERR_BREAKDOWN) status = GENEO_ERR_BREAKDOWN;
+    else if (st[j] == GENEO_NOT_CONVERGED && status == GENEO_OK) status = GENEO_NOT_CONVERGED;
+  }
+  return status;
+}
+
 }  // namespace geneo

@@ -260,16 +260,21 @@ void build_topology(int nx, int ny, int nz, const double h[3], const uint8_t *ac
 }
 
 void build_decomposition(const Topology &t, int px, int py, int pz, int overlap,
-                         Decomposition &d) {
+                         Decomposition &d, const int32_t *cell_part) {
   d = Decomposition();
   d.overlap = overlap;
   const int nx = t.nx, ny = t.ny, nz = t.nz;
-  const int64_t nb = (int64_t)px * py * pz;
+  int64_t nb = (int64_t)px * py * pz;
+  if (cell_part) {
+    nb = 0;
+    for (int32_t c : t.cells) nb = std::max<int64_t>(nb, (int64_t)cell_part[c] + 1);
+  }
   std::vector<int32_t> bid(t.ncells, -1);
   std::vector<int32_t> renum(nb, -1);
   for (int32_t c : t.cells) {
     const int64_t i = c % nx, j = (c / nx) % ny, k = c / ((int64_t)nx * ny);
-    const int64_t b = i * px / nx + px * (j * py / ny + (int64_t)py * (k * pz / nz));
+    const int64_t b = cell_part ? (int64_t)cell_part[c]
+                                : i * px / nx + px * (j * py / ny + (int64_t)py * (k * pz / nz));
     bid[c] = (int32_t)b;
     renum[b] = 1;
   }

@@ -90,8 +90,10 @@ struct SNKColumns {
 
 void build_topology(int nx, int ny, int nz, const double h[3], const uint8_t *active,
                     Topology &t);
+// Boxes px x py x pz, or (cell_part non-null) the given subdomain of every
+// active cell; empty parts are dropped and the rest renumbered in order.
 void build_decomposition(const Topology &t, int px, int py, int pz, int overlap,
-                         Decomposition &d);
+                         Decomposition &d, const int32_t *cell_part = nullptr);
 void build_local_structure(const Topology &t, const Decomposition &d, LocalStructure &ls);
 void build_snk(const Topology &t, const Decomposition &d, SNKColumns &snk);
 

@@ -187,3 +187,33 @@ def test_manufactured_solution_rate():
     errs = [_manufactured_error(n) for n in (4, 8, 16)]
     rates = [np.log2(errs[k] / errs[k + 1]) for k in range(2)]
     assert all(r >= 0.9 for r in rates), (errs, rates)
+
+
+def test_compose_is_block_diagonal():
+    """workloads.compose: independent problems stacked along z give an
+    operator that is block diagonal, one block per problem, each equal to
+    that problem's own A (the only change is gamma folded into eps and the
+    z offset of the coordinates, i.e. rounding), in the same unknown order."""
+    from oracle.pipeline import build_problem
+    rng = np.random.default_rng(5)
+    ps = [W.box(4, 4, 3, h=0.25, parts=(2, 1, 1), gamma=1e-2,
+                mu_inv=10.0 ** rng.uniform(0, 2, 48), f='random', seed=1),
+          W.box(3, 2, 2, h=0.25, parts=(1, 1, 1), gamma=1.0, f='random', seed=2),
+          # another cell size: mapped onto h = 1/4 by rescaling mu^-1, eps, f
+          W.box(3, 3, 3, parts=(1, 1, 1), gamma=0.3, eps=10.0 ** rng.uniform(-1, 1, 27),
+                f='random', seed=3)]
+    c = W.compose(ps)
+    assert c.hx == 0.25 and ps[2].hx == 1 / 3
+    assert sorted(set(c.cell_part[c.active == 1].tolist())) == [0, 1, 2, 3]
+    pc = build_problem(c, geneo=False)
+    A = pc.A.tocsr()
+    lo = 0
+    for w in ps:
+        prob = build_problem(w, geneo=False)
+        n = prob.A.shape[0]
+        Ap = prob.A.toarray()
+        assert np.abs(A[lo:lo + n, lo:lo + n].toarray() - Ap).max() <= 1e-14 * np.abs(Ap).max()
+        assert A[lo:lo + n, :lo].nnz == 0 and A[lo:lo + n, lo + n:].nnz == 0
+        assert np.abs(pc.b[0][lo:lo + n] - prob.b[0]).max() <= 1e-14 * np.abs(prob.b[0]).max()
+        lo += n
+    assert lo == A.shape[0]

@@ -47,6 +47,7 @@ class Workload:
     tau: float                  # GenEO threshold (convention chosen by the solver)
     f_slot: np.ndarray          # float64 [nrhs, nverts, 7, 3]
     meta: dict = field(default_factory=dict)
+    cell_part: np.ndarray = None  # int32 [ncells] explicit subdomain per cell, or None (boxes)
 
     @property
     def ncells(self):
@@ -245,3 +246,54 @@ def many_problems(count=256, seed=3):
                 holes=holes, name=f"batch{p}_n{n}")
         out.append(w)
     return out
+
+
+def compose(problems, name="composite"):
+    """Independent problems in one grid: problem p is placed at z offset
+    zoff[p] (one inactive cell layer between consecutive problems) and at
+    x = y = 0, cells outside it inactive.  gamma_p is folded into eps
+    (the composite has gamma = 1), each problem keeps its own boxes through
+    an explicit cell partition, and its edge-slot source field is copied to
+    its vertices.  Cubic cells of another size h_p are mapped onto the
+    composite's size H (the smallest) exactly: with lowest-order edge
+    elements the curl-curl term of a tetrahedron scales as 1/h, the mass
+    term as h and the load as h^2, so with r = h_p / H the same matrix and
+    right-hand side come from mu^-1 / r, gamma eps r and f r^2.  All problems
+    must share the overlap and tau.  meta["zoff"] records the offsets."""
+    for w in problems:
+        assert w.hx == w.hy == w.hz and w.overlap == problems[0].overlap
+        assert w.tau == problems[0].tau and w.nrhs == problems[0].nrhs
+    h = min(w.hx for w in problems)
+    nx = max(w.nx for w in problems)
+    ny = max(w.ny for w in problems)
+    zoff, z = [], 0
+    for w in problems:
+        zoff.append(z)
+        z += w.nz + 1
+    nz = z - 1
+    nc = nx * ny * nz
+    active = np.zeros(nc, dtype=np.uint8)
+    mu = np.ones(nc)
+    eps = np.ones(nc)
+    part = np.zeros(nc, dtype=np.int32)
+    nv = (nx + 1) * (ny + 1) * (nz + 1)
+    f = np.zeros((problems[0].nrhs, nv, 7, 3))
+    pbase = 0
+    for w, zo in zip(problems, zoff):
+        ci, cj, ck = _cell_ijk(w.nx, w.ny, w.nz)
+        g = ci + nx * (cj + ny * (ck + zo))
+        r = w.hx / h
+        active[g] = w.active
+        mu[g] = np.asarray(w.mu_inv, dtype=np.float64) / r
+        eps[g] = np.asarray(w.eps, dtype=np.float64) * w.gamma * r
+        px, py, pz = w.parts
+        part[g] = pbase + (ci * px // w.nx) + px * ((cj * py // w.ny) + py * (ck * pz // w.nz))
+        pbase += px * py * pz
+        v = np.arange(w.nverts)
+        vi = v % (w.nx + 1)
+        vj = (v // (w.nx + 1)) % (w.ny + 1)
+        vk = v // ((w.nx + 1) * (w.ny + 1))
+        f[:, vi + (nx + 1) * (vj + (ny + 1) * (vk + zo))] = w.f_slot * (r * r)
+    return Workload(name, nx, ny, nz, h, h, h, active, mu, eps, 1.0, (1, 1, 1),
+                    problems[0].overlap, problems[0].tau, f, meta={"zoff": zoff},
+                    cell_part=part)
