@@ -118,6 +118,15 @@ typedef struct {
   const struct geneo_mlp *warm_start;  /* non-NULL: the first LOBPCG block of every subdomain
                                 is this network's output on the edge features (needs
                                 lobpcg_block == 8); NULL: seeded random block */
+  int32_t lobpcg_neumann;    /* 1: LOBPCG for small boxes with high contrast and tiny gamma:
+                                the search directions use the explicit inverse of
+                                A_j^Neu + 1e-10 diag(A_j^Neu) (the right-hand operator of the
+                                GEVP) instead of A_j^-1, the Rayleigh-Ritz step works in the
+                                B-Gram basis of [X W P], and a Ritz value that has stayed
+                                within 1e-4 relative for five iterations, at least 1% away
+                                from tau, counts as converged (float64 residuals of such
+                                pencils stall far above lobpcg_tol).  Use with
+                                lobpcg_block = 16.  0: off */
 } geneo_options;
 
 typedef struct {

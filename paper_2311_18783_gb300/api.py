@@ -39,7 +39,8 @@ class Options(C.Structure):
                 ("lobpcg_maxit", C.c_int32), ("lobpcg_tol", C.c_double), ("seed", C.c_uint64),
                 ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32),
                 ("use_graph", C.c_int32), ("gradient_shift", C.c_int32),
-                ("keep_eigvecs", C.c_int32), ("warm_start", C.c_void_p)]
+                ("keep_eigvecs", C.c_int32), ("warm_start", C.c_void_p),
+                ("lobpcg_neumann", C.c_int32)]
 
 
 class Sizes(C.Structure):

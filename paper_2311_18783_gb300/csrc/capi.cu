@@ -115,6 +115,8 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
     return fail(GENEO_ERR_INVALID_ARG, "a warm start needs lobpcg_block = 8");
   if (o.keep_eigvecs != 0 && o.keep_eigvecs != 1)
     return fail(GENEO_ERR_INVALID_ARG, "keep_eigvecs must be 0 or 1");
+  if (o.lobpcg_neumann != 0 && o.lobpcg_neumann != 1)
+    return fail(GENEO_ERR_INVALID_ARG, "lobpcg_neumann must be 0 or 1");
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
       (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");

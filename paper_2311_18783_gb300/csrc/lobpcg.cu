@@ -444,7 +444,136 @@ __global__ void k_resid(const double *__restrict__ LX, const double *__restrict_
   }
 }
 
+// A_j^Neu values (on the local CSR of N_j) into the tile-packed layout of the
+// local factors, lower tiles only, with the diagonal scaled by 1 + delta
+__global__ void k_neumann_tiles(const int64_t *__restrict__ Noff, const int64_t *__restrict__ lrowptr,
+                                const int32_t *__restrict__ lcol, const double *__restrict__ nval,
+                                const int64_t *__restrict__ toff, double delta,
+                                double *__restrict__ tiles) {
+  const int m = blockIdx.y;
+  const int64_t ni = Noff[m + 1] - Noff[m];
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ni;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = Noff[m] + r;
+    const int I = (int)(r / kTile), rr = (int)(r % kTile);
+    for (int64_t q = lrowptr[slot]; q < lrowptr[slot + 1]; ++q) {
+      const int c = lcol[q];
+      const int J = c / kTile;
+      if (J > I) continue;
+      const double v = (c == r) ? nval[q] * (1.0 + delta) : nval[q];
+      tiles[(toff[m] + (int64_t)I * (I + 1) / 2 + J) * kTileElems + rr * kTile + (c % kTile)] = v;
+    }
+  }
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Small dense symmetric eigenproblems on the host (cyclic Jacobi): a is n x n
+// row-major and is destroyed; w gets the eigenvalues, v (n x n, row-major)
+// the eigenvectors as columns.
+static void host_sym_eig(int n, std::vector<double> &a, std::vector<double> &w,
+                         std::vector<double> &v) {
+  v.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) v[(size_t)i * n + i] = 1.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double h = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
+      a[(size_t)i * n + j] = a[(size_t)j * n + i] = h;
+    }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double x = a[(size_t)i * n + j] * a[(size_t)i * n + j];
+        tot += x;
+        if (i != j) off += x;
+      }
+    if (!(off > 1e-32 * tot)) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+        const double z = (aqq - app) / (2.0 * apq);
+        const double t = (z >= 0 ? 1.0 : -1.0) / (std::fabs(z) + std::sqrt(1.0 + z * z));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        for (int r = 0; r < n; ++r) {
+          const double arp = a[(size_t)r * n + p], arq = a[(size_t)r * n + q];
+          a[(size_t)r * n + p] = cs * arp - sn * arq;
+          a[(size_t)r * n + q] = sn * arp + cs * arq;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double apr = a[(size_t)p * n + r], aqr = a[(size_t)q * n + r];
+          a[(size_t)p * n + r] = cs * apr - sn * aqr;
+          a[(size_t)q * n + r] = sn * apr + cs * aqr;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double vrp = v[(size_t)r * n + p], vrq = v[(size_t)r * n + q];
+          v[(size_t)r * n + p] = cs * vrp - sn * vrq;
+          v[(size_t)r * n + q] = sn * vrp + cs * vrq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = a[(size_t)i * n + i];
+}
+
+// Rayleigh-Ritz of one subdomain in a basis S that is not B-orthonormal:
+// H = S^T L S and M = S^T B S (ns x ns, leading dimension ld).  M = U E U^T,
+// directions with E <= 1e-12 max(E) are dropped, F = U_keep E_keep^-1/2, and
+// the standard problem F^T H F y = theta y gives the Ritz vectors S F y.
+// Writes the kout largest theta and their coefficient columns C = F y
+// (C[i * ld + c]); missing columns (rank below kout) get theta = -1, C = 0.
+static void general_rr(int ns, int ld, int kout, const double *H, const double *M,
+                       double *theta, double *C) {
+  std::vector<double> a((size_t)ns * ns), e, U;
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < ns; ++j) a[(size_t)i * ns + j] = M[(size_t)i * ld + j];
+  host_sym_eig(ns, a, e, U);
+  double emax = 0;
+  for (double x : e) emax = std::max(emax, x);
+  std::vector<int> keep;
+  for (int i = 0; i < ns; ++i)
+    if (e[i] > 1e-12 * emax) keep.push_back(i);
+  const int r = (int)keep.size();
+  std::vector<double> F((size_t)ns * std::max(r, 1), 0.0);
+  for (int i = 0; i < ns; ++i)
+    for (int c = 0; c < r; ++c)
+      F[(size_t)i * r + c] = U[(size_t)i * ns + keep[c]] / std::sqrt(e[keep[c]]);
+  // Hr = F^T H F
+  std::vector<double> HF((size_t)ns * std::max(r, 1), 0.0), Hr((size_t)r * r, 0.0);
+  for (int i = 0; i < ns; ++i)
+    for (int c = 0; c < r; ++c) {
+      double acc = 0;
+      for (int j = 0; j < ns; ++j) acc += H[(size_t)i * ld + j] * F[(size_t)j * r + c];
+      HF[(size_t)i * r + c] = acc;
+    }
+  for (int a2 = 0; a2 < r; ++a2)
+    for (int c = 0; c < r; ++c) {
+      double acc = 0;
+      for (int i = 0; i < ns; ++i) acc += F[(size_t)i * r + a2] * HF[(size_t)i * r + c];
+      Hr[(size_t)a2 * r + c] = acc;
+    }
+  std::vector<double> th, Y;
+  if (r > 0) host_sym_eig(r, Hr, th, Y);
+  std::vector<int> order(r);
+  for (int i = 0; i < r; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return th[x] > th[y]; });
+  for (int i = 0; i < ld * ld; ++i) C[i] = 0.0;
+  for (int c = 0; c < kout; ++c) {
+    if (c >= r) {
+      theta[c] = -1.0;
+      continue;
+    }
+    theta[c] = th[order[c]];
+    for (int i = 0; i < ns; ++i) {
+      double acc = 0;
+      for (int a2 = 0; a2 < r; ++a2) acc += F[(size_t)i * r + a2] * Y[(size_t)a2 * r + order[c]];
+      C[(size_t)i * ld + c] = acc;
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -852,6 +981,22 @@ void geneo_eigenvectors(geneo_ctx *c) {
   L.theta.alloc((int64_t)L.nsub * k);
   L.nq.assign(L.nsub, 0);
   grow_q(L, 16);
+  // search-direction operator: A_j^-1, or (A_j^Neu + 1e-10 diag)^-1 for lobpcg_neumann
+  const bool neu = c->opt.lobpcg_neumann != 0;
+  DevBuf<double> neu_inv;
+  if (neu) {
+    neu_inv.alloc(tile_elems(c->loc));
+    tiles_init_padding(c->loc, neu_inv.p, s);
+    k_neumann_tiles<<<dim3(64, L.nsub), 256, 0, s>>>(L.op.Noff.p, L.op.lrp.p, L.op.lcol.p,
+                                                      L.op.nval.p, c->loc.d_toff.p, 1e-10,
+                                                      neu_inv.p);
+    GENEO_CHECK_LAUNCH();
+    DevBuf<double> ws;
+    ws.alloc(spd_workspace_elems(c->loc));
+    spd_invert(c->loc, neu_inv.p, ws.p, c->d_err.p, s);
+    check_device_error(c, s);
+  }
+  const double *Tdir = neu ? neu_inv.p : c->loc_f64.p;
   const double tau = c->tau_p, tol = c->opt.lobpcg_tol;
   std::vector<uint8_t> done(L.nsub, 0);
   std::vector<std::vector<double>> lam_locked(L.nsub);
@@ -890,6 +1035,10 @@ void geneo_eigenvectors(geneo_ctx *c) {
     // and the iterations since it last dropped by 10%
     std::vector<double> best(L.nsub, 1e300);
     std::vector<int> stall(L.nsub, 0);
+    // lobpcg_neumann: the last kHist Ritz values of every subdomain (ring)
+    constexpr int kHist = 6;
+    std::vector<double> thist(neu ? (size_t)L.nsub * kHist * k : 0);
+    std::vector<int> nhist(L.nsub, 0);
     for (int m = 0; m < L.nsub; ++m) finished[m] = done[m];
     for (int it = 0; it < c->opt.lobpcg_maxit; ++it) {
       k_resid<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.LX.p, L.BX.p, L.theta.p, k, L.op.pos_sub.p,
@@ -938,12 +1087,28 @@ void geneo_eigenvectors(geneo_ctx *c) {
           ++stall[m];
         }
         const double tol_m = stall[m] >= 10 ? std::max(tol, 1e-4) : tol;
+        if (neu) {
+          double *h = thist.data() + ((size_t)m * kHist + nhist[m] % kHist) * k;
+          for (int j = 0; j < k; ++j) h[j] = th[m * k + j];
+          ++nhist[m];
+        }
+        // a Ritz value that has stayed within 1e-4 relative over the last
+        // kHist iterations, clear of tau (lobpcg_neumann only)
+        auto stagnant = [&](int j) {
+          if (!neu || nhist[m] < kHist) return false;
+          const double t = th[m * k + j];
+          if (!(std::fabs(t - tau) > 1e-2 * tau)) return false;
+          double dev = 0;
+          for (int q = 0; q < kHist; ++q)
+            dev = std::max(dev, std::fabs(thist[((size_t)m * kHist + q) * k + j] - t));
+          return dev <= 1e-4 * std::max(std::fabs(t), tau);
+        };
         int lead = 0;
         for (int j = 0; j < k; ++j) {
           const double rn = std::sqrt(std::max(gr[(size_t)m * ld * ld + j * ld + j], 0.0));
           const double bn = std::sqrt(std::max(gb[(size_t)m * ld * ld + j * ld + j], 0.0));
           const double sc = std::max(std::fabs(th[m * k + j]), tau) * bn;
-          if (rn <= tol_m * sc || bn == 0.0) ++lead;
+          if (rn <= tol_m * sc || bn == 0.0 || stagnant(j)) ++lead;
           else break;
         }
         bool fin = false, stop = false;
@@ -989,7 +1154,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
       if (all) break;
       // W = T R (explicit local inverse), B-orthogonal to Q and X, B-orthonormal
       for (int col = 0; col < k; ++col) {
-        symv_batch<double>(c->loc, c->loc_f64.p, L.R.p + (int64_t)col * L.vlen,
+        symv_batch<double>(c->loc, Tdir, L.R.p + (int64_t)col * L.vlen,
                            L.W.p + (int64_t)col * L.vlen, c->d_err.p, s);
       }
       project_gradients_B(L, L.W.p, k);
@@ -1041,9 +1206,34 @@ void geneo_eigenvectors(geneo_ctx *c) {
                   H[(size_t)m * ld * ld + (a * k + i) * ld + (b * k + j)] =
                       g[(size_t)m * ld * ld + i * ld + j];
           }
-        L.coef.upload(H, s);
-        k_rr_jacobi<<<grid_for(L.nsub, 32), 32, 0, s>>>(L.coef.p, ns, ld, k, L.theta.p, L.tmat.p,
-                                                        L.nsub);
+        if (neu) {
+          // B-Gram of the basis and the Rayleigh-Ritz step in its
+          // B-orthonormalised span (the blocks are B-orthonormalised one
+          // against the other by single passes, which the B^-1-like
+          // directions of this mode leave far from B-orthonormal)
+          std::vector<double> Mg((size_t)L.nsub * ld * ld, 0.0);
+          const DevBuf<double> *BSb[3] = {&L.BX, &L.BW, &L.BP};
+          for (int a = 0; a < ns / k; ++a)
+            for (int b = 0; b < ns / k; ++b) {
+              gram(L, Sb[a]->p, k, BSb[b]->p, k, L.gram.p);
+              std::vector<double> g = L.gram.download(s);
+              for (int m = 0; m < L.nsub; ++m)
+                for (int i = 0; i < k; ++i)
+                  for (int j = 0; j < k; ++j)
+                    Mg[(size_t)m * ld * ld + (a * k + i) * ld + (b * k + j)] =
+                        g[(size_t)m * ld * ld + i * ld + j];
+            }
+          std::vector<double> thh((size_t)L.nsub * k), Cm((size_t)L.nsub * ld * ld);
+          for (int m = 0; m < L.nsub; ++m)
+            general_rr(ns, ld, k, H.data() + (size_t)m * ld * ld, Mg.data() + (size_t)m * ld * ld,
+                       thh.data() + (size_t)m * k, Cm.data() + (size_t)m * ld * ld);
+          L.theta.upload(thh, s);
+          L.tmat.upload(Cm, s);
+        } else {
+          L.coef.upload(H, s);
+          k_rr_jacobi<<<grid_for(L.nsub, 32), 32, 0, s>>>(L.coef.p, ns, ld, k, L.theta.p,
+                                                          L.tmat.p, L.nsub);
+        }
       }
       // new X, P and their images
       {
