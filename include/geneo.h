@@ -233,6 +233,40 @@ int geneo_solve_block(geneo_ctx *ctx, const double *B_dev, double *X_dev, int32_
 int geneo_solve_segments(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol,
                          int32_t maxit, geneo_solve_info *info, void *stream);
 
+/* Composition of independent problems into one grid, host only (no device
+ * work; callable without a GPU).  Problem p is placed at x = y = 0 and at
+ * z offset zoff[p], one inactive cell layer above problem p-1; the composite
+ * grid is max nx x max ny x (sum (nz_p + 1) - 1) cubic cells of side
+ * H = min h_p.  Each problem keeps its subdomains through the composite's
+ * cell partition (its boxes, or its own cell_part, offset past the parts of
+ * the problems before it).  Its gamma is folded into eps (the composite has
+ * gamma = 1) and a cell side h_p != H is mapped exactly: lowest-order edge
+ * elements give a curl-curl term that scales as 1/h, a mass term as h and a
+ * load as h^2 (Sec. 2, eq. "bilinearformposmax"), so mu^-1 / r,
+ * gamma eps r and f r^2 with r = h_p / H give the problem's own A and b.
+ * A (and Z, M^-1_AS,2) of the composite are block diagonal over the problems.
+ * Every problem needs cubic cells and the same overlap and tau.
+ *
+ * geneo_compose_size: dims = {nx, ny, nz} of the composite, *h = H.
+ * geneo_compose: fills host arrays of nx*ny*nz entries (active, mu_inv, eps,
+ *   cell_part; cells outside every problem are inactive with mu^-1 = eps = 1)
+ *   and, if zoff is not NULL, zoff[nprob].
+ * geneo_compose_field: f_slot[p] host [nrhs][nverts_p][7][3] (the edge-slot
+ *   load of geneo_assemble_rhs; NULL = zero) into f_out host
+ *   [nrhs][nverts][7][3] of the composite (overwritten), scaled by r^2.
+ * geneo_setup_batch: geneo_setup of the composite (gamma = 1, overlap and
+ *   tau of the problems, the composed cell partition); solve it with
+ *   geneo_solve_segments, one PCG per problem, in problem order.
+ * Errors: INVALID_ARG (no problem, non-cubic cells, mixed overlap or tau,
+ * null arrays, composite above 2^28 cells), and those of geneo_setup. */
+int geneo_compose_size(int32_t nprob, const geneo_problem *probs, int32_t *dims, double *h);
+int geneo_compose(int32_t nprob, const geneo_problem *probs, uint8_t *active, double *mu_inv,
+                  double *eps, int32_t *cell_part, int32_t *zoff);
+int geneo_compose_field(int32_t nprob, const geneo_problem *probs, const double *const *f_slot,
+                        int32_t nrhs, double *f_out);
+int geneo_setup_batch(int32_t nprob, const geneo_problem *probs, const geneo_options *opt,
+                      geneo_ctx **out);
+
 /* Selects the local factors used by later solves when the context holds
  * several: GENEO_PREC_FP64 (explicit float64 inverses), GENEO_PREC_BF16 (built
  * when options.precision was BF16, together with the float32 split) or GENEO_PREC_FP32 (the

@@ -6,8 +6,8 @@ The computation lives in the C-ABI shared library ``libgeneo.so`` (see
 loads the library and raises if it has not been built: there is no CPU
 fallback.
 """
-from .api import (GeneoError, Mlp, Options, Solver, load_library, PREC_FP64, PREC_FP32,
-                  PREC_BF16, COARSE_NONE, COARSE_SNK, TAU_RECIPROCAL, TAU_PAPER)
+from .api import (GeneoError, Mlp, Options, Solver, compose, load_library, PREC_FP64,
+                  PREC_FP32, PREC_BF16, COARSE_NONE, COARSE_SNK, TAU_RECIPROCAL, TAU_PAPER)
 
-__all__ = ["GeneoError", "Mlp", "Options", "Solver", "load_library", "PREC_FP64", "PREC_FP32", "PREC_BF16",
-           "COARSE_NONE", "COARSE_SNK", "TAU_RECIPROCAL", "TAU_PAPER"]
+__all__ = ["GeneoError", "Mlp", "Options", "Solver", "compose", "load_library", "PREC_FP64",
+           "PREC_FP32", "PREC_BF16", "COARSE_NONE", "COARSE_SNK", "TAU_RECIPROCAL", "TAU_PAPER"]

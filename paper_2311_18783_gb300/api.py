@@ -89,6 +89,14 @@ _SIGS = {
                                    C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_segments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                        C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_compose_size": (C.c_int, [C.c_int32, C.POINTER(Problem), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]),
+    "geneo_compose": (C.c_int, [C.c_int32, C.POINTER(Problem), C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p]),
+    "geneo_compose_field": (C.c_int, [C.c_int32, C.POINTER(Problem), C.POINTER(C.c_void_p),
+                                      C.c_int32, C.c_void_p]),
+    "geneo_setup_batch": (C.c_int, [C.c_int32, C.POINTER(Problem), C.POINTER(Options),
+                                    C.POINTER(C.c_void_p)]),
     "geneo_apply_preconditioner_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
                                                    C.c_int32, C.c_void_p]),
     "geneo_solve_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
@@ -174,6 +182,58 @@ def default_options(**kw):
     return o
 
 
+def _problem_array(workloads, keep):
+    """ctypes array of Problem structs for workload-like objects (nx, ny, nz,
+    hx, hy, hz, active, mu_inv, eps, gamma, parts, overlap, tau and an
+    optional cell_part); the NumPy arrays they point to are appended to keep."""
+    arr = (Problem * len(workloads))()
+    for q, w in enumerate(workloads):
+        nc = w.nx * w.ny * w.nz
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(w.active, dtype=np.uint8), (nc,)))
+        mu = np.ascontiguousarray(np.broadcast_to(np.asarray(w.mu_inv, dtype=np.float64), (nc,)))
+        ep = np.ascontiguousarray(np.broadcast_to(np.asarray(w.eps, dtype=np.float64), (nc,)))
+        keep += [a, mu, ep]
+        cp = None
+        if getattr(w, "cell_part", None) is not None:
+            keep.append(np.ascontiguousarray(w.cell_part, dtype=np.int32))
+            cp = keep[-1].ctypes.data_as(C.POINTER(C.c_int32))
+        arr[q] = Problem(w.nx, w.ny, w.nz, w.hx, w.hy, w.hz,
+                         a.ctypes.data_as(C.POINTER(C.c_uint8)),
+                         mu.ctypes.data_as(C.POINTER(C.c_double)),
+                         ep.ctypes.data_as(C.POINTER(C.c_double)),
+                         w.gamma, w.parts[0], w.parts[1], w.parts[2], w.overlap, w.tau, cp)
+    return arr
+
+
+def compose(workloads):
+    """Independent problems composed into one grid by the library (host
+    only, no GPU needed); see geneo_compose in include/geneo.h.  Returns a
+    dict with nx, ny, nz, h, active, mu_inv, eps, cell_part, zoff and, when
+    every workload has f_slot [nrhs, nverts, 7, 3], the composed f_slot."""
+    lib = load_library()
+    keep = []
+    probs = _problem_array(workloads, keep)
+    np_ = len(workloads)
+    dims = (C.c_int32 * 3)()
+    h = C.c_double()
+    _check(lib.geneo_compose_size(np_, probs, dims, C.byref(h)))
+    nx, ny, nz = dims
+    nc = nx * ny * nz
+    out = {"nx": nx, "ny": ny, "nz": nz, "h": h.value,
+           "active": np.empty(nc, np.uint8), "mu_inv": np.empty(nc), "eps": np.empty(nc),
+           "cell_part": np.empty(nc, np.int32), "zoff": np.empty(np_, np.int32)}
+    _check(lib.geneo_compose(np_, probs, *(out[k].ctypes.data_as(C.c_void_p) for k in
+                                           ("active", "mu_inv", "eps", "cell_part", "zoff"))))
+    if all(getattr(w, "f_slot", None) is not None for w in workloads):
+        fs = [np.ascontiguousarray(w.f_slot, dtype=np.float64) for w in workloads]
+        nrhs = fs[0].shape[0]
+        ptrs = (C.c_void_p * np_)(*(f.ctypes.data for f in fs))
+        f = np.empty((nrhs, (nx + 1) * (ny + 1) * (nz + 1), 7, 3))
+        _check(lib.geneo_compose_field(np_, probs, ptrs, nrhs, f.ctypes.data_as(C.c_void_p)))
+        out["f_slot"] = f
+    return out
+
+
 class Solver:
     """One set-up problem on the current CUDA device."""
 
@@ -205,6 +265,24 @@ class Solver:
     def from_workload(cls, w, **kw):
         return cls(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active, w.mu_inv, w.eps, w.gamma,
                    w.parts, w.overlap, w.tau, cell_part=getattr(w, "cell_part", None), **kw)
+
+    @classmethod
+    def batch(cls, workloads, options=None, **opt_kw):
+        """Independent problems in one context (geneo_setup_batch); solve with
+        solve_segments, one PCG per problem in the given order.  The composed
+        load of every problem's f_slot comes from compose(workloads)."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self._keep = []
+        probs = _problem_array(workloads, self._keep)
+        o = options if options is not None else default_options(**opt_kw)
+        ctx = C.c_void_p()
+        _check(lib.geneo_setup_batch(len(workloads), probs, C.byref(o), C.byref(ctx)))
+        self._ctx = ctx
+        self.options = o
+        self.sizes = self.query()
+        self.n = self.sizes["n"]
+        return self
 
     def close(self):
         if getattr(self, "_ctx", None):

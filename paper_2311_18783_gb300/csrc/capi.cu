@@ -3,6 +3,7 @@
 #include <cstring>
 #include <string>
 
+#include "compose.hpp"
 #include "setup.hpp"
 
 namespace {
@@ -256,6 +257,70 @@ int geneo_solve_segments(geneo_ctx *c, const double *b, double *x, double tol, i
   if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded([&]() { return geneo::pcg_segments(c, b, x, tol, maxit, info, as_stream(s)); });
+}
+
+int geneo_compose_size(int32_t nprob, const geneo_problem *probs, int32_t *dims, double *h) {
+  if (!dims || !h) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() {
+    geneo::Composite c;
+    geneo::compose_problems(nprob, probs, false, c);
+    dims[0] = c.nx;
+    dims[1] = c.ny;
+    dims[2] = c.nz;
+    *h = c.h;
+    return GENEO_OK;
+  });
+}
+
+int geneo_compose(int32_t nprob, const geneo_problem *probs, uint8_t *active, double *mu_inv,
+                  double *eps, int32_t *cell_part, int32_t *zoff) {
+  if (!active || !mu_inv || !eps || !cell_part) return fail(GENEO_ERR_INVALID_ARG, "null array");
+  return guarded([&]() {
+    geneo::Composite c;
+    geneo::compose_problems(nprob, probs, true, c);
+    std::memcpy(active, c.active.data(), c.active.size());
+    std::memcpy(mu_inv, c.mu_inv.data(), sizeof(double) * c.mu_inv.size());
+    std::memcpy(eps, c.eps.data(), sizeof(double) * c.eps.size());
+    std::memcpy(cell_part, c.part.data(), sizeof(int32_t) * c.part.size());
+    if (zoff) std::memcpy(zoff, c.zoff.data(), sizeof(int32_t) * c.zoff.size());
+    return GENEO_OK;
+  });
+}
+
+int geneo_compose_field(int32_t nprob, const geneo_problem *probs, const double *const *f_slot,
+                        int32_t nrhs, double *f_out) {
+  return guarded([&]() {
+    geneo::Composite c;
+    geneo::compose_problems(nprob, probs, false, c);
+    geneo::compose_field(nprob, probs, c, f_slot, nrhs, f_out);
+    return GENEO_OK;
+  });
+}
+
+int geneo_setup_batch(int32_t nprob, const geneo_problem *probs, const geneo_options *opt,
+                      geneo_ctx **out) {
+  if (!out) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  geneo::Composite c;
+  const int rc = guarded([&]() {
+    geneo::compose_problems(nprob, probs, true, c);
+    return GENEO_OK;
+  });
+  if (rc != GENEO_OK) return rc;
+  geneo_problem q{};
+  q.nx = c.nx;
+  q.ny = c.ny;
+  q.nz = c.nz;
+  q.hx = q.hy = q.hz = c.h;
+  q.active = c.active.data();
+  q.mu_inv = c.mu_inv.data();
+  q.eps = c.eps.data();
+  q.gamma = 1.0;
+  q.px = q.py = q.pz = 1;
+  q.overlap = probs[0].overlap;
+  q.tau = probs[0].tau;
+  q.cell_part = c.part.data();
+  return geneo_setup(&q, opt, out);
 }
 
 int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int32_t maxit,

@@ -253,8 +253,9 @@ def compose(problems, name="composite"):
     zoff[p] (one inactive cell layer between consecutive problems) and at
     x = y = 0, cells outside it inactive.  gamma_p is folded into eps
     (the composite has gamma = 1), each problem keeps its own boxes through
-    an explicit cell partition, and its edge-slot source field is copied to
-    its vertices.  Cubic cells of another size h_p are mapped onto the
+    an explicit cell partition (its boxes, or its own cell_part offset past
+    the previous problems' parts), and its edge-slot source field is copied
+    to its vertices.  Cubic cells of another size h_p are mapped onto the
     composite's size H (the smallest) exactly: with lowest-order edge
     elements the curl-curl term of a tetrahedron scales as 1/h, the mass
     term as h and the load as h^2, so with r = h_p / H the same matrix and
@@ -286,9 +287,14 @@ def compose(problems, name="composite"):
         active[g] = w.active
         mu[g] = np.asarray(w.mu_inv, dtype=np.float64) / r
         eps[g] = np.asarray(w.eps, dtype=np.float64) * w.gamma * r
-        px, py, pz = w.parts
-        part[g] = pbase + (ci * px // w.nx) + px * ((cj * py // w.ny) + py * (ck * pz // w.nz))
-        pbase += px * py * pz
+        if w.cell_part is not None:
+            own = np.where(w.active == 1, np.asarray(w.cell_part, dtype=np.int64), 0)
+            part[g] = pbase + own
+            pbase += int(own[w.active == 1].max()) + 1
+        else:
+            px, py, pz = w.parts
+            part[g] = pbase + (ci * px // w.nx) + px * ((cj * py // w.ny) + py * (ck * pz // w.nz))
+            pbase += px * py * pz
         v = np.arange(w.nverts)
         vi = v % (w.nx + 1)
         vj = (v // (w.nx + 1)) % (w.ny + 1)
