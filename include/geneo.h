@@ -256,7 +256,8 @@ int geneo_solve_segments(geneo_ctx *ctx, const double *b_dev, double *x_dev, dou
  *   [nrhs][nverts][7][3] of the composite (overwritten), scaled by r^2.
  * geneo_setup_batch: geneo_setup of the composite (gamma = 1, overlap and
  *   tau of the problems, the composed cell partition); solve it with
- *   geneo_solve_segments, one PCG per problem, in problem order.
+ *   geneo_solve_segments, one PCG per problem, in problem order (a problem
+ *   without interior edges has no unknown and no component).
  * Errors: INVALID_ARG (no problem, non-cubic cells, mixed overlap or tau,
  * null arrays, composite above 2^28 cells), and those of geneo_setup. */
 int geneo_compose_size(int32_t nprob, const geneo_problem *probs, int32_t *dims, double *h);
