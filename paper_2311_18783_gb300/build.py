@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgeneo.so")
-SOURCES = ["topology.cpp", "compose.cpp", "dense.cu", "setup.cu", "solve.cu", "lobpcg.cu", "capi.cu",
+SOURCES = ["topology.cpp", "compose.cpp", "small_eig.cpp", "dense.cu", "setup.cu", "solve.cu", "lobpcg.cu", "capi.cu",
            "noalloc.cu", "coarse_mf.cu", "tc_symm.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
