@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgeneo.so")
-SOURCES = ["topology.cpp", "compose.cpp", "small_eig.cpp", "dense.cu", "setup.cu", "solve.cu", "lobpcg.cu", "capi.cu",
+SOURCES = ["topology.cpp", "compose.cpp", "small_eig.cpp", "ordered_drop.cpp", "dense.cu", "setup.cu", "solve.cu", "lobpcg.cu", "capi.cu",
            "noalloc.cu", "coarse_mf.cu", "tc_symm.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -43,7 +43,7 @@ def build(verbose=False, extra=()):
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -14,6 +14,7 @@
 #include <functional>
 
 #include "ctx.hpp"
+#include "ordered_drop.hpp"
 #include "setup.hpp"
 #include "xi.hpp"
 
@@ -525,8 +526,6 @@ static Columns coarse_columns(const geneo_ctx *c, int64_t gap_after_snk) {
 // complement E_hh - E_hg E_gg^-1 E_gh is below kDepTol times their diagonal.
 constexpr double kDepTol = 1e-8;
 
-static std::vector<int64_t> ordered_drop(const std::vector<double> &S,
-                                         const std::vector<double> &diag, int64_t nh);
 static void apply_geneo_keep(geneo_ctx *c, const std::vector<int64_t> &keep);
 
 // The same filter through the multifrontal: the root front holds the GenEO
@@ -535,7 +534,7 @@ static void apply_geneo_keep(geneo_ctx *c, const std::vector<int64_t> &keep);
 static void geneo_filter_mf(geneo_ctx *c) {
   MfSchur sc;
   mf_setup(c, &sc);
-  apply_geneo_keep(c, ordered_drop(sc.S, sc.diag, sc.nh));
+  apply_geneo_keep(c, ordered_drop(sc.S, sc.diag, sc.nh, kDepTol));
 }
 
 static void geneo_filter(geneo_ctx *c) {
@@ -572,30 +571,7 @@ static void geneo_filter(geneo_ctx *c) {
   std::vector<double> S(nh * nh);
   for (int64_t i = 0; i < nh; ++i)
     for (int64_t j = 0; j <= i; ++j) S[i * nh + j] = S[j * nh + i] = host[get(off + i, off + j)];
-  apply_geneo_keep(c, ordered_drop(S, diag, nh));
-}
-
-// Ordered Cholesky of the GenEO Schur complement S (nh x nh, row-major)
-// keeping the columns whose pivot stays at or above kDepTol times their
-// diagonal in E (Sec. 3.2 needs a full-rank Z)
-static std::vector<int64_t> ordered_drop(const std::vector<double> &S,
-                                         const std::vector<double> &diag, int64_t nh) {
-  std::vector<double> Lm(nh * nh, 0.0);
-  std::vector<int64_t> keep;
-  for (int64_t kk = 0; kk < nh; ++kk) {
-    double piv = S[kk * nh + kk];
-    for (int64_t q : keep) piv -= Lm[kk * nh + q] * Lm[kk * nh + q];
-    if (!(piv >= kDepTol * diag[kk])) continue;
-    const double d = std::sqrt(piv);
-    Lm[kk * nh + kk] = d;
-    for (int64_t r = kk + 1; r < nh; ++r) {
-      double v = S[r * nh + kk];
-      for (int64_t q : keep) v -= Lm[r * nh + q] * Lm[kk * nh + q];
-      Lm[r * nh + kk] = v / d;
-    }
-    keep.push_back(kk);
-  }
-  return keep;
+  apply_geneo_keep(c, ordered_drop(S, diag, nh, kDepTol));
 }
 
 // Z without the dropped GenEO columns
