@@ -205,6 +205,27 @@ def _problem_array(workloads, keep):
     return arr
 
 
+def shard_problems(workloads, rank, world):
+    """Indices of the independent problems rank `rank` of `world` sets up:
+    largest-first assignment by active cell count to the least loaded rank
+    (ties to the lower rank), so every problem goes to exactly one rank and
+    the loads differ by at most one problem.  Independent problems need no
+    exchange between ranks."""
+    if not 0 <= rank < world:
+        raise ValueError("rank must lie in [0, world)")
+    size = [int(np.count_nonzero(np.broadcast_to(w.active, (w.nx * w.ny * w.nz,))))
+            for w in workloads]
+    order = sorted(range(len(workloads)), key=lambda i: (-size[i], i))
+    load = [0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += size[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
 def compose(workloads):
     """Independent problems composed into one grid by the library (host
     only, no GPU needed); see geneo_compose in include/geneo.h.  Returns a
