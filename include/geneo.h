@@ -167,6 +167,16 @@ void geneo_default_options(geneo_options *opt);
  * overlap < 1, empty mesh), OOM, CUDA, NOT_SPD. */
 int geneo_setup(const geneo_problem *prob, const geneo_options *opt, geneo_ctx **out);
 
+/* The host part of geneo_setup only, without any CUDA call (callable without
+ * a GPU): mesh, Dirichlet elimination and unknown numbering (Sec. 4 mesh,
+ * Sec. 1 eq. "positivemaxwell"), CSR pattern, subdomains with overlap and
+ * partition of unity (Sec. 2, eq. "PoU"), k0/k1, independent components and
+ * the split near-kernel columns (Sec. 2, definition "near-kernelCS") when
+ * opt->coarse is SNK.  The context answers geneo_query and the integer
+ * names of geneo_export; every call that needs device data returns STATE.
+ * Same arguments and errors as geneo_setup. */
+int geneo_setup_topology(const geneo_problem *prob, const geneo_options *opt, geneo_ctx **out);
+
 /* Releases every resource of the context (NULL is allowed). */
 void geneo_destroy(geneo_ctx *ctx);
 

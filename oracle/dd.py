@@ -56,17 +56,26 @@ def dilate(mask3, active3):
     return out & active3
 
 
-def decompose(mesh, parts, overlap, pou="boolean"):
+def decompose(mesh, parts, overlap, pou="boolean", cell_part=None):
+    """Boxes (parts = (px, py, pz)), or any cell partition (cell_part: a
+    non-negative id per active cell, as from a graph partitioner; Sec. 4
+    uses METIS partitions for its strong scaling study).  Parts that hold
+    no active cell are skipped; the others are numbered in increasing id."""
     nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
     px, py, pz = parts
     ncells = nx * ny * nz
     c = np.arange(ncells)
     ci, cj, ck = c % nx, (c // nx) % ny, c // (nx * ny)
-    bid = (ci * px // nx) + px * ((cj * py // ny) + py * (ck * pz // nz))
     active = np.zeros(ncells, dtype=bool)
     active[mesh.cells] = True
+    if cell_part is None:
+        bid = (ci * px // nx) + px * ((cj * py // ny) + py * (ck * pz // nz))
+        nb = px * py * pz
+    else:
+        bid = np.where(active, np.asarray(cell_part, dtype=np.int64), 0)
+        nb = int(bid[active].max()) + 1
     present = np.unique(bid[active])
-    renum = np.full(px * py * pz, -1)
+    renum = np.full(nb, -1)
     renum[present] = np.arange(len(present))
     box_of_cell = np.where(active, renum[bid], -1)
     nsub = len(present)

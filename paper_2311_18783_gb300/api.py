@@ -76,6 +76,8 @@ _LIB = None
 _SIGS = {
     "geneo_default_options": (None, [C.POINTER(Options)]),
     "geneo_setup": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+    "geneo_setup_topology": (C.c_int, [C.POINTER(Problem), C.POINTER(Options),
+                                       C.POINTER(C.c_void_p)]),
     "geneo_destroy": (None, [C.c_void_p]),
     "geneo_query": (C.c_int, [C.c_void_p, C.POINTER(Sizes)]),
     "geneo_assemble_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -286,6 +288,23 @@ class Solver:
     def from_workload(cls, w, **kw):
         return cls(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active, w.mu_inv, w.eps, w.gamma,
                    w.parts, w.overlap, w.tau, cell_part=getattr(w, "cell_part", None), **kw)
+
+    @classmethod
+    def topology(cls, w, options=None, **opt_kw):
+        """Host-only context of a workload (geneo_setup_topology, no GPU
+        needed): query() and the integer names of export() only."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self._keep = []
+        probs = _problem_array([w], self._keep)
+        o = options if options is not None else default_options(**opt_kw)
+        ctx = C.c_void_p()
+        _check(lib.geneo_setup_topology(probs, C.byref(o), C.byref(ctx)))
+        self._ctx = ctx
+        self.options = o
+        self.sizes = self.query()
+        self.n = self.sizes["n"]
+        return self
 
     @classmethod
     def batch(cls, workloads, options=None, **opt_kw):

@@ -81,7 +81,9 @@ void geneo_default_options(geneo_options *o) {
   o->use_graph = 1;
 }
 
-int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **out) {
+// Argument checks shared by geneo_setup and geneo_setup_topology; fills o.
+static int check_setup_args(const geneo_problem *p, const geneo_options *opt, geneo_ctx **out,
+                            geneo_options &o) {
   if (!p || !out) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->hx > 0) || !(p->hy > 0) || !(p->hz > 0))
@@ -102,7 +104,6 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
     for (int64_t c = 0; c < nc; ++c)
       if (p->active[c] && (p->cell_part[c] < 0 || p->cell_part[c] >= (1 << 24)))
         return fail(GENEO_ERR_INVALID_ARG, "cell_part must lie in [0, 2^24) on active cells");
-  geneo_options o;
   geneo_default_options(&o);
   if (opt) o = *opt;
   if (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32 &&
@@ -121,27 +122,41 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
       (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
+  return GENEO_OK;
+}
+
+// A context holding the problem copy (no device work yet).
+static geneo_ctx *new_context(const geneo_problem *p, const geneo_options &o) {
+  const int64_t nc = (int64_t)p->nx * p->ny * p->nz;
+  auto c = new geneo_ctx();
+  c->nx = p->nx;
+  c->ny = p->ny;
+  c->nz = p->nz;
+  c->h[0] = p->hx;
+  c->h[1] = p->hy;
+  c->h[2] = p->hz;
+  c->gamma = p->gamma;
+  c->tau = p->tau;
+  c->tau_p = o.tau_convention == GENEO_TAU_PAPER ? p->tau : 1.0 / p->tau;
+  c->px = p->px;
+  c->py = p->py;
+  c->pz = p->pz;
+  c->overlap = p->overlap;
+  c->active.assign(p->active, p->active + nc);
+  c->mu_inv.assign(p->mu_inv, p->mu_inv + nc);
+  c->eps.assign(p->eps, p->eps + nc);
+  if (p->cell_part) c->cell_part.assign(p->cell_part, p->cell_part + nc);
+  c->opt = o;
+  return c;
+}
+
+int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **out) {
+  geneo_options o;
+  const int rc = check_setup_args(p, opt, out, o);
+  if (rc != GENEO_OK) return rc;
   return guarded([&]() {
-    auto c = new geneo_ctx();
+    geneo_ctx *c = new_context(p, o);
     try {
-      c->nx = p->nx;
-      c->ny = p->ny;
-      c->nz = p->nz;
-      c->h[0] = p->hx;
-      c->h[1] = p->hy;
-      c->h[2] = p->hz;
-      c->gamma = p->gamma;
-      c->tau = p->tau;
-      c->tau_p = o.tau_convention == GENEO_TAU_PAPER ? p->tau : 1.0 / p->tau;
-      c->px = p->px;
-      c->py = p->py;
-      c->pz = p->pz;
-      c->overlap = p->overlap;
-      c->active.assign(p->active, p->active + nc);
-      c->mu_inv.assign(p->mu_inv, p->mu_inv + nc);
-      c->eps.assign(p->eps, p->eps + nc);
-      if (p->cell_part) c->cell_part.assign(p->cell_part, p->cell_part + nc);
-      c->opt = o;
       GENEO_CUDA(cudaGetDevice(&c->device));
       c->sm_count = geneo::device_sm_count();
       GENEO_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -156,9 +171,27 @@ int geneo_setup(const geneo_problem *p, const geneo_options *opt, geneo_ctx **ou
   });
 }
 
+int geneo_setup_topology(const geneo_problem *p, const geneo_options *opt, geneo_ctx **out) {
+  geneo_options o;
+  const int rc = check_setup_args(p, opt, out, o);
+  if (rc != GENEO_OK) return rc;
+  return guarded([&]() {
+    geneo_ctx *c = new_context(p, o);
+    c->host_only = true;
+    try {
+      geneo::setup_topology(c);
+    } catch (...) {
+      delete c;
+      throw;
+    }
+    *out = c;
+    return GENEO_OK;
+  });
+}
+
 void geneo_destroy(geneo_ctx *c) {
   if (!c) return;
-  cudaDeviceSynchronize();
+  if (!c->host_only) cudaDeviceSynchronize();
   delete c;
 }
 
@@ -186,6 +219,7 @@ int geneo_query(const geneo_ctx *c, geneo_sizes *o) {
 }
 
 int geneo_assemble_rhs(geneo_ctx *c, const double *f, double *b, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !f || !b) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     geneo::assemble_rhs(c, f, b, as_stream(s));
@@ -194,6 +228,7 @@ int geneo_assemble_rhs(geneo_ctx *c, const double *f, double *b, void *s) {
 }
 
 int geneo_spmv(geneo_ctx *c, const double *x, double *y, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !x || !y) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     geneo::spmv(c, x, y, as_stream(s));
@@ -202,6 +237,7 @@ int geneo_spmv(geneo_ctx *c, const double *x, double *y, void *s) {
 }
 
 int geneo_local_solve(geneo_ctx *c, const double *r, double *w, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !r || !w) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     geneo::local_solve(c, r, w, as_stream(s));
@@ -210,6 +246,7 @@ int geneo_local_solve(geneo_ctx *c, const double *r, double *w, void *s) {
 }
 
 int geneo_coarse_solve(geneo_ctx *c, const double *r, double *y, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !r || !y) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     geneo::coarse_solve(c, r, y, as_stream(s));
@@ -218,6 +255,7 @@ int geneo_coarse_solve(geneo_ctx *c, const double *r, double *y, void *s) {
 }
 
 int geneo_apply_preconditioner(geneo_ctx *c, const double *r, double *z, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !r || !z) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     geneo::apply_preconditioner(c, r, z, as_stream(s));
@@ -227,6 +265,7 @@ int geneo_apply_preconditioner(geneo_ctx *c, const double *r, double *z, void *s
 
 int geneo_solve(geneo_ctx *c, const double *b, double *x, double tol, int32_t maxit,
                 geneo_solve_info *info, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded([&]() { return geneo::pcg(c, b, x, tol, maxit, info, as_stream(s)); });
@@ -234,6 +273,7 @@ int geneo_solve(geneo_ctx *c, const double *b, double *x, double tol, int32_t ma
 
 int geneo_apply_preconditioner_block(geneo_ctx *c, const double *r, double *z, int32_t nrhs,
                                      void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !r || !z) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(GENEO_ERR_INVALID_ARG, "nrhs must be in 1..16");
   return guarded([&]() {
@@ -245,6 +285,7 @@ int geneo_apply_preconditioner_block(geneo_ctx *c, const double *r, double *z, i
 
 int geneo_solve_block(geneo_ctx *c, const double *b, double *x, int32_t nrhs, double tol,
                       int32_t maxit, geneo_solve_info *info, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1 || nrhs > kMaxRhs) return fail(GENEO_ERR_INVALID_ARG, "nrhs must be in 1..16");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
@@ -254,6 +295,7 @@ int geneo_solve_block(geneo_ctx *c, const double *b, double *x, int32_t nrhs, do
 
 int geneo_solve_segments(geneo_ctx *c, const double *b, double *x, double tol, int32_t maxit,
                          geneo_solve_info *info, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded([&]() { return geneo::pcg_segments(c, b, x, tol, maxit, info, as_stream(s)); });
@@ -325,6 +367,7 @@ int geneo_setup_batch(int32_t nprob, const geneo_problem *probs, const geneo_opt
 
 int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int32_t maxit,
                      geneo_solve_info *info, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !bh || !xh) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded([&]() {
@@ -340,6 +383,7 @@ int geneo_solve_host(geneo_ctx *c, const double *bh, double *xh, double tol, int
 }
 
 int geneo_use_precision(geneo_ctx *c, int32_t precision) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (precision == GENEO_PREC_FP64 && c->loc_f64.p) {
     c->local_prec = GENEO_PREC_FP64;
@@ -357,12 +401,14 @@ int geneo_use_precision(geneo_ctx *c, int32_t precision) {
 }
 
 int geneo_profile_enable(geneo_ctx *c, int32_t on) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   c->prof = on != 0;
   return GENEO_OK;
 }
 
 int geneo_profile_read(geneo_ctx *c, geneo_profile *o) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c || !o) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     std::memset(o, 0, sizeof(*o));
@@ -407,6 +453,8 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
       buf.assign((const unsigned char *)p, (const unsigned char *)p + bytes);
     };
     const std::string nm(name);
+    if (c->host_only && (nm == "A_val" || nm == "loc_f32" || nm == "mlp_features" || nm == "eig_V"))
+      return fail(GENEO_ERR_STATE, "topology-only context: no device data");
     const geneo::Topology &t = c->topo;
     if (nm == "edges") put(t.edges.data(), t.edges.size() * 4);
     else if (nm == "dir_edge") put(t.dir_edge.data(), t.dir_edge.size());
@@ -503,6 +551,7 @@ int geneo_mlp_set_params(geneo_mlp *mlp, const float *host) {
 }
 
 int geneo_mlp_loss_grad(geneo_mlp *mlp, geneo_ctx *c, double *loss, float *grad_host, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!mlp || !c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     const double l = geneo::mlp_loss_grad(mlp->m, c, as_stream(s));
@@ -517,6 +566,7 @@ int geneo_mlp_loss_grad(geneo_mlp *mlp, geneo_ctx *c, double *loss, float *grad_
 
 int geneo_mlp_train(geneo_mlp *mlp, geneo_ctx *c, int32_t steps, double lr, double *loss_host,
                     void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!mlp || !c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (steps < 0 || !(lr > 0)) return fail(GENEO_ERR_INVALID_ARG, "steps >= 0, lr > 0");
   return guarded([&]() {
@@ -531,6 +581,7 @@ int geneo_mlp_train(geneo_mlp *mlp, geneo_ctx *c, int32_t steps, double lr, doub
 }
 
 int geneo_mlp_infer(const geneo_mlp *mlp, geneo_ctx *c, double *X, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!mlp || !c || !X) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   return guarded([&]() {
     geneo::mlp_infer(mlp->m, c, X, as_stream(s));

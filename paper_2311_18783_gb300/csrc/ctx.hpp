@@ -33,9 +33,11 @@ struct geneo_ctx {
   std::vector<uint8_t> active;
   std::vector<double> mu_inv, eps;
   std::vector<int32_t> cell_part;  // explicit partition, empty for boxes
+  bool host_only = false;          // geneo_setup_topology: integer data only, no device
   // independent components (vertex-connected active cells): unknown ranges
   // [seg_off[s], seg_off[s+1]) when contiguous (seg_ok), per-unknown component
   std::vector<int64_t> seg_off;
+  std::vector<int32_t> seg_of;  // component of every unknown
   bool seg_ok = false;
   geneo::DevBuf<int32_t> d_seg_of;
   geneo::DevBuf<int64_t> d_seg_off;

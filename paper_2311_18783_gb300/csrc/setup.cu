@@ -645,13 +645,10 @@ static void build_components(geneo_ctx *c) {
     if ((int64_t)c->seg_off.size() != ncomp + 1) c->seg_ok = false;
   }
   if (!c->seg_ok) c->seg_off.clear();
-  c->d_seg_of.upload(seg, c->stream);
-  if (c->seg_ok) c->d_seg_off.upload(c->seg_off, c->stream);
+  c->seg_of = std::move(seg);
 }
 
-void setup_all(geneo_ctx *c) {
-  const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t s = c->stream;
+void setup_topology(geneo_ctx *c) {
   Topology &t = c->topo;
   build_topology(c->nx, c->ny, c->nz, c->h, c->active.data(), t);
   if (t.ndofs() == 0) throw Error(GENEO_ERR_INVALID_ARG, "the mesh has no interior edge");
@@ -659,6 +656,19 @@ void setup_all(geneo_ctx *c) {
                       c->cell_part.empty() ? nullptr : c->cell_part.data());
   build_components(c);
   build_local_structure(t, c->dec, c->ls);
+  if (c->host_only && c->opt.coarse == GENEO_COARSE_SNK) {
+    build_snk(t, c->dec, c->snk);
+    c->n0 = c->n0_snk = (int64_t)c->snk.sub.size();
+  }
+}
+
+void setup_all(geneo_ctx *c) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c->stream;
+  Topology &t = c->topo;
+  setup_topology(c);
+  c->d_seg_of.upload(c->seg_of, s);
+  if (c->seg_ok) c->d_seg_off.upload(c->seg_off, s);
   c->d_err.alloc(1);
   c->d_err.zero(s);
 

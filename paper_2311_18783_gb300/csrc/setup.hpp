@@ -42,6 +42,9 @@ void coltet_build(geneo_ctx *c, const Columns &X, std::vector<int64_t> &ct_ptr,
 void tet_operators(geneo_ctx *c, DevBuf<double> &tcurl, DevBuf<double> &tmass, cudaStream_t s);
 
 void setup_all(geneo_ctx *c);
+// Host part only: topology, decomposition, components, local structure and,
+// for a host-only context, the split near-kernel columns.  No CUDA call.
+void setup_topology(geneo_ctx *c);
 void assemble_rhs(geneo_ctx *c, const double *fslot_host, double *b, cudaStream_t s);
 void check_device_error(geneo_ctx *c, cudaStream_t s);
 // GenEO eigenvectors of every subdomain (batched LOBPCG); appends columns

@@ -1,0 +1,121 @@
+"""Integer set-up data of the library against the oracle, bit for bit, on
+the CPU: geneo_setup_topology runs the host part of the set-up without any
+CUDA call.  Mesh edges, Dirichlet flags, unknown numbering, CSR pattern,
+subdomain index sets N_i, partition-of-unity owners, split near-kernel
+columns and k0/k1 must be identical to the oracle's (oracle/mesh.py,
+oracle/dd.py, oracle/coarse.py) on the parity cases, the 32^3 benchmark
+workload, an explicit cell partition and composed independent problems;
+compute calls on such a context are refused with STATE."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2311_18783_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    import paper_2311_18783_gb300 as p
+    p.load_library()
+    return p
+
+
+def _hetero(seed=0, parts=(3, 2, 1), overlap=1, n=(10, 8, 6), holes=(((4, 6), (3, 5), (0, 6)),)):
+    rng = np.random.default_rng(seed)
+    nc = n[0] * n[1] * n[2]
+    return W.box(*n, parts=parts, overlap=overlap, gamma=1e-3,
+                 mu_inv=10.0 ** rng.uniform(0, 2, nc), eps=10.0 ** rng.uniform(-0.5, 0.5, nc),
+                 holes=holes, f='random', seed=seed, tau=0.1)
+
+
+def _composite():
+    rng = np.random.default_rng(5)
+    a = W.box(6, 6, 6, h=1 / 6, parts=(2, 1, 1), gamma=1e-2, mu_inv=10.0 ** rng.uniform(0, 2, 216),
+              f='random', seed=1, holes=(((2, 4), (2, 4), (1, 5)),))
+    b = W.box(5, 4, 4, h=1 / 6, parts=(1, 2, 1), f='random', seed=2)
+    return W.compose([a, b])
+
+
+def _metis_like():
+    w = _hetero(seed=3, parts=(1, 1, 1), holes=())
+    rng = np.random.default_rng(4)
+    # an irregular partition: random seeds grown by distance (Voronoi cells)
+    c = np.arange(w.nx * w.ny * w.nz)
+    xyz = np.stack([c % w.nx, (c // w.nx) % w.ny, c // (w.nx * w.ny)], 1)
+    seeds = xyz[rng.choice(len(c), 7, replace=False)]
+    w.cell_part = np.argmin(((xyz[:, None, :] - seeds[None]) ** 2).sum(-1), 1).astype(np.int32)
+    return w
+
+
+CASES = {
+    "cube8": W.unit_cube_8,
+    "hetero_hole": lambda: _hetero(),
+    "overlap2": lambda: _hetero(seed=1, parts=(2, 2, 1), overlap=2, n=(9, 9, 5), holes=()),
+    "one_sub": lambda: _hetero(seed=2, parts=(1, 1, 1), n=(5, 4, 4), holes=()),
+    "ragged_beam": lambda: W.box(13, 3, 3, h=1 / 3, parts=(4, 1, 1), overlap=1, gamma=0.5),
+    "cube32_hole_channels": W.cube32_hole_channels,
+    "voronoi_partition": _metis_like,
+    "composite": _composite,
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_integer_setup_matches_oracle(pkg, name):
+    from oracle.mesh import build_mesh
+    from oracle.fem import assemble_A
+    from oracle.dd import decompose, k0, k1
+    from oracle.coarse import snk_columns
+    w = CASES[name]()
+    s = pkg.Solver.topology(w)
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    dec = decompose(m, w.parts, w.overlap, cell_part=getattr(w, "cell_part", None))
+    assert np.array_equal(s.export("edges").reshape(-1, 2), m.edges)
+    assert np.array_equal(s.export("dir_edge").astype(bool), m.dir_edge)
+    assert np.array_equal(s.export("dof_edge"), m.dof_edge)
+    assert np.array_equal(s.export("dof_vert"), m.dof_vert)
+    A = assemble_A(m, w)
+    assert np.array_equal(s.export("A_rowptr"), A.indptr)
+    assert np.array_equal(s.export("A_col"), A.indices)
+    noff, nidx = s.export("N_off"), s.export("N_idx")
+    assert len(noff) == dec.nsub + 1 == s.sizes["nsub"] + 1
+    for i in range(dec.nsub):
+        assert np.array_equal(nidx[noff[i]:noff[i + 1]], dec.N[i])
+    assert np.array_equal(s.export("owner"), dec.owner)
+    snk = snk_columns(m, dec)
+    assert np.array_equal(s.export("snk_sub"), np.array([c[0] for c in snk], np.int32))
+    assert np.array_equal(s.export("snk_vert"), np.array([c[1] for c in snk], np.int32))
+    assert s.sizes["n0_snk"] == len(snk)
+    assert list(s.export("k0k1")) == [k0(A, dec), k1(dec)]
+    s.close()
+
+
+def test_composite_components(pkg):
+    """Composed problems: one contiguous unknown range per problem, in
+    problem order, each the size of the problem alone."""
+    from oracle.mesh import build_mesh
+    rng = np.random.default_rng(5)
+    ps = [W.box(6, 6, 6, h=1 / 6, parts=(2, 1, 1), gamma=1e-2,
+                mu_inv=10.0 ** rng.uniform(0, 2, 216)),
+          W.box(5, 4, 4, h=1 / 6, parts=(1, 2, 1)),
+          W.box(4, 4, 3, h=1 / 6, parts=(2, 1, 1))]
+    s = pkg.Solver.topology(W.compose(ps))
+    off = s.export("seg_off")
+    sizes = [build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active).ndofs for w in ps]
+    assert list(np.diff(off)) == sizes
+    s.close()
+
+
+def test_compute_calls_refused(pkg):
+    s = pkg.Solver.topology(W.unit_cube_8())
+    for name in ("A_val", "loc_f32"):
+        with pytest.raises(pkg.GeneoError) as e:
+            s.export(name)
+        assert e.value.status == -7
+    lib = pkg.load_library()
+    assert lib.geneo_use_precision(s._ctx, pkg.PREC_FP64) == -7
+    assert lib.geneo_solve(s._ctx, None, None, 1e-8, 10, None, None) == -7
+    s.close()

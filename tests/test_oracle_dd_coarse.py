@@ -312,3 +312,26 @@ def test_galerkin_through_curl_operator():
     G = gradient_dofs(m)
     CG = C @ G
     assert abs(CG.T @ CG).max() <= 1e-24 * abs(K).max()
+
+
+def test_cell_partition_equal_to_boxes():
+    """decompose with an explicit cell partition that repeats the boxes
+    (ids shifted, one id unused) gives the same subdomains, owners and
+    weights as the boxes themselves."""
+    import numpy as np
+    import workloads as W
+    from oracle.mesh import build_mesh
+    from oracle.dd import decompose
+    w = W.box(7, 5, 4, parts=(3, 2, 2), overlap=1, holes=(((2, 4), (1, 3), (0, 4)),))
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    ref = decompose(m, w.parts, w.overlap)
+    c = np.arange(w.nx * w.ny * w.nz)
+    ci, cj, ck = c % w.nx, (c // w.nx) % w.ny, c // (w.nx * w.ny)
+    box = (ci * 3 // w.nx) + 3 * ((cj * 2 // w.ny) + 2 * (ck * 2 // w.nz))
+    got = decompose(m, (1, 1, 1), w.overlap, cell_part=2 * box + 5)
+    assert got.nsub == ref.nsub
+    assert np.array_equal(got.box_of_cell, ref.box_of_cell)
+    assert np.array_equal(got.owner, ref.owner)
+    for i in range(ref.nsub):
+        assert np.array_equal(got.N[i], ref.N[i])
+        assert np.array_equal(got.D[i], ref.D[i])
