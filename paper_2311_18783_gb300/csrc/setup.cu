@@ -659,6 +659,9 @@ void setup_topology(geneo_ctx *c) {
   if (c->host_only && c->opt.coarse == GENEO_COARSE_SNK) {
     build_snk(t, c->dec, c->snk);
     c->n0 = c->n0_snk = (int64_t)c->snk.sub.size();
+    c->zc_ptr = c->snk.ptr;
+    c->zc_row = c->snk.row;
+    c->zc_val.assign(c->snk.sgn.begin(), c->snk.sgn.end());
   }
 }
 

@@ -89,6 +89,11 @@ def test_integer_setup_matches_oracle(pkg, name):
     assert np.array_equal(s.export("snk_sub"), np.array([c[0] for c in snk], np.int32))
     assert np.array_equal(s.export("snk_vert"), np.array([c[1] for c in snk], np.int32))
     assert s.sizes["n0_snk"] == len(snk)
+    zp, zr, zv = s.export("Zcol_ptr"), s.export("Zcol_row"), s.export("Zcol_val")
+    assert len(zp) == len(snk) + 1
+    for k, (_, _, rows, vals) in enumerate(snk):
+        assert np.array_equal(zr[zp[k]:zp[k + 1]], rows)
+        assert np.array_equal(zv[zp[k]:zp[k + 1]], vals)
     assert list(s.export("k0k1")) == [k0(A, dec), k1(dec)]
     s.close()
 
