@@ -319,7 +319,15 @@ int geneo_profile_read(geneo_ctx *ctx, geneo_profile *out);
  *  "geneo_found" int32 [nsub]       eigenvalues above the threshold found per subdomain
  *  "Zcol_ptr" int64 [n0+1], "Zcol_row" int32 [nnzZ], "Zcol_val" float64 [nnzZ]
  *  "k0k1"        int32 [2]
- * Returns INVALID_ARG for an unknown name or a too small buffer. */
+ *  "xv_off"      int64 [nsub+1], "xv_vert" int32  kept vertices of G_j per subdomain
+ *  "seg_off"     int64 [ncomp+1]    unknown ranges of the independent components
+ *  "loc_nt" int32 [nsub], "loc_toff" int64 [nsub+1], "loc_voff" int64 [nsub+1],
+ *  "loc_vlen" int64 [1], "loc_f32" float32  tile layout and float32 local factors
+ *  "lobpcg_iters", "lobpcg_iters_first" int32 [nsub]  LOBPCG iterations (all, first block)
+ *  "mlp_features" float32 [loc_vlen][5], "eig_V" float64 [8][loc_vlen],
+ *  "eig_nq" int32 [nsub]            warm-start features and training targets
+ * Returns INVALID_ARG for an unknown name or a too small buffer, STATE for a
+ * device-backed name on a topology-only context. */
 int geneo_export(const geneo_ctx *ctx, const char *name, void *dst, int64_t capacity,
                  int64_t *size);
 

@@ -133,6 +133,7 @@ _EXPORT_DTYPES = {
     "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
     "loc_vlen": np.int64, "mlp_features": np.float32, "eig_V": np.float64, "eig_nq": np.int32,
     "lobpcg_iters": np.int32, "lobpcg_iters_first": np.int32, "seg_off": np.int64,
+    "xv_off": np.int64, "xv_vert": np.int32,
 }
 
 

@@ -483,6 +483,8 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
     else if (nm == "loc_toff") put(c->loc.toff.data(), c->loc.toff.size() * 8);
     else if (nm == "loc_voff") put(c->loc.voff.data(), c->loc.voff.size() * 8);
     else if (nm == "seg_off") put(c->seg_off.data(), c->seg_off.size() * 8);
+    else if (nm == "xv_off") put(c->ls.xv_off.data(), c->ls.xv_off.size() * 8);
+    else if (nm == "xv_vert") put(c->ls.xv_vert.data(), c->ls.xv_vert.size() * 4);
     else if (nm == "loc_vlen") {
       const int64_t v = c->loc.vlen;
       put(&v, 8);

@@ -5,7 +5,8 @@ subdomain index sets N_i, partition-of-unity owners, split near-kernel
 columns and k0/k1 must be identical to the oracle's (oracle/mesh.py,
 oracle/dd.py, oracle/coarse.py) on the parity cases, the 32^3 benchmark
 workload, an explicit cell partition and composed independent problems;
-compute calls on such a context are refused with STATE."""
+the kept vertices of every local gradient G_j as well; compute calls on
+such a context are refused with STATE."""
 import os
 
 import numpy as np
@@ -60,6 +61,9 @@ CASES = {
     "cube32_hole_channels": W.cube32_hole_channels,
     "voronoi_partition": _metis_like,
     "composite": _composite,
+    # a batching cube with a box whose edges all join boundary vertices
+    # (no kept vertex, an empty G_j)
+    "batch35_n9": lambda: [w for w in W.many_problems(256, seed=3) if w.nx <= 10][4],
 }
 
 
@@ -95,6 +99,10 @@ def test_integer_setup_matches_oracle(pkg, name):
         assert np.array_equal(zr[zp[k]:zp[k + 1]], rows)
         assert np.array_equal(zv[zp[k]:zp[k + 1]], vals)
     assert list(s.export("k0k1")) == [k0(A, dec), k1(dec)]
+    from oracle.coarse import local_gradient
+    xo, xv = s.export("xv_off"), s.export("xv_vert")
+    for j in range(dec.nsub):
+        assert np.array_equal(xv[xo[j]:xo[j + 1]], local_gradient(m, dec, j)[1])
     s.close()
 
 
