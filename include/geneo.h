@@ -93,6 +93,12 @@ typedef struct {
                                 every active cell (px, py, pz ignored).  Independent problems
                                 placed in one grid, separated by inactive cells and stacked
                                 along z, are solved together by geneo_solve_segments. */
+  const uint8_t *natural_faces; /* NULL: E x n = 0 on every boundary face; else [nx*ny*nz]
+                                per cell, bit 2a + s (a = 0, 1, 2 for x, y, z; s = 0 lower,
+                                1 upper side) marks that face of the cell as a natural
+                                (Neumann) boundary when it lies on the boundary (hole
+                                surfaces, lateral faces: Sec. 4, mixed boundary conditions);
+                                its edges and vertices are then unknowns. */
 } geneo_problem;
 
 typedef struct {

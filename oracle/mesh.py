@@ -60,12 +60,18 @@ def vertex_id(i, j, k, nx, ny):
     return i + (nx + 1) * (j + (ny + 1) * k)
 
 
-def build_mesh(nx, ny, nz, h, active):
+def build_mesh(nx, ny, nz, h, active, natural=None):
     """Split every active cell into six Kuhn tetrahedra, number the edges in
     lexicographic (tail, head) order and mark the Dirichlet boundary: faces
     with exactly one incident active tetrahedron carry E x n = 0 (Sec. 1,
     eq. "positivemaxwell"), so their edges and vertices are eliminated from
-    the unknowns."""
+    the unknowns.
+
+    natural (optional, uint8 per cell): bit 2a + s set marks the face of the
+    cell on axis a (x, y, z) at its lower (s = 0) or upper (s = 1) side as a
+    natural (Neumann) boundary when it lies on the boundary, as on the hole
+    surfaces and lateral faces of Sec. 4; only the remaining boundary faces
+    are Dirichlet."""
     h = np.broadcast_to(np.asarray(h, dtype=np.float64), (3,)).copy()
     nverts = (nx + 1) * (ny + 1) * (nz + 1)
     v = np.arange(nverts)
@@ -103,7 +109,25 @@ def build_mesh(nx, ny, nz, h, active):
     faces = np.stack([ufk // (nverts * nverts), (ufk // nverts) % nverts, ufk % nverts], axis=1)
     tet_faces = finv.reshape(4, -1).T.copy()
 
-    bface = faces[fcount == 1]
+    bmask = fcount == 1
+    if natural is not None:
+        # the cell face each boundary triangle lies on, from its one tetrahedron
+        ntet = len(tets)
+        owner = np.empty(len(faces), dtype=np.int64)
+        owner[tet_faces.reshape(-1)] = np.repeat(np.arange(ntet), 4)
+        bidx = np.nonzero(bmask)[0]
+        cell = tet_cell[owner[bidx]]
+        fc = np.stack([vi[faces[bidx]], vj[faces[bidx]], vk[faces[bidx]]], axis=2)  # [nb, 3 v, 3 axes]
+        lo = np.stack([cell % nx, (cell // nx) % ny, cell // (nx * ny)], axis=1)
+        flat = np.all(fc == fc[:, :1, :], axis=1)       # axes on which the triangle is flat
+        assert np.all(flat.sum(1) == 1)
+        axis = np.argmax(flat, axis=1)
+        side = fc[np.arange(len(bidx)), 0, axis] - lo[np.arange(len(bidx)), axis]
+        assert np.all((side == 0) | (side == 1))
+        nat = (np.asarray(natural, dtype=np.int64)[cell] >> (2 * axis + side)) & 1
+        bmask = bmask.copy()
+        bmask[bidx[nat == 1]] = False
+    bface = faces[bmask]
     dir_vert = np.zeros(nverts, dtype=bool)
     dir_vert[bface.reshape(-1)] = True
     bpairs = np.concatenate([bface[:, [0, 1]], bface[:, [0, 2]], bface[:, [1, 2]]])

@@ -33,7 +33,8 @@ class OracleProblem:
 
 def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
                   pou="boolean"):
-    mesh = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    mesh = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active,
+                      natural=getattr(w, "natural", None))
     A = assemble_A(mesh, w)
     AT = local_element_A(mesh, w)
     b = assemble_rhs(mesh, w)

@@ -30,7 +30,8 @@ class Problem(C.Structure):
                 ("eps", C.POINTER(C.c_double)), ("gamma", C.c_double),
                 ("px", C.c_int32), ("py", C.c_int32), ("pz", C.c_int32),
                 ("overlap", C.c_int32), ("tau", C.c_double),
-                ("cell_part", C.POINTER(C.c_int32))]
+                ("cell_part", C.POINTER(C.c_int32)),
+                ("natural_faces", C.POINTER(C.c_uint8))]
 
 
 class Options(C.Structure):
@@ -196,15 +197,18 @@ def _problem_array(workloads, keep):
         mu = np.ascontiguousarray(np.broadcast_to(np.asarray(w.mu_inv, dtype=np.float64), (nc,)))
         ep = np.ascontiguousarray(np.broadcast_to(np.asarray(w.eps, dtype=np.float64), (nc,)))
         keep += [a, mu, ep]
-        cp = None
+        cp = nat = None
         if getattr(w, "cell_part", None) is not None:
             keep.append(np.ascontiguousarray(w.cell_part, dtype=np.int32))
             cp = keep[-1].ctypes.data_as(C.POINTER(C.c_int32))
+        if getattr(w, "natural", None) is not None:
+            keep.append(np.ascontiguousarray(w.natural, dtype=np.uint8))
+            nat = keep[-1].ctypes.data_as(C.POINTER(C.c_uint8))
         arr[q] = Problem(w.nx, w.ny, w.nz, w.hx, w.hy, w.hz,
                          a.ctypes.data_as(C.POINTER(C.c_uint8)),
                          mu.ctypes.data_as(C.POINTER(C.c_double)),
                          ep.ctypes.data_as(C.POINTER(C.c_double)),
-                         w.gamma, w.parts[0], w.parts[1], w.parts[2], w.overlap, w.tau, cp)
+                         w.gamma, w.parts[0], w.parts[1], w.parts[2], w.overlap, w.tau, cp, nat)
     return arr
 
 
@@ -262,21 +266,24 @@ class Solver:
     """One set-up problem on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, h, active, mu_inv, eps, gamma, parts, overlap, tau,
-                 options=None, cell_part=None, **opt_kw):
+                 options=None, cell_part=None, natural=None, **opt_kw):
         lib = load_library()
         self._keep = [np.ascontiguousarray(active, dtype=np.uint8),
                       np.ascontiguousarray(mu_inv, dtype=np.float64),
                       np.ascontiguousarray(eps, dtype=np.float64)]
-        cp = None
+        cp = nat = None
         if cell_part is not None:
             self._keep.append(np.ascontiguousarray(cell_part, dtype=np.int32))
             cp = self._keep[-1].ctypes.data_as(C.POINTER(C.c_int32))
+        if natural is not None:
+            self._keep.append(np.ascontiguousarray(natural, dtype=np.uint8))
+            nat = self._keep[-1].ctypes.data_as(C.POINTER(C.c_uint8))
         hx, hy, hz = (h, h, h) if np.isscalar(h) else h
         p = Problem(nx, ny, nz, hx, hy, hz,
                     self._keep[0].ctypes.data_as(C.POINTER(C.c_uint8)),
                     self._keep[1].ctypes.data_as(C.POINTER(C.c_double)),
                     self._keep[2].ctypes.data_as(C.POINTER(C.c_double)),
-                    gamma, parts[0], parts[1], parts[2], overlap, tau, cp)
+                    gamma, parts[0], parts[1], parts[2], overlap, tau, cp, nat)
         o = options if options is not None else default_options(**opt_kw)
         ctx = C.c_void_p()
         _check(lib.geneo_setup(C.byref(p), C.byref(o), C.byref(ctx)))
@@ -288,7 +295,8 @@ class Solver:
     @classmethod
     def from_workload(cls, w, **kw):
         return cls(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active, w.mu_inv, w.eps, w.gamma,
-                   w.parts, w.overlap, w.tau, cell_part=getattr(w, "cell_part", None), **kw)
+                   w.parts, w.overlap, w.tau, cell_part=getattr(w, "cell_part", None),
+                   natural=getattr(w, "natural", None), **kw)
 
     @classmethod
     def topology(cls, w, options=None, **opt_kw):

@@ -146,6 +146,7 @@ static geneo_ctx *new_context(const geneo_problem *p, const geneo_options &o) {
   c->mu_inv.assign(p->mu_inv, p->mu_inv + nc);
   c->eps.assign(p->eps, p->eps + nc);
   if (p->cell_part) c->cell_part.assign(p->cell_part, p->cell_part + nc);
+  if (p->natural_faces) c->natural.assign(p->natural_faces, p->natural_faces + nc);
   c->opt = o;
   return c;
 }

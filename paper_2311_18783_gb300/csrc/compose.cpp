@@ -19,6 +19,7 @@ void compose_problems(int32_t nprob, const geneo_problem *probs, bool arrays, Co
     const geneo_problem &q = probs[p];
     if (q.nx < 1 || q.ny < 1 || q.nz < 1) bad("compose: grid sizes must be positive");
     if (!(q.hx > 0) || q.hx != q.hy || q.hx != q.hz) bad("compose: cells must be cubic");
+    if (q.natural_faces) bad("compose: natural boundary faces are not supported");
     if (!(q.gamma > 0)) bad("compose: gamma must be > 0");
     if (q.overlap != probs[0].overlap || q.tau != probs[0].tau)
       bad("compose: all problems must share overlap and tau");

@@ -33,6 +33,7 @@ struct geneo_ctx {
   std::vector<uint8_t> active;
   std::vector<double> mu_inv, eps;
   std::vector<int32_t> cell_part;  // explicit partition, empty for boxes
+  std::vector<uint8_t> natural;    // natural boundary faces per cell, empty for none
   bool host_only = false;          // geneo_setup_topology: integer data only, no device
   // independent components (vertex-connected active cells): unknown ranges
   // [seg_off[s], seg_off[s+1]) when contiguous (seg_ok), per-unknown component

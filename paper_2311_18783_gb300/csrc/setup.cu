@@ -650,7 +650,8 @@ static void build_components(geneo_ctx *c) {
 
 void setup_topology(geneo_ctx *c) {
   Topology &t = c->topo;
-  build_topology(c->nx, c->ny, c->nz, c->h, c->active.data(), t);
+  build_topology(c->nx, c->ny, c->nz, c->h, c->active.data(), t,
+                 c->natural.empty() ? nullptr : c->natural.data());
   if (t.ndofs() == 0) throw Error(GENEO_ERR_INVALID_ARG, "the mesh has no interior edge");
   build_decomposition(t, c->px, c->py, c->pz, c->overlap, c->dec,
                       c->cell_part.empty() ? nullptr : c->cell_part.data());

@@ -50,7 +50,7 @@ struct UnionFind {
 }  // namespace
 
 void build_topology(int nx, int ny, int nz, const double h[3], const uint8_t *active,
-                    Topology &t) {
+                    Topology &t, const uint8_t *natural) {
   t = Topology();
   t.nx = nx;
   t.ny = ny;
@@ -130,7 +130,8 @@ void build_topology(int nx, int ny, int nz, const double h[3], const uint8_t *ac
       t.first_cell[id] = std::min(t.first_cell[id], t.tet_cell[tt]);
     }
   // boundary: a square cell face whose neighbour cell is absent; both of its
-  // triangles are boundary faces (exactly one incident active tetrahedron)
+  // triangles are boundary faces (exactly one incident active tetrahedron).
+  // Dirichlet unless the cell marks that face natural.
   t.dir_edge.assign(ne, 0);
   t.dir_vert.assign(t.nverts, 0);
   t.used_vert.assign(t.nverts, 0);
@@ -153,6 +154,7 @@ void build_topology(int nx, int ny, int nz, const double h[3], const uint8_t *ac
         int64_t nb[3] = {ci, cj, ck};
         nb[a] += side ? 1 : -1;
         if (is_active(nb[0], nb[1], nb[2])) continue;
+        if (natural && ((natural[c] >> (2 * a + side)) & 1)) continue;  // Neumann face
         // square face at coordinate a = side, spanned by the other axes b < c
         const int b = (a + 1) % 3 < (a + 2) % 3 ? (a + 1) % 3 : (a + 2) % 3;
         const int cc = 3 - a - b;

@@ -88,8 +88,11 @@ struct SNKColumns {
   std::vector<int8_t> sgn;          // +1 / -1
 };
 
+// natural (optional): per cell, bit 2a + s marks its face on axis a at side
+// s (0 lower, 1 upper) as a natural boundary when that face is on the
+// boundary; the other boundary faces are Dirichlet (E x n = 0).
 void build_topology(int nx, int ny, int nz, const double h[3], const uint8_t *active,
-                    Topology &t);
+                    Topology &t, const uint8_t *natural = nullptr);
 // Boxes px x py x pz, or (cell_part non-null) the given subdomain of every
 // active cell; empty parts are dropped and the rest renumbered in order.
 void build_decomposition(const Topology &t, int px, int py, int pz, int overlap,

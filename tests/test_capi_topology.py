@@ -4,7 +4,8 @@ CUDA call.  Mesh edges, Dirichlet flags, unknown numbering, CSR pattern,
 subdomain index sets N_i, partition-of-unity owners, split near-kernel
 columns and k0/k1 must be identical to the oracle's (oracle/mesh.py,
 oracle/dd.py, oracle/coarse.py) on the parity cases, the 32^3 benchmark
-workload, an explicit cell partition and composed independent problems;
+workload, an explicit cell partition, composed independent problems and
+natural (Neumann) boundary faces on lateral sides and hole surfaces;
 the kept vertices of every local gradient G_j as well; compute calls on
 such a context are refused with STATE."""
 import os
@@ -52,6 +53,11 @@ def _metis_like():
     return w
 
 
+def _natural(w, **kw):
+    w.natural = W.natural_faces(w, **kw)
+    return w
+
+
 CASES = {
     "cube8": W.unit_cube_8,
     "hetero_hole": lambda: _hetero(),
@@ -64,6 +70,14 @@ CASES = {
     # a batching cube with a box whose edges all join boundary vertices
     # (no kept vertex, an empty G_j)
     "batch35_n9": lambda: [w for w in W.many_problems(256, seed=3) if w.nx <= 10][4],
+    # natural (Neumann) boundary faces, Sec. 4's mixed conditions
+    "beam_mixed": lambda: _natural(W.box(16, 4, 4, h=0.25, parts=(4, 1, 1)),
+                                   sides=((1, 0), (1, 1))),
+    "holes_natural": lambda: _natural(_hetero(seed=5), holes=True),
+    "beam_holes_natural": lambda: W.beam_holes(4),
+    "beam_holes_dirichlet": lambda: W.beam_holes(4, natural_holes=False),
+    "all_natural": lambda: _natural(W.box(5, 4, 3, parts=(2, 2, 1), holes=(((2, 3), (1, 3), (1, 2)),)),
+                                    holes=True, sides=[(a, s) for a in range(3) for s in (0, 1)]),
 }
 
 
@@ -75,7 +89,8 @@ def test_integer_setup_matches_oracle(pkg, name):
     from oracle.coarse import snk_columns
     w = CASES[name]()
     s = pkg.Solver.topology(w)
-    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active,
+                   natural=getattr(w, "natural", None))
     dec = decompose(m, w.parts, w.overlap, cell_part=getattr(w, "cell_part", None))
     assert np.array_equal(s.export("edges").reshape(-1, 2), m.edges)
     assert np.array_equal(s.export("dir_edge").astype(bool), m.dir_edge)

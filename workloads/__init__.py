@@ -48,6 +48,7 @@ class Workload:
     f_slot: np.ndarray          # float64 [nrhs, nverts, 7, 3]
     meta: dict = field(default_factory=dict)
     cell_part: np.ndarray = None  # int32 [ncells] explicit subdomain per cell, or None (boxes)
+    natural: np.ndarray = None    # uint8 [ncells] natural boundary faces (bit 2a + side), or None
 
     @property
     def ncells(self):
@@ -262,6 +263,7 @@ def compose(problems, name="composite"):
     right-hand side come from mu^-1 / r, gamma eps r and f r^2.  All problems
     must share the overlap and tau.  meta["zoff"] records the offsets."""
     for w in problems:
+        assert w.natural is None, "natural boundary faces are not supported here"
         assert w.hx == w.hy == w.hz and w.overlap == problems[0].overlap
         assert w.tau == problems[0].tau and w.nrhs == problems[0].nrhs
     h = min(w.hx for w in problems)
@@ -303,3 +305,63 @@ def compose(problems, name="composite"):
     return Workload(name, nx, ny, nz, h, h, h, active, mu, eps, 1.0, (1, 1, 1),
                     problems[0].overlap, problems[0].tau, f, meta={"zoff": zoff},
                     cell_part=part)
+
+
+def natural_faces(w, holes=False, sides=()):
+    """Natural (Neumann) boundary faces of workload w as a uint8 mask per
+    cell, bit 2a + s for the face on axis a (0, 1, 2 = x, y, z) at the lower
+    (s = 0) or upper (s = 1) side of the cell.  holes=True marks every face
+    towards an inactive cell inside the grid (the hole surfaces of Sec. 4);
+    sides lists (a, s) pairs of the grid's outer faces to mark (e.g. two
+    opposite lateral faces of the beam: ((1, 0), (1, 1))).  Other boundary
+    faces stay Dirichlet."""
+    nx, ny, nz = w.nx, w.ny, w.nz
+    act = np.asarray(w.active).reshape(nz, ny, nx).astype(bool)
+    mask = np.zeros((nz, ny, nx), dtype=np.uint8)
+    n = (nx, ny, nz)
+    for a in range(3):
+        ax = 2 - a  # array axis of grid axis a (k, j, i order)
+        for s in (0, 1):
+            if holes:
+                nb = np.zeros_like(act)
+                src = [slice(None)] * 3
+                dst = [slice(None)] * 3
+                if s == 0:
+                    src[ax], dst[ax] = slice(0, n[a] - 1), slice(1, n[a])
+                else:
+                    src[ax], dst[ax] = slice(1, n[a]), slice(0, n[a] - 1)
+                nb[tuple(dst)] = ~act[tuple(src)]  # neighbour inside the grid and inactive
+                mask |= (nb & act).astype(np.uint8) << (2 * a + s)
+            if (a, s) in tuple(sides):
+                edge = [slice(None)] * 3
+                edge[ax] = 0 if s == 0 else n[a] - 1
+                layer = np.zeros_like(act)
+                layer[tuple(edge)] = True
+                mask |= (layer & act).astype(np.uint8) << (2 * a + s)
+    return mask.reshape(-1)
+
+
+def beam_holes(nsub=4, m=8, natural_holes=True, gamma=1e-3, tau=0.1):
+    """The beam with holes of Sec. 4 at mesh size h = 1/m: (nsub/2) x 1 x 1,
+    nsub boxes along x, overlap 1.  Four square holes (side h * max(1, m/8))
+    run along the whole length at y, z in {m/4, 3m/4 - 1} cells; in every
+    box two square holes cross from the lateral face y = 0 to y = 1, at
+    z = m/4 (a quarter into the box) and at z = 3m/4 - 1 (three quarters
+    in), each meeting two of the length holes.  The hole sizes and
+    positions are a reading of the paper's description (its figure is not
+    available).  natural_holes: Neumann conditions on the hole surfaces
+    (Sec. 4, mixed), the outer faces Dirichlet; else Dirichlet everywhere."""
+    nx, ny, nz = nsub * m // 2, m, m
+    L = nx // nsub
+    a, b = m // 4, m - m // 4 - 1
+    s = max(1, m // 8)
+    holes = [((0, nx), (y, y + s), (z, z + s)) for (y, z) in ((a, a), (a, b), (b, a), (b, b))]
+    for q in range(nsub):
+        x0 = q * L
+        holes.append(((x0 + L // 4, x0 + L // 4 + s), (0, ny), (a, a + s)))
+        holes.append(((x0 + 3 * L // 4 - s, x0 + 3 * L // 4), (0, ny), (b, b + s)))
+    w = box(nx, ny, nz, h=1.0 / m, parts=(nsub, 1, 1), overlap=1, gamma=gamma, tau=tau,
+            holes=holes, name=f"beam_holes_{nsub}_{'natural' if natural_holes else 'dirichlet'}")
+    if natural_holes:
+        w.natural = natural_faces(w, holes=True)
+    return w
