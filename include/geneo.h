@@ -70,6 +70,8 @@ extern "C" {
 
 #define GENEO_COARSE_NONE 0        /* one-level additive Schwarz (eq. "AS") */
 #define GENEO_COARSE_SNK 1         /* split near-kernel space (definition "near-kernelCS") */
+#define GENEO_COARSE_NK 2          /* global near-kernel G: one gradient column per interior
+                                      vertex (Sec. 4, variants AS-NK and AS-NK-GenEO) */
 
 #define GENEO_TAU_RECIPROCAL 0     /* select lambda > 1/tau */
 #define GENEO_TAU_PAPER 1          /* select lambda > tau (GEVP "tauthresholdAS" literally) */

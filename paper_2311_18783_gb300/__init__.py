@@ -7,9 +7,9 @@ point loads the library first and raises if it has not been built: there is
 no CPU fallback.
 """
 from .api import (GeneoError, Mlp, Options, Solver, compose, load_library, shard_problems,
-                  PREC_FP64, PREC_FP32, PREC_BF16, COARSE_NONE, COARSE_SNK, TAU_RECIPROCAL,
-                  TAU_PAPER)
+                  PREC_FP64, PREC_FP32, PREC_BF16, COARSE_NONE, COARSE_SNK, COARSE_NK,
+                  TAU_RECIPROCAL, TAU_PAPER)
 
 __all__ = ["GeneoError", "Mlp", "Options", "Solver", "compose", "load_library", "shard_problems",
-           "PREC_FP64", "PREC_FP32", "PREC_BF16", "COARSE_NONE", "COARSE_SNK", "TAU_RECIPROCAL",
-           "TAU_PAPER"]
+           "PREC_FP64", "PREC_FP32", "PREC_BF16", "COARSE_NONE", "COARSE_SNK", "COARSE_NK",
+           "TAU_RECIPROCAL", "TAU_PAPER"]

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgeneo.so")
 
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
-COARSE_NONE, COARSE_SNK = 0, 1
+COARSE_NONE, COARSE_SNK, COARSE_NK = 0, 1, 2
 TAU_RECIPROCAL, TAU_PAPER = 0, 1
 NOT_CONVERGED = 1
 

@@ -109,7 +109,8 @@ static int check_setup_args(const geneo_problem *p, const geneo_options *opt, ge
   if (o.precision != GENEO_PREC_FP64 && o.precision != GENEO_PREC_FP32 &&
       o.precision != GENEO_PREC_BF16)
     return fail(GENEO_ERR_INVALID_ARG, "unknown precision");
-  if (o.coarse != GENEO_COARSE_NONE && o.coarse != GENEO_COARSE_SNK)
+  if (o.coarse != GENEO_COARSE_NONE && o.coarse != GENEO_COARSE_SNK &&
+      o.coarse != GENEO_COARSE_NK)
     return fail(GENEO_ERR_INVALID_ARG, "unknown coarse mode");
   if (o.lobpcg_block < 1 || o.lobpcg_block > 16 || o.lobpcg_maxit < 1 || !(o.lobpcg_tol > 0))
     return fail(GENEO_ERR_INVALID_ARG, "bad LOBPCG parameters");

@@ -657,8 +657,9 @@ void setup_topology(geneo_ctx *c) {
                       c->cell_part.empty() ? nullptr : c->cell_part.data());
   build_components(c);
   build_local_structure(t, c->dec, c->ls);
-  if (c->host_only && c->opt.coarse == GENEO_COARSE_SNK) {
-    build_snk(t, c->dec, c->snk);
+  if (c->host_only && c->opt.coarse != GENEO_COARSE_NONE) {
+    if (c->opt.coarse == GENEO_COARSE_NK) build_nk(t, c->snk);
+    else build_snk(t, c->dec, c->snk);
     c->n0 = c->n0_snk = (int64_t)c->snk.sub.size();
     c->zc_ptr = c->snk.ptr;
     c->zc_row = c->snk.row;
@@ -758,8 +759,10 @@ void setup_all(geneo_ctx *c) {
 
   // --- coarse space
   c->n0 = c->n0_snk = c->n0_geneo = 0;
-  if (c->opt.coarse == GENEO_COARSE_SNK) {
-    build_snk(t, d, c->snk);
+  if (c->opt.coarse != GENEO_COARSE_NONE) {
+    // near-kernel part of Z: split (SNK, the method) or global (NK, Sec. 4)
+    if (c->opt.coarse == GENEO_COARSE_NK) build_nk(t, c->snk);
+    else build_snk(t, d, c->snk);
     c->n0_snk = (int64_t)c->snk.sub.size();
     c->zc_ptr = c->snk.ptr;
     c->zc_row = c->snk.row;

@@ -525,6 +525,37 @@ void build_local_structure(const Topology &t, const Decomposition &d, LocalStruc
   for (int64_t q = 0; q < tot; ++q) ls.g2l_slot[fill[d.N_idx[q]]++] = q;
 }
 
+void build_nk(const Topology &t, SNKColumns &nk) {
+  nk = SNKColumns();
+  const int64_t nv = (int64_t)t.dof_vert.size();
+  std::vector<int64_t> cnt(nv + 1, 0);
+  const int64_t n = t.ndofs();
+  for (int64_t r = 0; r < n; ++r) {
+    const int32_t e = t.dof_edge[r];
+    for (int s = 0; s < 2; ++s) {
+      const int32_t k = t.vert_dof[t.edges[2 * e + s]];
+      if (k >= 0) cnt[k + 1]++;
+    }
+  }
+  for (int64_t k = 0; k < nv; ++k) cnt[k + 1] += cnt[k];
+  nk.ptr = cnt;
+  nk.row.assign(cnt[nv], 0);
+  nk.sgn.assign(cnt[nv], 0);
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int64_t r = 0; r < n; ++r) {  // rows visited in ascending order
+    const int32_t e = t.dof_edge[r];
+    for (int s = 0; s < 2; ++s) {
+      const int32_t k = t.vert_dof[t.edges[2 * e + s]];
+      if (k < 0) continue;
+      nk.row[fill[k]] = (int32_t)r;
+      nk.sgn[fill[k]] = s ? 1 : -1;  // head +1, tail -1
+      ++fill[k];
+    }
+  }
+  nk.sub.assign(nv, -1);
+  nk.vert.assign(t.dof_vert.begin(), t.dof_vert.end());
+}
+
 void build_snk(const Topology &t, const Decomposition &d, SNKColumns &snk) {
   snk = SNKColumns();
   snk.ptr.push_back(0);

@@ -99,6 +99,10 @@ void build_decomposition(const Topology &t, int px, int py, int pz, int overlap,
                          Decomposition &d, const int32_t *cell_part = nullptr);
 void build_local_structure(const Topology &t, const Decomposition &d, LocalStructure &ls);
 void build_snk(const Topology &t, const Decomposition &d, SNKColumns &snk);
+// The global near-kernel G (Sec. 4, "NK"): one column per interior vertex in
+// dof_vert order, +1 on the unknown edges ending at it and -1 on those
+// starting at it, rows ascending; sub = -1.
+void build_nk(const Topology &t, SNKColumns &nk);
 
 // kept vertices of an edge set: interior endpoints minus the highest vertex of
 // every component (through edges between interior vertices) with no edge to a

@@ -147,3 +147,24 @@ def test_compute_calls_refused(pkg):
     assert lib.geneo_use_precision(s._ctx, pkg.PREC_FP64) == -7
     assert lib.geneo_solve(s._ctx, None, None, 1e-8, 10, None, None) == -7
     s.close()
+
+
+@pytest.mark.parametrize("name", ["hetero_hole", "beam_holes_natural", "cube8"])
+def test_global_near_kernel_columns(pkg, name):
+    """coarse = NK (Sec. 4, AS-NK): one gradient column per interior vertex,
+    equal to the oracle's nk_columns (rows and signs)."""
+    from oracle.mesh import build_mesh
+    from oracle.coarse import nk_columns
+    w = CASES[name]()
+    s = pkg.Solver.topology(w, coarse=pkg.COARSE_NK)
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active,
+                   natural=getattr(w, "natural", None))
+    ref = nk_columns(m)
+    assert s.sizes["n0_snk"] == len(ref) == m.nvdofs
+    zp, zr, zv = s.export("Zcol_ptr"), s.export("Zcol_row"), s.export("Zcol_val")
+    assert np.array_equal(s.export("snk_vert"), np.array([c[1] for c in ref], np.int32))
+    for k, (_, _, rows, vals) in enumerate(ref):
+        o = np.argsort(rows)
+        assert np.array_equal(zr[zp[k]:zp[k + 1]], rows[o])
+        assert np.array_equal(zv[zp[k]:zp[k + 1]], vals[o])
+    s.close()
