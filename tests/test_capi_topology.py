@@ -168,3 +168,40 @@ def test_global_near_kernel_columns(pkg, name):
         assert np.array_equal(zr[zp[k]:zp[k + 1]], rows[o])
         assert np.array_equal(zv[zp[k]:zp[k + 1]], vals[o])
     s.close()
+
+
+def test_invalid_problems_rejected_without_gpu(pkg):
+    """Argument checks of the set-up (shared by geneo_setup and
+    geneo_setup_topology) on the CPU: each bad input gives INVALID_ARG (-1)
+    and no context."""
+    def expect_invalid(w, **opt):
+        with pytest.raises(pkg.GeneoError) as e:
+            pkg.Solver.topology(w, **opt)
+        assert e.value.status == -1
+    ok = W.box(4, 3, 3, parts=(2, 1, 1))
+    s = pkg.Solver.topology(ok)
+    assert s.sizes["nsub"] == 2
+    s.close()
+    bad = W.box(4, 3, 3, parts=(2, 1, 1), gamma=1.0)
+    bad.gamma = 0.0
+    expect_invalid(bad)
+    bad = W.box(4, 3, 3, parts=(2, 1, 1))
+    bad.overlap = 0
+    expect_invalid(bad)
+    bad = W.box(4, 3, 3, parts=(5, 1, 1))
+    expect_invalid(bad)
+    bad = W.box(4, 3, 3, parts=(2, 1, 1))
+    bad.mu_inv = np.where(np.arange(36) == 7, -1.0, 1.0)
+    expect_invalid(bad)
+    bad = W.box(4, 3, 3, parts=(2, 1, 1))
+    bad.cell_part = np.full(36, -2, np.int32)
+    expect_invalid(bad)
+    # no active cell: no unknown at all
+    expect_invalid(W.box(2, 2, 2, parts=(1, 1, 1), holes=(((0, 2), (0, 2), (0, 2)),)))
+    # one cell still has one unknown, its body diagonal (the only edge off the faces)
+    one = pkg.Solver.topology(W.box(1, 1, 1, parts=(1, 1, 1)))
+    assert one.n == 1
+    one.close()
+    expect_invalid(ok, lobpcg_block=17)
+    expect_invalid(ok, coarse=3)
+    expect_invalid(ok, lobpcg_neumann=2)
