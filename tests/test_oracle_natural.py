@@ -4,6 +4,9 @@ conditions), pinned by what the mathematics and the paper fix:
   is eliminated (the closed-form edge count of the box);
 * a natural mark on a face that is not on the boundary changes nothing;
 * K G = 0 still holds with the gradients of the vertices on natural faces;
+* a manufactured curl-free field whose tangential trace vanishes only on
+  the Dirichlet faces is recovered at the expected rate, and not at all
+  when the natural faces are made Dirichlet;
 * Sec. 4, beam with holes: with Dirichlet conditions on the hole surfaces
   GenEO selects nothing, and with Neumann conditions there it selects
   vectors in every box, the same number in every interior box whatever the
@@ -71,3 +74,46 @@ def test_geneo_needs_natural_holes():
         assert len(set(c[1:-1])) == 1       # the same count in every interior box
     assert counts[4][1] == counts[6][1]
     assert counts[4][0] == counts[6][0] and counts[4][-1] == counts[6][-1]
+
+
+def _natural_error(n, natural=True):
+    """Relative discrete L2 error of the FE solution against the edge
+    interpolant of E* = grad(sin pi x cos pi y sin pi z) on the unit cube,
+    with f = gamma E* (curl E* = 0, so curl E* x n = 0 holds on every face),
+    E* x n = 0 on the faces x = 0, 1 and z = 0, 1, and a nonzero tangential
+    trace on y = 0, 1, which are the natural faces."""
+    import scipy.sparse.linalg as spla
+    from oracle.mesh import edge_slot
+    from oracle.fem import assemble_A, assemble_rhs, element_matrices, assemble_edges
+    from test_oracle_mesh_fem import edge_vectors
+    w = W.box(n, n, n, gamma=1.0)
+    nat = W.natural_faces(w, sides=((1, 0), (1, 1))) if natural else None
+    m = build_mesh(n, n, n, 1.0 / n, w.active, natural=nat)
+    pi = np.pi
+    Es = lambda x: np.stack([pi * np.cos(pi * x[:, 0]) * np.cos(pi * x[:, 1]) * np.sin(pi * x[:, 2]),
+                             -pi * np.sin(pi * x[:, 0]) * np.sin(pi * x[:, 1]) * np.sin(pi * x[:, 2]),
+                             pi * np.sin(pi * x[:, 0]) * np.cos(pi * x[:, 1]) * np.cos(pi * x[:, 2])],
+                            axis=1)
+    base, d = edge_slot(m)
+    mid = 0.5 * (m.coords[m.edges[:, 0]] + m.coords[m.edges[:, 1]])
+    f_slot = np.zeros((1, m.nverts, 7, 3))
+    f_slot[0, base, d] = Es(mid)
+    w.f_slot = f_slot
+    u = spla.spsolve(assemble_A(m, w).tocsc(), assemble_rhs(m, w)[0])
+    t = edge_vectors(m)
+    gp = [(0.5 - np.sqrt(15) / 10, 5 / 18), (0.5, 8 / 18), (0.5 + np.sqrt(15) / 10, 5 / 18)]
+    pi_u = sum(wq * np.einsum('ei,ei->e', Es(m.coords[m.edges[:, 0]] + s * t), t) for s, wq in gp)
+    pi_u = pi_u[m.dof_edge]
+    _, M, _ = element_matrices(m.coords[m.tets], np.ones(len(m.tets)), np.ones(len(m.tets)))
+    Mf = assemble_edges(m, M)[m.dof_edge][:, m.dof_edge]
+    e = u - pi_u
+    return np.sqrt(e @ (Mf @ e) / (pi_u @ (Mf @ pi_u)))
+
+
+@pytest.mark.slow
+def test_natural_faces_manufactured_rate():
+    errs = [_natural_error(n) for n in (4, 8, 16)]
+    rates = [np.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(r >= 0.9 for r in rates), (errs, rates)
+    # the same field with Dirichlet y faces is not a solution: no convergence
+    assert _natural_error(16, natural=False) > 0.2
