@@ -335,3 +335,35 @@ def test_cell_partition_equal_to_boxes():
     for i in range(ref.nsub):
         assert np.array_equal(got.N[i], ref.N[i])
         assert np.array_equal(got.D[i], ref.D[i])
+
+
+def test_classical_pencil_has_too_many_large_eigenvalues():
+    """Sec. 3.2, remark on eq. "eigGenEOClassis": without the filter
+    (I - xi_0j), the pencil D_j A_j D_j V = lambda A_j^Neu V has many large
+    eigenvalues (the gradients of the kept vertices, which A_j^Neu nearly
+    annihilates), while the filtered pencil of eq. "eigAtildeBAS" keeps only
+    the few that matter (none on this Dirichlet beam with holes)."""
+    import numpy as np
+    import scipy.linalg as sla
+    import workloads as W
+    from oracle.mesh import build_mesh
+    from oracle.fem import assemble_A, local_element_A
+    from oracle.dd import decompose
+    from oracle.coarse import local_gevp, tau_paper
+    w = W.beam_holes(4, natural_holes=False)
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    A = assemble_A(m, w)
+    AT = local_element_A(m, w)
+    dec = decompose(m, w.parts, w.overlap)
+    tp = tau_paper(w.tau, "reciprocal")
+    j = 1
+    g = local_gevp(m, w, A, AT, dec, j)
+    D = dec.D[j]
+    Ai = g.Ai.toarray() if hasattr(g.Ai, "toarray") else np.asarray(g.Ai)
+    classical = sla.eigvalsh(D[:, None] * Ai * D[None, :], np.asarray(g.Aneu))
+    n_classical = int((classical > tp).sum())
+    n_filtered = int((g.lam > tp).sum())
+    assert n_filtered == 0
+    assert n_classical > 50
+    # they are gradient-driven, far above tau (order 1/gamma)
+    assert classical[classical > tp].min() > 100 * tp
