@@ -30,7 +30,10 @@ three-dimensional general topologies" (arXiv 2311.18783):
 Every function states the passage it follows.  All floating point is
 float64.  Where the paper is silent the oracle takes these readings: the
 Kuhn six-tetrahedra split of each cubic cell, Dirichlet dofs eliminated, the
-core-edge partition of unity D_i(e) = chi_i(e) / sum_j chi_j(e), the
-reciprocal tau convention (select lambda > 1/tau) by default, and removal of
-duplicate and floating near-kernel columns so that Z has full rank.
+Boolean partition of unity (an edge belongs to the subdomain of the lowest
+active cell containing it, D_i = 1 on the edges subdomain i owns; the
+core-edge alternative D_i(e) = chi_i(e) / sum_j chi_j(e) is kept as
+``decompose(..., pou="core")``), the reciprocal tau convention (select
+lambda > 1/tau) by default, and removal of duplicate and floating
+near-kernel columns so that Z has full rank.
 """

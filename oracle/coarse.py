@@ -109,10 +109,16 @@ def snk_columns(mesh, dec):
 
 def nk_columns(mesh):
     """Global near-kernel G (coarse variant 'NK' of Sec. 4): one column per
-    interior vertex."""
+    interior vertex, except the highest vertex of every connected component
+    of unknown edges that has no edge to a Dirichlet vertex (possible when
+    every boundary face of a component is natural): there G times the
+    constant vanishes, and Sec. 3.2 needs a Z of full column rank."""
     G = mesh_gradient(mesh).tocsc()
+    kept = set(_kept_vertices(mesh, np.arange(mesh.dof_edge.shape[0])).tolist())
     cols = []
     for k, v in enumerate(mesh.dof_vert.tolist()):
+        if v not in kept:
+            continue
         s = slice(G.indptr[k], G.indptr[k + 1])
         cols.append((-1, v, G.indices[s].copy(), G.data[s].copy()))
     return cols

@@ -528,32 +528,43 @@ void build_local_structure(const Topology &t, const Decomposition &d, LocalStruc
 void build_nk(const Topology &t, SNKColumns &nk) {
   nk = SNKColumns();
   const int64_t nv = (int64_t)t.dof_vert.size();
-  std::vector<int64_t> cnt(nv + 1, 0);
   const int64_t n = t.ndofs();
+  // A connected component of unknown edges with no edge to a Dirichlet
+  // vertex (every boundary face natural) carries the constant in the kernel
+  // of G: its highest vertex is dropped so that Z = G keeps full column rank
+  // and E = G^T A G stays SPD (Sec. 3.2 needs a full-rank Z).
+  std::vector<int32_t> all(n);
+  for (int64_t r = 0; r < n; ++r) all[r] = (int32_t)r;
+  const std::vector<int32_t> kv = kept_vertices(t, all.data(), n);
+  std::vector<int32_t> col_of(nv, -1);  // vertex unknown -> column
+  for (size_t q = 0; q < kv.size(); ++q) col_of[t.vert_dof[kv[q]]] = (int32_t)q;
+  const int64_t ncol = (int64_t)kv.size();
+  std::vector<int64_t> cnt(ncol + 1, 0);
   for (int64_t r = 0; r < n; ++r) {
     const int32_t e = t.dof_edge[r];
     for (int s = 0; s < 2; ++s) {
       const int32_t k = t.vert_dof[t.edges[2 * e + s]];
-      if (k >= 0) cnt[k + 1]++;
+      if (k >= 0 && col_of[k] >= 0) cnt[col_of[k] + 1]++;
     }
   }
-  for (int64_t k = 0; k < nv; ++k) cnt[k + 1] += cnt[k];
+  for (int64_t k = 0; k < ncol; ++k) cnt[k + 1] += cnt[k];
   nk.ptr = cnt;
-  nk.row.assign(cnt[nv], 0);
-  nk.sgn.assign(cnt[nv], 0);
+  nk.row.assign(cnt[ncol], 0);
+  nk.sgn.assign(cnt[ncol], 0);
   std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
   for (int64_t r = 0; r < n; ++r) {  // rows visited in ascending order
     const int32_t e = t.dof_edge[r];
     for (int s = 0; s < 2; ++s) {
       const int32_t k = t.vert_dof[t.edges[2 * e + s]];
-      if (k < 0) continue;
-      nk.row[fill[k]] = (int32_t)r;
-      nk.sgn[fill[k]] = s ? 1 : -1;  // head +1, tail -1
-      ++fill[k];
+      if (k < 0 || col_of[k] < 0) continue;
+      const int32_t q = col_of[k];
+      nk.row[fill[q]] = (int32_t)r;
+      nk.sgn[fill[q]] = s ? 1 : -1;  // head +1, tail -1
+      ++fill[q];
     }
   }
-  nk.sub.assign(nv, -1);
-  nk.vert.assign(t.dof_vert.begin(), t.dof_vert.end());
+  nk.sub.assign(ncol, -1);
+  nk.vert.assign(kv.begin(), kv.end());
 }
 
 void build_snk(const Topology &t, const Decomposition &d, SNKColumns &snk) {

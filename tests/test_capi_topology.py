@@ -149,18 +149,27 @@ def test_compute_calls_refused(pkg):
     s.close()
 
 
-@pytest.mark.parametrize("name", ["hetero_hole", "beam_holes_natural", "cube8"])
+@pytest.mark.parametrize("name", ["hetero_hole", "beam_holes_natural", "cube8", "all_natural"])
 def test_global_near_kernel_columns(pkg, name):
     """coarse = NK (Sec. 4, AS-NK): one gradient column per interior vertex,
-    equal to the oracle's nk_columns (rows and signs)."""
+    minus the highest vertex of each component with no Dirichlet vertex,
+    equal to the oracle's nk_columns (rows and signs).  On the all-natural
+    box (one floating component) exactly one column is dropped, and the kept
+    columns have full rank: the incidence matrix of a connected graph has
+    rank (vertices - 1), so G minus any one column is injective."""
     from oracle.mesh import build_mesh
-    from oracle.coarse import nk_columns
+    from oracle.coarse import nk_columns, assemble_Z
     w = CASES[name]()
     s = pkg.Solver.topology(w, coarse=pkg.COARSE_NK)
     m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active,
                    natural=getattr(w, "natural", None))
     ref = nk_columns(m)
-    assert s.sizes["n0_snk"] == len(ref) == m.nvdofs
+    floating = 1 if name == "all_natural" else 0
+    assert s.sizes["n0_snk"] == len(ref) == m.nvdofs - floating
+    if floating:
+        Z = assemble_Z(m.ndofs, ref).toarray()
+        assert np.linalg.matrix_rank(Z) == Z.shape[1]
+        assert ref[-1][1] < m.dof_vert.max()  # the highest vertex is the one dropped
     zp, zr, zv = s.export("Zcol_ptr"), s.export("Zcol_row"), s.export("Zcol_val")
     assert np.array_equal(s.export("snk_vert"), np.array([c[1] for c in ref], np.int32))
     for k, (_, _, rows, vals) in enumerate(ref):

@@ -367,3 +367,37 @@ def test_classical_pencil_has_too_many_large_eigenvalues():
     assert n_classical > 50
     # they are gradient-driven, far above tau (order 1/gamma)
     assert classical[classical > tp].min() > 100 * tp
+
+
+def test_curl_route_against_assembled_product_at_small_gamma():
+    """Where the two Galerkin routes differ.  For the global gradients G the
+    curl-curl part vanishes exactly (K G = 0, Sec. 1: the gradients span the
+    kernel of the discrete curl-curl operator), so the exact coarse matrix is
+    E = gamma G^T M G.  The assembled product G^T (A G) carries the rounding
+    of K G, about u |K|, which relative to gamma |M| grows as 1/gamma; the
+    curl route (C G)^T (C G) + gamma G^T M G carries only (u |C|)^2.
+    Measured here under a 1e3 contrast of mu^-1: the assembled route loses
+    digits in proportion to 1/gamma and turns indefinite at gamma = 1e-12,
+    the curl route stays at the rounding level of G^T M G."""
+    from oracle.fem import assemble_mass
+    from oracle.coarse import galerkin
+    errs = []
+    for g in (1e-2, 1e-6, 1e-10, 1e-12):
+        rng = np.random.default_rng(1)
+        w = small(n=(6, 5, 4), gamma=g, mu=10.0 ** rng.uniform(0, 3, 120))
+        m, A, AT, dec = setup(w)
+        G = gradient_dofs(m)
+        Eref = (w.gamma * (G.T @ (assemble_mass(m, w) @ G))).toarray()
+        Ec = galerkin(m, w, G)
+        Ec = Ec.toarray() if sp.issparse(Ec) else np.asarray(Ec)
+        Ea = (G.T @ (A @ G)).toarray()
+        nr = np.abs(Eref).max()
+        e_curl, e_asm = np.abs(Ec - Eref).max() / nr, np.abs(Ea - Eref).max() / nr
+        assert e_curl <= 1e-14
+        errs.append(e_asm)
+        if g == 1e-12:
+            assert np.linalg.eigvalsh(0.5 * (Ea + Ea.T))[0] < 0 < np.linalg.eigvalsh(Ec)[0]
+    # the assembled route's error grows at least like 1/gamma (factor 1e4 per
+    # 1e-4 of gamma, less a margin of 10)
+    assert errs[1] > 1e3 * errs[0] and errs[2] > 1e3 * errs[1]
+    assert errs[2] > 1e-3 and errs[3] > 1.0

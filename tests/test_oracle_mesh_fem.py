@@ -217,3 +217,50 @@ def test_compose_is_block_diagonal():
         assert np.abs(pc.b[0][lo:lo + n] - prob.b[0]).max() <= 1e-14 * np.abs(prob.b[0]).max()
         lo += n
     assert lo == A.shape[0]
+
+
+def test_snk_dimension_under_boolean_pou_on_paper_beam():
+    """The split near-kernel dimension on the N = 8 beam of Table
+    "homogeneous_beam_both" under this oracle's partition of unity.
+
+    The paper's "SNK size" row (25K) counts every vertex of every overlapping
+    subdomain, 24,854 (pinned above): a D_i that is nonzero on all of
+    Omega_i.  Sec. 2, eq. "PoU", fixes only sum_i R_i^T D_i R_i = I and
+    D_i >= 0; this oracle takes the Boolean owner PoU, so column (i, v) is
+    g_v restricted to the edges subdomain i owns.  The owned edge sets are
+    disjoint, so the span of Z_G is the direct sum over i of range(G[O_i, :]),
+    whose dimension is (interior vertices touched by O_i) minus (connected
+    components of the O_i edge graph that touch no Dirichlet vertex): the
+    rank of a graph's incidence matrix.  That count is taken here with
+    scipy's connected_components, independently of the oracle's
+    union-find, and it equals the oracle's column count: 15,750.  The
+    paper-equivalent count after eliminating Dirichlet vertices, the
+    interior vertices of every Omega_i, is printed beside it."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    from oracle.coarse import snk_columns
+    m = build_mesh(64, 16, 16, 1 / 16, np.ones(64 * 256, np.uint8))
+    dec = decompose(m, (8, 1, 1), 1)
+    cols = snk_columns(m, dec)
+    nv = m.nverts
+    interior = m.vert_dof >= 0
+    dim = 0
+    for i in range(dec.nsub):
+        own = dec.N[i][dec.D[i] > 0]
+        e = m.edges[m.dof_edge[own]]
+        touched = np.unique(e[interior[e]])
+        both = interior[e[:, 0]] & interior[e[:, 1]]
+        g = sp.coo_matrix((np.ones(both.sum()), (e[both, 0], e[both, 1])), shape=(nv, nv))
+        ncomp, lab = connected_components(g, directed=False)
+        anchored = np.zeros(ncomp, bool)
+        one = interior[e[:, 0]] ^ interior[e[:, 1]]
+        anchored[lab[np.where(interior[e[one, 0]], e[one, 0], e[one, 1])]] = True
+        floating = len(np.setdiff1d(np.unique(lab[touched]), np.nonzero(anchored)[0]))
+        dim += len(touched) - floating
+    assert len(cols) == dim == 15750
+    # the paper's D_i-nonzero-on-Omega_i count without the eliminated vertices
+    per_sub = [np.unique(m.tets[dec.sub_tets[i]]) for i in range(dec.nsub)]
+    full_interior = sum(int(interior[v].sum()) for v in per_sub)
+    print(f"SNK: Boolean PoU {len(cols)}, interior vertices of all Omega_i {full_interior}, "
+          f"all vertices of all Omega_i {sum(len(v) for v in per_sub)} (paper: 25K)")
+    assert full_interior > len(cols)

@@ -68,6 +68,36 @@ def test_noalloc_symv_matches_local_solve_twice():
     s.close()
 
 
+def test_noalloc_symv_at_the_size_limit_matches_numpy():
+    """dim = 4096, the largest size the fixed scratch array holds (64 tiles
+    per side, every column-partial slot used), on a random symmetric matrix,
+    two calls in a row.  Reference: NumPy's float64 product T @ x on the
+    host.  Both sums have at most dim terms, so each side is within
+    dim * u * (|T| |x|) of the exact product (the standard bound for a dot
+    product in floating point); the test allows 64 dim u (|T| |x|)."""
+    import paper_2311_18783_gb300 as pkg
+    lib = pkg.load_library()
+    rng = np.random.default_rng(33)
+    dim = 4096
+    T = rng.standard_normal((dim, dim))
+    T = 0.5 * (T + T.T)
+    tiles = torch.as_tensor(pack(T), device="cuda")
+    stream = torch.cuda.current_stream()
+    for trial in range(2):
+        x = rng.standard_normal(dim)
+        xd = torch.as_tensor(x, device="cuda")
+        y = torch.full_like(xd, np.nan)
+        rc = lib.geneo_symv_packed_noalloc(ctypes.c_void_p(tiles.data_ptr()), dim,
+                                           ctypes.c_void_p(xd.data_ptr()),
+                                           ctypes.c_void_p(y.data_ptr()),
+                                           ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        ref = T @ x
+        bound = 64 * dim * U * (np.abs(T) @ np.abs(x))
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= bound)
+
+
 def test_noalloc_rejects_sizes_beyond_the_limit():
     import paper_2311_18783_gb300 as pkg
     lib = pkg.load_library()
@@ -75,3 +105,19 @@ def test_noalloc_rejects_sizes_beyond_the_limit():
     p = ctypes.c_void_p(x.data_ptr())
     assert lib.geneo_symv_packed_noalloc(p, 4097, p, p, None) == -1
     assert lib.geneo_symv_packed_noalloc(p, 0, p, p, None) == -1
+
+
+def test_noalloc_rejects_misaligned_tiles():
+    """The tiles are read by bulk copies from 16-byte aligned addresses
+    only: a pointer 8 bytes past an aligned one is refused with INVALID_ARG
+    before any launch."""
+    import paper_2311_18783_gb300 as pkg
+    lib = pkg.load_library()
+    t = torch.zeros(2 * 4096 + 2, dtype=torch.float64, device="cuda")
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    y = torch.zeros(64, dtype=torch.float64, device="cuda")
+    assert t.data_ptr() % 16 == 0
+    rc = lib.geneo_symv_packed_noalloc(ctypes.c_void_p(t.data_ptr() + 8), 64,
+                                       ctypes.c_void_p(x.data_ptr()),
+                                       ctypes.c_void_p(y.data_ptr()), None)
+    assert rc == -1
