@@ -348,7 +348,8 @@ int geneo_export(const geneo_ctx *ctx, const char *name, void *dst, int64_t capa
  * y_dev[dim] = T x_dev for one symmetric matrix T given in the tile-packed
  * layout used for the local factors: nt = ceil(dim/64) tiles per side, tile
  * (I, J), J <= I, a full 64x64 row-major block at element offset
- * (I(I+1)/2 + J) * 4096 of tiles_dev (float64, device, 16-byte aligned);
+ * (I(I+1)/2 + J) * 4096 of tiles_dev (float64, device, 16-byte aligned;
+ * x_dev and y_dev 8-byte aligned);
  * diagonal tiles hold both triangles; entries past dim must be finite
  * (zero).  1 <= dim <= 4096.
  *
@@ -358,8 +359,11 @@ int geneo_export(const geneo_ctx *ctx, const char *name, void *dst, int64_t capa
  * the kernel's shared-memory limit, so it must come before any stream
  * capture.  All calls share the array and later calls overwrite it: calls
  * that overlap on the GPU (other threads, other streams) race.  The call
- * waits for `stream` before returning.  Errors: INVALID_ARG (null pointer or
- * dim outside [1, 4096]), TIMEOUT (a bounded device wait gave up), CUDA. */
+ * waits for `stream` before returning.  Errors: INVALID_ARG (null or
+ * misaligned pointer, dim outside [1, 4096]), TIMEOUT (a bounded device wait
+ * gave up and the copies in flight were drained), CUDA (a CUDA call failed,
+ * or a drain wait gave up as well: a copy may still have been writing shared
+ * memory when the kernel exited, so treat the CUDA context as lost). */
 int geneo_symv_packed_noalloc(const double *tiles_dev, int32_t dim, const double *x_dev,
                               double *y_dev, void *stream);
 

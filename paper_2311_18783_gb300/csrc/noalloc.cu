@@ -29,6 +29,7 @@ constexpr int kNaStages = 4;
 constexpr int64_t kNaColOff = kNaMaxDim;
 constexpr int64_t kNaErrOff = kNaColOff + (int64_t)kNaMaxTiles * kTile;
 constexpr int64_t kNaScratch = kNaErrOff + 1;
+constexpr int kNaDrainLost = 0x7fff;  // error word: a drain wait gave up too
 
 static __device__ __align__(256) double g_noalloc_scratch[kNaScratch];
 
@@ -146,9 +147,14 @@ __global__ void __launch_bounds__(256, 1)
       if (l == 0) rowpart[I * kTile + w * 8 + r] = v;
     }
   }
+  // drain the copies still in flight before the CTA leaves; a drain wait
+  // that gives up as well is recorded separately: a copy may then still land
+  // in this CTA's shared memory after it exits, so the host reports the
+  // context as lost (GENEO_ERR_CUDA) instead of a recoverable timeout
   if (failed && tid == 0)
     while (consumed < issued) {
-      na_wait(&bar[consumed % kNaStages], (uint32_t)((consumed / kNaStages) & 1));
+      if (!na_wait(&bar[consumed % kNaStages], (uint32_t)((consumed / kNaStages) & 1)))
+        atomicExch(err, kNaDrainLost);
       ++consumed;
     }
 }
@@ -173,6 +179,10 @@ extern "C" int geneo_symv_packed_noalloc(const double *tiles, int32_t dim, const
   using namespace geneo;
   if (!tiles || !x || !y) return GENEO_ERR_INVALID_ARG;
   if (dim < 1 || dim > kNaMaxDim) return GENEO_ERR_INVALID_ARG;
+  // cp.async.bulk reads the tiles from 16-byte aligned addresses only; x and
+  // y are read and written as float64
+  if (((uintptr_t)tiles & 15) != 0 || ((uintptr_t)x & 7) != 0 || ((uintptr_t)y & 7) != 0)
+    return GENEO_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GENEO_ERR_CUDA;
   const size_t smem = (size_t)kNaStages * kTileElems * 8 + kNaStages * 8 + 8 * kTile * 8;
@@ -210,5 +220,6 @@ extern "C" int geneo_symv_packed_noalloc(const double *tiles, int32_t dim, const
   if (cudaStreamSynchronize(s) != cudaSuccess) return GENEO_ERR_CUDA;
   if (cudaMemcpy(&e, scratch + kNaErrOff, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return GENEO_ERR_CUDA;
+  if (e == kNaDrainLost) return GENEO_ERR_CUDA;
   return e ? GENEO_ERR_TIMEOUT : GENEO_OK;
 }
