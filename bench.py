@@ -6,9 +6,13 @@ removed), mu^-1 log-uniform in [1, 1e3] inside four random 2x2 channels,
 eps = 1, gamma = 1e-4, f uniform in [-1, 1]^3 per edge (seeded), 4x4x4 = 64
 subdomains, overlap 2, GenEO threshold lambda > 10 (tau = 0.1, reciprocal).
 
-A step is one preconditioned CG solve to ||r|| / ||b|| <= 1e-8 from x0 = 0
-on the GPU, the right-hand side resident in HBM (the local factors, 10-22 GB,
-exceed the 129 MB L2, so no flush is needed).  Set-up (assembly, local
+A step is one preconditioned CG solve to ||r|| / ||b|| <= 1e-8 on the GPU in
+the balanced form (x0 = Z E^-1 Z^T b, one coarse solve per iteration), the
+right-hand side resident in HBM (the local factors, 10-22 GB, exceed the
+129 MB L2, so no flush is needed).  The literal form (x0 = 0, two coarse
+solves per iteration), plain float64 local factors and the refined solves
+(accurate residuals) are timed beside it, and every solution is compared
+with the oracle's stored accurate solution.  Set-up (assembly, local
 inverses, GenEO eigensolves, coarse factor) is timed separately.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -145,14 +149,28 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle, bounded sample (baseline only)
 
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 class OracleSample:
     """One preconditioned CG iteration of the CPU oracle on the same
-    workload, with the local solves measured on `nsample` of the 64
-    subdomains and scaled to all of them, the coarse solve on the split
-    near-kernel columns (the GenEO columns add about 1% to n0), the global
-    SpMVs and the vector updates.  Set-up happens once in the constructor."""
+    workload: the local sparse-LU solves of all 64 subdomains, the coarse
+    solves on the split near-kernel columns (the GenEO columns add under 1%
+    to n0; the oracle's dense GenEO eigensolves take about an hour, so they
+    are left out of this baseline's set-up), the global SpMVs and the vector
+    updates.  Set-up happens once in the constructor."""
 
-    def __init__(self, nsample=4, seed=0):
+    def __init__(self, seed=0):
         import numpy as np
         import scipy.sparse as sp
         import scipy.sparse.linalg as spla
@@ -165,19 +183,18 @@ class OracleSample:
         m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
         self.A = assemble_A(m, w)
         dec = decompose(m, w.parts, w.overlap)
-        self.nsub, self.nsample = dec.nsub, nsample
+        self.nsub = dec.nsub
         self.Z = assemble_Z(self.A.shape[0], snk_columns(m, dec))
         self.Elu = spla.splu(sp.csc_matrix(coarse_matrix(m, w, self.Z)))
-        rng = np.random.default_rng(seed)
-        pick = sorted(rng.choice(dec.nsub, size=nsample, replace=False).tolist())
         self.facs = [(dec.N[i], spla.splu(sp.csc_matrix(self.A[dec.N[i]][:, dec.N[i]])))
-                     for i in pick]
+                     for i in range(dec.nsub)]
+        rng = np.random.default_rng(seed)
         self.r = rng.standard_normal(self.A.shape[0])
         self.info = {"sample": f"one PCG iteration of the oracle on {WORKLOAD} "
-                               f"(n={self.A.shape[0]}), local sparse-LU solves timed on "
-                               f"{nsample} of {dec.nsub} subdomains and scaled, coarse sparse-LU "
-                               f"solves on the {self.Z.shape[1]} split near-kernel columns",
-                     "cores": os.cpu_count()}
+                               f"(n={self.A.shape[0]}): local sparse-LU solves of all "
+                               f"{dec.nsub} subdomains, coarse sparse-LU solves on the "
+                               f"{self.Z.shape[1]} split near-kernel columns",
+                     "cores": os.cpu_count(), "cpu": cpu_model()}
 
     def step(self):
         import numpy as np
@@ -185,18 +202,15 @@ class OracleSample:
         t0 = time.perf_counter()
         y0 = Z @ Elu.solve(Z.T @ r)
         s = r - A @ y0
-        tl = time.perf_counter()
         wv = np.zeros_like(r)
         for Ni, f in self.facs:
             wv[Ni] += f.solve(s[Ni])
-        t_loc = (time.perf_counter() - tl) * self.nsub / self.nsample
-        tc = time.perf_counter()
         z = y0 + wv - Z @ Elu.solve(Z.T @ (A @ wv))
         q = A @ z
         alpha = (r @ z) / (z @ q)
         rr = r - alpha * q
         _ = rr @ rr
-        return (tl - t0) + t_loc + (time.perf_counter() - tc)
+        return time.perf_counter() - t0
 
 
 def oracle_iterations(default):
@@ -225,7 +239,9 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "tol": TOL, "iterations": iters,
                        "iterations_source": src},
             "cpu_baseline": {"value": value, "unit": "s", "cores": info["cores"],
-                             "kind": "oracle", "sample": info["sample"]},
+                             "cpu": info["cpu"], "kind": "oracle",
+                             "sample": info["sample"] + f"; per-iteration median x {iters} "
+                                       f"iterations ({src})"},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -419,6 +435,20 @@ def run_warm(args):
     net.close()
 
 
+def load_oracle_solution(workload, n):
+    """The oracle's accurate solution of the benchmark workload, stored by
+    tests/golden/make_cube32_solution.py (a file read, no oracle code run),
+    or None."""
+    if workload != WORKLOAD:
+        return None
+    path = os.path.join(ROOT, "tests", "golden", "cube32_solution.npy")
+    if not os.path.exists(path):
+        return None
+    import numpy as np
+    x = np.load(path)
+    return x if x.shape == (n,) else None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -444,64 +474,93 @@ def main():
     w = getattr(W, args.workload)()
     prec = pkg.PREC_FP32 if args.precision == "mixed" else pkg.PREC_FP64
     t0 = time.perf_counter()
-    s = pkg.Solver.from_workload(w, precision=prec)
+    s = pkg.Solver.from_workload(w, precision=prec, balanced=1)
     setup_s = time.perf_counter() - t0
     n = s.n
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     s.assemble_rhs(w.f_slot[0], b)
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
-    fp64_side = None
-    if prec == pkg.PREC_FP32:
-        # plain float64 factors on the same GPU, same problem (reported beside)
-        s.use_precision(pkg.PREC_FP64)
-        for _ in range(args.warmup):
+    xo = load_oracle_solution(args.workload, n)
+
+    def err_vs_oracle(v):
+        if xo is None:
+            return None
+        return float(np.linalg.norm(v.cpu().numpy() - xo) / np.linalg.norm(xo))
+
+    def timed_variant(p, bal, steps, warmup, prof=False):
+        """Mean device time of `steps` PCG solves to TOL with local factors p
+        in the balanced (bal) or literal form, after `warmup` untimed ones."""
+        s.use_precision(p)
+        s.use_balanced(bal)
+        for _ in range(warmup):
             s.solve(b, x, tol=TOL, maxit=1000)
         torch.cuda.synchronize()
-        s.profile(True)
-        s.profile_read()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            i64 = s.solve(b, x, tol=TOL, maxit=1000)
-        f1.record(stream)
+        if prof:
+            s.profile(True)
+            s.profile_read()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = []
+        for _ in range(steps):
+            info = s.solve(b, x, tol=TOL, maxit=1000)
+            its.append(info["iters"])
+        e1.record(stream)
         torch.cuda.synchronize()
-        p64 = s.profile_read()
-        s.profile(False)
+        out = {"value": e0.elapsed_time(e1) / steps / 1e3, "unit": "s", "pcg_iters": its[-1],
+               "err_vs_oracle_fp64": err_vs_oracle(x)}
+        pr = None
+        if prof:
+            pr = s.profile_read()
+            s.profile(False)
+        return out, its, pr
+
+    def timed_refined(p, nref=2):
+        s.use_precision(p)
+        s.use_balanced(True)
+        xr = torch.zeros_like(b)
+        s.solve_refined(b, xr, tol=TOL, maxit=1000, nref=nref)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = s.solve_refined(b, xr, tol=TOL, maxit=1000, nref=nref)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"value": e0.elapsed_time(e1) / 1e3, "unit": "s", "nref": nref,
+                "pcg_iters_total": info["iters"], "accurate_relres": info["relres"],
+                "err_vs_oracle_fp64": err_vs_oracle(xr)}
+
+    side = max(1, min(args.steps, 5))
+    variants = {}
+    fp64_side = None
+    if prec == pkg.PREC_FP32:
+        # plain float64 factors on the same GPU, same problem and form
+        v64, _, p64 = timed_variant(pkg.PREC_FP64, True, side, max(1, min(args.warmup, 2)), True)
         l64 = p64["local_symv_ms"] / max(1, p64["local_symv_launches"]) * 1e-3
-        fp64_side = {"value": f0.elapsed_time(f1) / args.steps / 1e3, "unit": "s",
-                     "pcg_iters": i64["iters"],
-                     "local_symv_tflops": p64["local_symv_flops"] / l64 / 1e12,
-                     "local_symv_frac_of_fp64_peak": p64["local_symv_flops"] / l64 / 1e9 /
-                     FP64_PEAK_GFLOPS}
-        s.use_precision(pkg.PREC_FP32)
+        v64["local_symv_tflops"] = p64["local_symv_flops"] / l64 / 1e12
+        v64["local_symv_frac_of_fp64_peak"] = p64["local_symv_flops"] / l64 / 1e9 / FP64_PEAK_GFLOPS
+        fp64_side = v64
+        variants["fp64_literal"], _, _ = timed_variant(pkg.PREC_FP64, False, side, 1)
+        variants["mixed_literal"], _, _ = timed_variant(pkg.PREC_FP32, False, side, 1)
+    # headline: balanced form with the precision asked for, clocks sampled
+    s.use_precision(prec)
+    s.use_balanced(True)
     for _ in range(args.warmup):
-        info = s.solve(b, x, tol=TOL, maxit=1000)
+        s.solve(b, x, tol=TOL, maxit=1000)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    s.profile(True)
-    s.profile_read()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
-    e0.record(stream)
-    iters = []
-    for _ in range(args.steps):
-        info = s.solve(b, x, tol=TOL, maxit=1000)
-        iters.append(info["iters"])
-    e1.record(stream)
+    head, iters, prof = timed_variant(prec, True, args.steps, 0, True)
     torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    prof = s.profile_read()
-    s.profile(False)
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    ms = max_over_ranks(head["value"] * 1e3, world, "cuda")
     clk = clocks.stop()
     # end to end through the host-buffer entry point (copies inside)
     bh = b.cpu().pin_memory()
@@ -514,6 +573,11 @@ def main():
         s.solve_host(bh, tol=TOL, maxit=1000, out=xh)
         te.append(time.perf_counter() - t1)
     e2e_s = statistics.mean(te)
+    refined = {}
+    if prec == pkg.PREC_FP32:
+        refined["mixed"] = timed_refined(pkg.PREC_FP32)
+    refined["fp64"] = timed_refined(pkg.PREC_FP64)
+    s.use_precision(prec)
     # roofline of the dominant kernel: the local-factor SYMV
     peaks, peak_src = load_peaks()
     launches = max(1, prof["local_symv_launches"])
@@ -544,13 +608,19 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == pkg.PREC_FP64 else "f32+f64",
             "plain_fp64": fp64_side,
+            "err_vs_oracle_fp64": head["err_vs_oracle_fp64"],
+            "variants": variants, "refined": refined,
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "nsub": s.sizes["nsub"],
                        "n0": s.sizes["n0"], "n0_geneo": s.sizes["n0_geneo"], "tol": TOL,
+                       "form": "balanced (x0 = Z E^-1 Z^T b, one coarse solve per iteration)",
                        "coarse_factor_gb": s.sizes["coarse_factor_bytes"] / 1e9,
                        "pcg_iters": iters[-1], "precision": args.precision,
                        "l2": "inputs larger than L2 (local factors "
                              f"{s.sizes['local_factor_bytes'] / 1e9:.1f} GB)",
+                       "oracle_solution": None if xo is None else
+                       "tests/golden/cube32_solution.npy (sparse LU + extended-precision "
+                       "refinement, written by tests/golden/make_cube32_solution.py)",
                        "setup_s": setup_s},
             "applies_per_s": applies_per_s,
             "roofline": roof, "clocks": clk, "gpu_launches": prof["launches"],
@@ -562,8 +632,8 @@ def main():
         per_iter, oinfo = statistics.median([o.step() for _ in range(2)]), o.info
         oit, src = oracle_iterations(iters[-1])
         line["cpu_baseline"] = {"value": per_iter * oit, "unit": "s", "cores": oinfo["cores"],
-                                "kind": "oracle", "sample": oinfo["sample"] + f"; x {oit} "
-                                f"iterations ({src})"}
+                                "cpu": oinfo["cpu"], "kind": "oracle",
+                                "sample": oinfo["sample"] + f"; x {oit} iterations ({src})"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()

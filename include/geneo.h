@@ -135,6 +135,14 @@ typedef struct {
                                 from tau, counts as converged (float64 residuals of such
                                 pencils stall far above lobpcg_tol).  Use with
                                 lobpcg_block = 16.  0: off */
+  int32_t balanced;          /* 1: PCG in the balanced form: start from x0 = Z E^-1 Z^T b, so
+                                Z^T r_k = 0 in exact arithmetic, where the closed form of
+                                M^-1_AS,2 (end of Sec. 3.2) reduces to (I - P0) sum_i R_i^T
+                                A_i^-1 R_i; applied as w + Z E^-1 Z^T (r - A w), one coarse
+                                solve per iteration instead of two (the Z E^-1 Z^T r part,
+                                zero in exact arithmetic, corrects the rounding drift of
+                                Z^T r_k).  0: x0 = 0 and the literal four-step apply.
+                                Switchable later with geneo_use_balanced. */
 } geneo_options;
 
 typedef struct {
@@ -216,6 +224,25 @@ int geneo_apply_preconditioner(geneo_ctx *ctx, const double *r_dev, double *z_de
  * BREAKDOWN. */
 int geneo_solve(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol, int32_t maxit,
                 geneo_solve_info *info, void *stream);
+
+/* geneo_solve followed by nref (0..16) steps of iterative refinement: each
+ * step evaluates r = b - A x as accurately as in twice the working precision
+ * (error-free products and sums, the Dot2 algorithm of Ogita, Rump and
+ * Oishi), solves A d = r with the same PCG and tolerance, and adds d to x.
+ * In float64, b - A x cannot be evaluated below u ||A|| ||x||, and when gamma
+ * is small the gradient part of x (of size 1/gamma, Sec. 1) makes that the
+ * floor of the forward error of every float64 solve; refinement removes it.
+ * b_dev and x_dev must not alias.  info->iters is the PCG iteration count of
+ * all solves, info->relres the accurate ||b - A x|| / ||b|| of the returned
+ * x (bounded below by the rounding of x itself to float64).  Returns OK,
+ * NOT_CONVERGED (some solve reached maxit) or BREAKDOWN. */
+int geneo_solve_refined(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol,
+                        int32_t maxit, int32_t nref, geneo_solve_info *info, void *stream);
+
+/* on = 1 / 0: later PCG solves of the context use the balanced form / the
+ * literal form (see geneo_options.balanced).  geneo_apply_preconditioner
+ * always applies the literal M^-1_AS,2. */
+int geneo_use_balanced(geneo_ctx *ctx, int32_t on);
 
 /* Same solve with host buffers: copies b_host[n] to the device, solves, and
  * copies x back to x_host[n] before returning. */

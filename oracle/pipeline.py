@@ -66,5 +66,11 @@ def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
     return OracleProblem(w, mesh, A, AT, b, dec, cols, gcols, gevps, Z, M, tp)
 
 
-def solve(prob, tol=1e-8, maxit=1000, rhs=0):
-    return pcg(prob.A, prob.b[rhs], prob.M.apply, tol=tol, maxit=maxit)
+def solve(prob, tol=1e-8, maxit=1000, rhs=0, balanced=False):
+    """PCG with M^-1_AS,2; balanced=True starts from x0 = Z E^-1 Z^T b and
+    applies the one-coarse-solve form (TwoLevel.apply_balanced)."""
+    b = prob.b[rhs]
+    if balanced and prob.M.Z is not None:
+        return pcg(prob.A, b, prob.M.apply_balanced, tol=tol, maxit=maxit,
+                   x0=prob.M.balanced_start(b))
+    return pcg(prob.A, b, prob.M.apply, tol=tol, maxit=maxit)

@@ -48,6 +48,30 @@ class TwoLevel:
         w = self.local(s)
         return y0 + w - self.coarse(self.A @ w)
 
+    # Balanced form (one coarse solve per apply).  If Z^T r = 0, the closed
+    # form of M^-1_AS,2 (end of Sec. 3.2) loses its first term, Z E^-1 Z^T r,
+    # and (I - P0^T) r = r - A Z E^-1 Z^T r = r, leaving (I - P0) M_loc r.
+    # PCG started from x0 = Z E^-1 Z^T b has Z^T r_0 = Z^T b - E E^-1 Z^T b
+    # = 0, and every later search direction lies in range(I - P0), on which
+    # Z^T A vanishes (Z^T A (I - P0) = Z^T A - E E^-1 Z^T A = 0), so
+    # Z^T r_k = 0 for every k in exact arithmetic.  In floating point Z^T r_k
+    # drifts, and (I - P0) M_loc alone never corrects that drift (its
+    # iterates stall above tight tolerances), so the apply adds back
+    # Z E^-1 Z^T r, which is zero in exact arithmetic:
+    #   z = w - Z E^-1 Z^T A w + Z E^-1 Z^T r = w + Z E^-1 Z^T (r - A w),
+    # one coarse solve per apply (the "A-DEF2" two-level form of Tang,
+    # Nabben, Vuik and Erlangga, J. Sci. Comput. 39, 2009).
+
+    def balanced_start(self, b):
+        """x0 = Z E^-1 Z^T b."""
+        return self.coarse(b)
+
+    def apply_balanced(self, r):
+        """w + Z E^-1 Z^T (r - A w) with w = sum_i R_i^T A_i^-1 R_i r; equal
+        to apply(r) when Z^T r = 0."""
+        w = self.local(r)
+        return w + self.coarse(r - self.A @ w)
+
 
 def factor_dense(E):
     """Dense Cholesky (library primitive); returns the solve."""
@@ -91,17 +115,18 @@ class PCGResult:
     history: list
 
 
-def pcg(A, b, Minv, tol=1e-8, maxit=1000):
-    """Preconditioned CG from x0 = 0."""
-    x = np.zeros_like(b)
-    r = b.copy()
+def pcg(A, b, Minv, tol=1e-8, maxit=1000, x0=None):
+    """Preconditioned CG from x0 (default 0); the stopping test is
+    ||r_k|| <= tol ||b|| on the recurrence residual."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b.copy() if x0 is None else b - A @ x
     nb = np.linalg.norm(b)
     if nb == 0.0:
-        return PCGResult(x, 0, 0.0, [0.0])
+        return PCGResult(np.zeros_like(b), 0, 0.0, [0.0])
     z = Minv(r)
     p = z.copy()
     rz = r @ z
-    hist = [1.0]
+    hist = [np.linalg.norm(r) / nb]
     for k in range(1, maxit + 1):
         q = A @ p
         alpha = rz / (p @ q)
@@ -121,3 +146,35 @@ def pcg(A, b, Minv, tol=1e-8, maxit=1000):
 
 def direct_solve(A, b):
     return spla.spsolve(sp.csc_matrix(A), b)
+
+
+def residual_extended(A, b, x):
+    """b - A x with every product and sum in numpy.longdouble (64-bit or
+    113-bit significand, against float64's 53), returned in longdouble."""
+    A = sp.csr_matrix(A)
+    ld = np.longdouble
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    acc = np.zeros(A.shape[0], dtype=ld)
+    np.add.at(acc, rows, A.data.astype(ld) * np.asarray(x, dtype=ld)[A.indices])
+    return np.asarray(b, dtype=ld) - acc
+
+
+def refined_direct_solve(A, b, steps=3):
+    """x = A^-1 b by a sparse LU (library primitive; symmetric mode, minimum
+    degree ordering on A + A^T) followed by `steps` rounds of classical
+    iterative refinement with residuals in extended precision (Wilkinson):
+    x <- x + LU^-1 (b - A x).  The float64 residual of any float64 x is
+    bounded below by about u ||A|| ||x||, which bounds the forward error of
+    plain float64 solves when A is ill conditioned (small gamma, Sec. 1);
+    the extended residual removes that floor.  Returns (x, relative size of
+    each correction)."""
+    lu = spla.splu(sp.csc_matrix(A), permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                   options=dict(SymmetricMode=True))
+    x = lu.solve(np.asarray(b, dtype=np.float64))
+    hist = []
+    for _ in range(steps):
+        r = residual_extended(A, b, x).astype(np.float64)
+        d = lu.solve(r)
+        x = x + d
+        hist.append(float(np.linalg.norm(d) / max(np.linalg.norm(x), 1e-300)))
+    return x, hist

@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32),
                 ("use_graph", C.c_int32), ("gradient_shift", C.c_int32),
                 ("keep_eigvecs", C.c_int32), ("warm_start", C.c_void_p),
-                ("lobpcg_neumann", C.c_int32)]
+                ("lobpcg_neumann", C.c_int32), ("balanced", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -88,6 +88,9 @@ _SIGS = {
     "geneo_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "geneo_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                               C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                      C.c_int32, C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
+    "geneo_use_balanced": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                    C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_segments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
@@ -378,6 +381,18 @@ class Solver:
                                      _stream(stream)))
         return {"status": st, "iters": info.iters, "relres": info.relres,
                 "seconds": info.seconds}
+
+    def solve_refined(self, b, x, tol=1e-8, maxit=1000, nref=1, stream=None):
+        """PCG plus nref refinement steps with accurate residuals; relres is
+        the accurate ||b - A x|| / ||b|| of the returned x."""
+        info = SolveInfo()
+        st = _check(_LIB.geneo_solve_refined(self._ctx, _ptr(b), _ptr(x), tol, maxit, nref,
+                                             C.byref(info), _stream(stream)))
+        return {"status": st, "iters": info.iters, "relres": info.relres,
+                "seconds": info.seconds}
+
+    def use_balanced(self, on=True):
+        _check(_LIB.geneo_use_balanced(self._ctx, 1 if on else 0))
 
     def apply_preconditioner_block(self, R, Z, stream=None):
         """R, Z: CUDA float64 tensors [nrhs, n] (contiguous)."""

@@ -120,6 +120,8 @@ static int check_setup_args(const geneo_problem *p, const geneo_options *opt, ge
     return fail(GENEO_ERR_INVALID_ARG, "keep_eigvecs must be 0 or 1");
   if (o.lobpcg_neumann != 0 && o.lobpcg_neumann != 1)
     return fail(GENEO_ERR_INVALID_ARG, "lobpcg_neumann must be 0 or 1");
+  if (o.balanced != 0 && o.balanced != 1)
+    return fail(GENEO_ERR_INVALID_ARG, "balanced must be 0 or 1");
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
       (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
@@ -149,6 +151,7 @@ static geneo_ctx *new_context(const geneo_problem *p, const geneo_options &o) {
   if (p->cell_part) c->cell_part.assign(p->cell_part, p->cell_part + nc);
   if (p->natural_faces) c->natural.assign(p->natural_faces, p->natural_faces + nc);
   c->opt = o;
+  c->balanced = o.balanced != 0;
   return c;
 }
 
@@ -271,6 +274,24 @@ int geneo_solve(geneo_ctx *c, const double *b, double *x, double tol, int32_t ma
   if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
   return guarded([&]() { return geneo::pcg(c, b, x, tol, maxit, info, as_stream(s)); });
+}
+
+int geneo_solve_refined(geneo_ctx *c, const double *b, double *x, double tol, int32_t maxit,
+                        int32_t nref, geneo_solve_info *info, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
+  if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
+  if (nref < 0 || nref > 16) return fail(GENEO_ERR_INVALID_ARG, "nref must be in 0..16");
+  if (b == x) return fail(GENEO_ERR_INVALID_ARG, "b and x must not alias");
+  return guarded([&]() { return geneo::pcg_refined(c, b, x, tol, maxit, nref, info, as_stream(s)); });
+}
+
+int geneo_use_balanced(geneo_ctx *c, int32_t on) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (on != 0 && on != 1) return fail(GENEO_ERR_INVALID_ARG, "on must be 0 or 1");
+  c->balanced = on != 0;
+  return GENEO_OK;
 }
 
 int geneo_apply_preconditioner_block(geneo_ctx *c, const double *r, double *z, int32_t nrhs,

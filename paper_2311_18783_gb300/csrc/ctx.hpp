@@ -92,6 +92,7 @@ struct geneo_ctx {
   // local operators (xi, S_j^-1, element data) for GenEO and the split solve
   std::unique_ptr<geneo::XiOp> xi;
   int local_prec = GENEO_PREC_FP64;  // precision used by the local solves
+  bool balanced = false;             // PCG in the balanced (one coarse solve) form
   // warm start of the local eigensolves: edge features [loc.vlen][5]; the
   // locked eigenvectors (first 8 per subdomain, and B times them) when kept
   geneo::DevBuf<float> d_feat;
@@ -104,6 +105,7 @@ struct geneo_ctx {
   geneo::DevBuf<double> v_y0, v_s, v_w, v_t, v_c, loc_x, loc_y, loc_xp, crs_x, crs_y;
   geneo::DevBuf<double> p_r, p_z, p_p, p_q, scal, partials;
   geneo::DevBuf<double> h_b, h_x;  // device copies used by geneo_solve_host
+  geneo::DevBuf<double> ref_r, ref_d;  // refinement: accurate residual and correction
   geneo::DevBuf<int> d_err;
   double *h_scal = nullptr;  // pinned host mirror of the PCG scalars
 

@@ -103,10 +103,18 @@ void tc_symm(geneo_ctx *c, const double *xl, double *yl, int k, cudaStream_t s, 
              cudaEvent_t e1);
 void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k = 1);
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k = 1);
-void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k = 1);
+// y = Z E^-1 Z^T r (+ add, when given)
+void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k = 1,
+                  const double *add = nullptr);
 void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k = 1);
+// one-coarse-solve form for residuals with Z^T r = 0: w + Z E^-1 Z^T (r - A w)
+void apply_balanced(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k = 1);
 int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_solve_info *info,
         cudaStream_t s, int k = 1);
+// PCG followed by nref refinement steps with accurate (twice the working
+// precision) residuals; info->relres is the accurate relative residual
+int pcg_refined(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int nref,
+                geneo_solve_info *info, cudaStream_t s);
 // one PCG per independent component (contiguous unknown ranges), same launches
 int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit,
                  geneo_solve_info *info, cudaStream_t s);

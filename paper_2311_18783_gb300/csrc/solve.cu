@@ -5,6 +5,13 @@
 //   y0 = Z E^-1 Z^T r ;  s = r - A y0 ;  w = sum_i R_i^T A_i^-1 R_i s ;
 //   z  = y0 + w - Z E^-1 Z^T (A w).
 // PCG: A is SPD (Sec. 2) and M^-1_AS,2 symmetric (eq. "AS2").
+//
+// Balanced form (optional): PCG starts from x0 = Z E^-1 Z^T b, so that
+// Z^T r_k = 0 in exact arithmetic, and applies
+//   w = sum_i R_i^T A_i^-1 R_i r ;  z = w + Z E^-1 Z^T (r - A w),
+// the same operator on such residuals with one coarse solve per apply
+// instead of two (the Z E^-1 Z^T r part of the added term corrects the
+// rounding drift of Z^T r_k).
 #include <chrono>
 
 #include "setup.hpp"
@@ -89,17 +96,66 @@ __global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict
   if (l == 0) t[a] = s;
 }
 
-// y[e] = (Z u)_e, one row per thread (CSR)
+// y[e] = (Z u)_e (+ add[e] when add is given), one row per thread (CSR)
 __global__ void k_z(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zcol,
                     const double *__restrict__ zval, const double *__restrict__ u,
-                    double *__restrict__ y, int64_t n, int64_t n0) {
+                    double *__restrict__ y, int64_t n, int64_t n0,
+                    const double *__restrict__ add) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
   u += blockIdx.y * n0;
   y += blockIdx.y * n;
   double s = 0;
   for (int64_t k = zptr[e]; k < zptr[e + 1]; ++k) s = fma(zval[k], u[zcol[k]], s);
-  y[e] = s;
+  y[e] = add ? add[blockIdx.y * n + e] + s : s;
+}
+
+// Error-free transformations for the accurate residual (Dot2 of Ogita, Rump
+// and Oishi, SIAM J. Sci. Comput. 26, 2005): a*b = p + e exactly with
+// p = fl(a*b), e = fma(a, b, -p); a + b = s + t exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &t) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  t = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// y = b - A x as accurately as if computed in twice the working precision,
+// then rounded to float64; 8 lanes per row
+__global__ void k_residual_dd(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              const double *__restrict__ val, const double *__restrict__ x,
+                              const double *__restrict__ b, double *__restrict__ y, int64_t n) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gt >> 3;
+  const int lane = threadIdx.x & 7;
+  double hi = 0, lo = 0;
+  if (row < n)
+    for (int32_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 8) {
+      const double a = val[k], v = x[col[k]];
+      const double p = __dmul_rn(a, v);
+      const double pe = fma(a, v, -p);
+      double t;
+      two_sum(hi, p, hi, t);
+      lo = __dadd_rn(lo, __dadd_rn(t, pe));
+    }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const double ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+    const double olo = __shfl_xor_sync(0xffffffffu, lo, o);
+    double t;
+    two_sum(hi, ohi, hi, t);
+    lo = __dadd_rn(lo, __dadd_rn(olo, t));
+  }
+  if (row < n && lane == 0) {
+    double sres, t;
+    two_sum(b[row], -hi, sres, t);
+    y[row] = __dadd_rn(sres, __dsub_rn(t, lo));
+  }
+}
+
+// x += d
+__global__ void k_axpy1(const double *__restrict__ d, double *__restrict__ x, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
 }
 
 // z = y0 + w - c
@@ -300,10 +356,12 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k
   GENEO_CHECK_LAUNCH();
 }
 
-void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k) {
+void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k,
+                  const double *add) {
   const int64_t n = c->topo.ndofs(), n0 = c->n0;
   if (n0 == 0) {
-    GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n * k, s));
+    if (add) GENEO_CUDA(cudaMemcpyAsync(y, add, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s));
+    else GENEO_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n * k, s));
     return;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -327,7 +385,7 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int 
     symv_batch<double>(c->crs, c->crs_f64.p, c->crs_x.p, c->crs_y.p, c->d_err.p, s, e0, e1);
   }
   k_z<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(c->d_zr_ptr.p, c->d_zr_col.p, c->d_zr_val.p,
-                                                c->crs_y.p, y, n, n0);
+                                                c->crs_y.p, y, n, n0, add);
   GENEO_CHECK_LAUNCH();
 }
 
@@ -348,11 +406,47 @@ void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t
   GENEO_CHECK_LAUNCH();
 }
 
+void apply_balanced(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k) {
+  const int64_t n = c->topo.ndofs();
+  if (c->n0 == 0) {
+    local_solve(c, r, z, s, k);
+    return;
+  }
+  local_solve(c, r, c->v_w.p, s, k);
+  c->launches += 1;
+  k_residual<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
+                                                           c->v_w.p, r, c->v_t.p, n);
+  GENEO_CHECK_LAUNCH();
+  coarse_solve(c, c->v_t.p, z, s, k, c->v_w.p);
+}
+
+// the preconditioner of the PCG iteration: literal or balanced form
+static void precondition(geneo_ctx *c, const double *r, double *z, cudaStream_t s, int k) {
+  if (c->balanced) apply_balanced(c, r, z, s, k);
+  else apply_preconditioner(c, r, z, s, k);
+}
+
+// x0 and r0 = b - A x0: zero and b, or Z E^-1 Z^T b and its residual
+static void pcg_start(geneo_ctx *c, const double *b, double *x, cudaStream_t s, int k) {
+  const int64_t n = c->topo.ndofs();
+  if (c->balanced && c->n0 > 0) {
+    coarse_solve(c, b, x, s, k);
+    c->launches += 1;
+    k_residual<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p,
+                                                             c->d_val.p, x, b, c->p_r.p, n);
+  } else {
+    GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n * k, s));
+    c->launches += 1;
+    k_copy<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(b, c->p_r.p, n);
+  }
+  GENEO_CHECK_LAUNCH();
+}
+
 // second half of a PCG iteration: z = M^-1 r, rz_new = (r, z), p = z + beta p
 static void pcg_precond_half(geneo_ctx *c, cudaStream_t s, int k) {
   const int64_t n = c->topo.ndofs();
   double *sc = c->scal.p;
-  apply_preconditioner(c, c->p_r.p, c->p_z.p, s, k);
+  precondition(c, c->p_r.p, c->p_z.p, s, k);
   dot(c, c->p_r.p, c->p_z.p, n, sc + 3, s, k);
   c->launches += 2;
   k_update_p<<<dim3(grid_for(n, 256), k), 256, 0, s>>>(sc, c->d_act.p, c->p_z.p, c->p_p.p, n);
@@ -379,7 +473,7 @@ static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s, int k) {
 // context's capture stream, with x = p_x; replayed on the caller's stream for
 // every iteration after the first.
 static void ensure_pcg_graph(geneo_ctx *c, int k) {
-  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) << 8) + k;
+  const int key = ((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0))) << 8) + k;
   if (c->pcg_exec && c->pcg_key == key) return;
   c->drop_graph();
   const int64_t l0 = c->launches;
@@ -438,11 +532,10 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
   const dim3 g(grid_for(n, 256), k);
   const bool graph = c->opt.use_graph != 0;
   double *xw = graph ? c->p_x.p : x;  // the graph is built on the context's own x
-  GENEO_CUDA(cudaMemsetAsync(xw, 0, sizeof(double) * n * k, s));
-  c->launches += 2;
-  k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
+  pcg_start(c, b, xw, s, k);
+  c->launches += 1;
   dot(c, b, b, n, sc + 4, s, k);
-  apply_preconditioner(c, c->p_r.p, c->p_z.p, s, k);
+  precondition(c, c->p_r.p, c->p_z.p, s, k);
   k_copy<<<g, 256, 0, s>>>(c->p_z.p, c->p_p.p, n);
   dot(c, c->p_r.p, c->p_z.p, n, sc + 0, s, k);
   GENEO_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * kScal * k, cudaMemcpyDeviceToHost, s));
@@ -593,11 +686,10 @@ int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit
                                cudaMemcpyDeviceToHost, s));
     GENEO_CUDA(cudaStreamSynchronize(s));
   };
-  GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  c->launches += 5;
-  k_copy<<<g, 256, 0, s>>>(b, c->p_r.p, n);
+  pcg_start(c, b, x, s, 1);
+  c->launches += 4;
   k_seg_dot<<<nseg, 256, 0, s>>>(b, b, off, sc + 4);
-  apply_preconditioner(c, c->p_r.p, c->p_z.p, s, 1);
+  precondition(c, c->p_r.p, c->p_z.p, s, 1);
   k_copy<<<g, 256, 0, s>>>(c->p_z.p, c->p_p.p, n);
   k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, off, sc + 0);
   GENEO_CHECK_LAUNCH();
@@ -618,7 +710,7 @@ int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit
                              cudaMemcpyHostToDevice, s));
   for (int it = 1; it <= maxit && nact > 0; ++it) {
     if (it > 1) {
-      apply_preconditioner(c, c->p_r.p, c->p_z.p, s, 1);
+      precondition(c, c->p_r.p, c->p_z.p, s, 1);
       c->launches += 3;
       k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, off, sc + 3);
       k_seg_update_p<<<g, 256, 0, s>>>(sc, c->seg_act.p, seg, c->p_z.p, c->p_p.p, n);
@@ -664,6 +756,59 @@ int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit
     }
     if (st[j] == GENEO_ERR_BREAKDOWN) status = GENEO_ERR_BREAKDOWN;
     else if (st[j] == GENEO_NOT_CONVERGED && status == GENEO_OK) status = GENEO_NOT_CONVERGED;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// Iterative refinement with accurate residuals.  In float64, b - A x cannot
+// be evaluated below u ||A|| ||x|| (the gradient part of x grows like
+// 1/gamma), so PCG iterates stop improving at a forward error far above the
+// recurrence residual.  Each refinement step evaluates r = b - A x with the
+// twice-the-working-precision residual kernel, solves A d = r with the same
+// PCG and adds d to x.
+
+int pcg_refined(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int nref,
+                geneo_solve_info *info, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = c->topo.ndofs();
+  geneo_solve_info one{};
+  int status = pcg(c, b, x, tol, maxit, &one, s);
+  int iters = one.iters;
+  if (c->ref_r.n < n) {
+    c->ref_r.alloc(n);
+    c->ref_d.alloc(n);
+  }
+  for (int q = 0; q < nref && status >= 0; ++q) {
+    c->launches += 1;
+    k_residual_dd<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x,
+                                                       b, c->ref_r.p, n);
+    GENEO_CHECK_LAUNCH();
+    const int st = pcg(c, c->ref_r.p, c->ref_d.p, tol, maxit, &one, s);
+    iters += one.iters;
+    if (st < 0) {
+      status = st;
+      break;
+    }
+    if (st == GENEO_NOT_CONVERGED) status = st;
+    c->launches += 1;
+    k_axpy1<<<grid_for(n, 256), 256, 0, s>>>(c->ref_d.p, x, n);
+    GENEO_CHECK_LAUNCH();
+  }
+  // accurate relative residual of the returned x
+  c->launches += 1;
+  k_residual_dd<<<grid_for(n * 8, 256), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x, b,
+                                                     c->ref_r.p, n);
+  GENEO_CHECK_LAUNCH();
+  dot(c, c->ref_r.p, c->ref_r.p, n, c->scal.p + 5, s);
+  dot(c, b, b, n, c->scal.p + 6, s);
+  double h[2];
+  GENEO_CUDA(cudaMemcpyAsync(h, c->scal.p + 5, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->relres = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return status;
 }

@@ -13,7 +13,17 @@ Checked on the GPU in the set-up the benchmark times:
 * PCG to 1e-8 in float64: the oracle's iteration count +-1;
 * PCG to 1e-8 with float32 split local factors: converged, at most two more
   iterations, and the relative difference from the float64 solution is
-  below 1e-6 (both stop at residual 1e-8; kappa(A) amplifies it).
+  below 1e-6 (both stop at residual 1e-8; kappa(A) amplifies it);
+* the solution, element by element, against the oracle's accurate solution
+  x = A^-1 b stored in tests/golden/cube32_solution.npy
+  (tests/golden/make_cube32_solution.py: sparse LU and refinement with
+  extended residuals, corrections below 1e-10 of x): float64 PCG to 1e-13,
+  float64 and mixed PCG to 1e-8 (literal and balanced forms), and both with
+  two refinement steps on accurate residuals, which must meet 1e-8.  The
+  plain float64 solves cannot: on this system (gamma = 1e-4) the float64
+  residual of a float64 x bottoms out near u ||A|| ||x|| = 5e-7 ||b||, and
+  the oracle's own float64 solves (sparse LU, PCG to 1e-13) are 1.3e-7 and
+  1.4e-7 away from the refined solution.
 """
 import json
 import os
@@ -28,6 +38,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                       "cube32_reference.json")
+SOLUTION = os.path.join(os.path.dirname(GOLDEN), "cube32_solution.npy")
 
 
 @pytest.fixture(scope="module")
@@ -86,3 +97,46 @@ def test_pcg_fp64_and_mixed(full):
     print(f"mixed vs float64 solution: relative difference {d:.3e}, "
           f"iterations {i32['iters']} vs {i64['iters']} (oracle {ref['pcg_iters']})")
     assert d <= 1e-6
+
+
+def test_solution_against_oracle_elementwise(full):
+    pkg, w, ref, s = full
+    xo = np.load(SOLUTION)
+    assert xo.shape == (s.n,)
+    b = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    s.assemble_rhs(w.f_slot[0], b)
+    nxo = np.linalg.norm(xo)
+    out = {}
+
+    def err(x):
+        return float(np.linalg.norm(x.cpu().numpy() - xo) / nxo)
+
+    for prec, name in ((pkg.PREC_FP64, "fp64"), (pkg.PREC_FP32, "mixed")):
+        s.use_precision(prec)
+        for bal in (False, True):
+            s.use_balanced(bal)
+            key = name + ("_balanced" if bal else "")
+            x = torch.zeros_like(b)
+            info = s.solve(b, x, tol=1e-8, maxit=1000)
+            assert info["status"] == 0
+            out[key + "_tol1e-8"] = (err(x), info["iters"])
+            x = torch.zeros_like(b)
+            info = s.solve_refined(b, x, tol=1e-8, maxit=1000, nref=2)
+            assert info["status"] == 0
+            out[key + "_refined2"] = (err(x), info["iters"])
+        s.use_balanced(False)
+    s.use_precision(pkg.PREC_FP64)
+    x = torch.zeros_like(b)
+    info = s.solve(b, x, tol=1e-13, maxit=1000)
+    out["fp64_tol1e-13"] = (err(x), info["iters"])
+    s.use_precision(pkg.PREC_FP32)
+    for k, (e, it) in sorted(out.items()):
+        print(f"{k:28s} relative error vs oracle {e:.3e}  PCG iterations {it}")
+    # the refined solves meet the 1e-8 target in every precision and form
+    for k, (e, it) in out.items():
+        if k.endswith("refined2"):
+            assert e <= 1e-8, (k, e)
+    # the plain float64 solves sit at the float64 floor the oracle shares
+    assert out["fp64_tol1e-13"][0] <= 5e-7
+    assert out["fp64_tol1e-8"][0] <= 1e-6 and out["mixed_tol1e-8"][0] <= 1e-6
+    assert abs(out["fp64_balanced_tol1e-8"][1] - ref["pcg_iters"]) <= 2

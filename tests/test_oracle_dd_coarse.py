@@ -401,3 +401,61 @@ def test_curl_route_against_assembled_product_at_small_gamma():
     # 1e-4 of gamma, less a margin of 10)
     assert errs[1] > 1e3 * errs[0] and errs[2] > 1e3 * errs[1]
     assert errs[2] > 1e-3 and errs[3] > 1.0
+
+
+@pytest.mark.parametrize("case", ["snk_geneo_hole", "paper_tau"])
+def test_balanced_start_one_coarse_solve(case):
+    """Balanced form of M^-1_AS,2 (closed form at the end of Sec. 3.2): for
+    r with Z^T r = 0 the apply w + Z E^-1 Z^T (r - A w) equals the literal
+    four-step apply (the first term and (I - P0^T) drop out); PCG from
+    x0 = Z E^-1 Z^T b then reaches the direct solution with the literal
+    form's iteration count (+-1) and keeps Z^T r small."""
+    if case == "snk_geneo_hole":
+        w = small(n=(6, 6, 4), parts=(2, 2, 2), overlap=1, gamma=1e-4,
+                  holes=[((2, 4), (2, 4), (0, 4))])
+        prob = build_problem(w)
+    else:
+        w = small(n=(6, 5, 4), parts=(2, 2, 1), overlap=1, tau=3.0)
+        prob = build_problem(w, tau_convention="paper")
+        assert len(prob.geneo) > 0
+    A, Z = prob.A, prob.Z
+    rng = np.random.default_rng(4)
+    rt = rng.standard_normal(A.shape[0])
+    # (I - P0^T) r~, so Z^T r = 0 up to the rounding of A Z E^-1 Z^T r~
+    # (gamma = 1e-4 makes the gradient part of Z E^-1 Z^T r~ large)
+    r = rt - A @ prob.M.coarse(rt)
+    assert np.linalg.norm(Z.T @ r) <= 1e-6 * np.linalg.norm(Z.T @ rt)
+    lit, bal = prob.M.apply(r), prob.M.apply_balanced(r)
+    assert np.linalg.norm(bal - lit) <= 1e-6 * np.linalg.norm(lit)
+    x = direct_solve(A, prob.b[0])
+    a = solve(prob, tol=1e-12, maxit=500)
+    b = solve(prob, tol=1e-12, maxit=500, balanced=True)
+    assert b.relres <= 1e-12 and abs(a.iters - b.iters) <= 1
+    ea = np.linalg.norm(a.x - x) / np.linalg.norm(x)
+    eb = np.linalg.norm(b.x - x) / np.linalg.norm(x)
+    assert eb <= 2 * ea + 1e-12
+    rb = prob.b[0] - A @ b.x
+    assert np.linalg.norm(Z.T @ rb) <= 1e-6 * np.linalg.norm(prob.b[0])
+
+
+def test_refined_direct_solve_against_high_precision():
+    """refined_direct_solve against a 50-digit solve of the same float64 A
+    and b (mpmath LU), on a small case made ill conditioned by gamma = 1e-6
+    under a 1e3 contrast of mu^-1 (kappa(A) near 2e11): the plain sparse
+    solve's forward error is near kappa u (5.6e-7 measured), the refined
+    one's near kappa times the extended residual's unit roundoff (2.4e-10
+    measured with a 64-bit significand)."""
+    mpmath = pytest.importorskip("mpmath")
+    from oracle.solver import refined_direct_solve
+    rng = np.random.default_rng(2)
+    w = small(n=(3, 3, 3), parts=(1, 1, 1), gamma=1e-6, mu=10.0 ** rng.uniform(0, 3, 27))
+    m, A, AT, dec = setup(w)
+    b = assemble_rhs(m, w)[0]
+    mpmath.mp.dps = 50
+    xm = mpmath.lu_solve(mpmath.matrix(A.toarray().tolist()), mpmath.matrix(b.tolist()))
+    xe = np.array([float(v) for v in xm])
+    err = lambda x: np.linalg.norm(x - xe) / np.linalg.norm(xe)
+    x1, hist = refined_direct_solve(A, b, steps=3)
+    assert err(direct_solve(A, b)) > 1e-8
+    assert err(x1) <= 1e-8
+    assert hist[-1] <= 1e-8
