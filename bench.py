@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "cube16_hole_channels", BLOCK_WORKLOAD, "beam128_mild",
-                            "beam64_layered", WARM_WORKLOAD],
+                            "beam64_layered", WARM_WORKLOAD, "paper_beam"],
                    help="cube16_hole_channels: the profiling-size companion (ncu captures); "
                         f"{BLOCK_WORKLOAD}: 16 right-hand sides as a block, bfloat16 local "
                         "factors on the tensor cores")
@@ -435,6 +435,65 @@ def run_warm(args):
     net.close()
 
 
+# Table "homogeneous_beam_both" (Sec. 4), N = 8: right-preconditioned GMRES
+# iterations to a relative residual of 1e-6 on the (N/2) x 1 x 1 beam at
+# h = 1/16, tau = 10, and the GenEO size (0 for every N and both BCs)
+PAPER_BEAM_N8 = {"dirichlet": {"AS": 12, "AS-SNK": 14, "AS-SNK-GenEO": 14, "AS-NK": 14,
+                               "AS-NK-GenEO": 14},
+                 "mixed": {"AS": 20, "AS-SNK": 15, "AS-SNK-GenEO": 15, "AS-NK": 19,
+                           "AS-NK-GenEO": 19}}
+
+
+def run_paper_beam(args):
+    """The paper's weak-scaling beam at N = 8 (64 x 16 x 16 cells, h = 1/16,
+    8 boxes, one overlap layer, mu = eps = 1, f = (1, 1, 1), gamma = 1e-3,
+    lambda > 10), Dirichlet on all faces and mixed (Neumann on the two y
+    faces), every coarse variant of Sec. 4 except AMS, solved with
+    right-preconditioned GMRES to 1e-6 as in Table "homogeneous_beam_both";
+    the paper's iteration counts are printed beside ours (context: the
+    paper penalises boundary dofs in FreeFEM, this library eliminates them,
+    and the partitions of unity differ)."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import workloads as W
+    import paper_2311_18783_gb300 as pkg
+    variants = {"AS": dict(coarse=pkg.COARSE_NONE, geneo=0),
+                "AS-SNK": dict(coarse=pkg.COARSE_SNK, geneo=0),
+                "AS-SNK-GenEO": dict(coarse=pkg.COARSE_SNK, geneo=1),
+                "AS-NK": dict(coarse=pkg.COARSE_NK, geneo=0),
+                "AS-NK-GenEO": dict(coarse=pkg.COARSE_NK, geneo=1)}
+    out = {}
+    for bc in ("dirichlet", "mixed"):
+        w = W.paper_beam(8)
+        if bc == "mixed":
+            w.natural = W.natural_faces(w, sides=((1, 0), (1, 1)))
+        out[bc] = {}
+        for name, kw in variants.items():
+            t0 = time.perf_counter()
+            s = pkg.Solver.from_workload(w, **kw)
+            setup = time.perf_counter() - t0
+            b = torch.empty(s.n, dtype=torch.float64, device="cuda")
+            s.assemble_rhs(w.f_slot[0], b)
+            x = torch.zeros_like(b)
+            g = s.solve_gmres(b, x, tol=1e-6, maxit=500, restart=100)
+            x2 = torch.zeros_like(b)
+            c = s.solve(b, x2, tol=1e-6, maxit=500)
+            out[bc][name] = {"gmres_iters": g["iters"], "paper_gmres_iters": PAPER_BEAM_N8[bc][name],
+                             "gmres_relres": g["relres"], "gmres_s": g["seconds"],
+                             "pcg_iters": c["iters"], "n0": s.sizes["n0"],
+                             "n0_geneo": s.sizes["n0_geneo"], "setup_s": setup}
+            out[bc]["dofs_unknown"] = s.n
+            s.close()
+            print(json.dumps({bc: {name: out[bc][name]}}), file=sys.stderr, flush=True)
+    line = {"metric": "GMRES iterations to 1e-6 on the paper's N = 8 beam", "value": None,
+            "unit": "iterations", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "paper_beam_N8", "cells": [64, 16, 16], "h": 1 / 16,
+                       "gamma": 1e-3, "tau_paper": 10, "krylov": "right-preconditioned GMRES(100)",
+                       "paper_table": "homogeneous_beam_both, N = 8"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def load_oracle_solution(workload, n):
     """The oracle's accurate solution of the benchmark workload, stored by
     tests/golden/make_cube32_solution.py (a file read, no oracle code run),
@@ -459,6 +518,9 @@ def main():
         return
     if args.workload == WARM_WORKLOAD:
         run_warm(args)
+        return
+    if args.workload == "paper_beam":
+        run_paper_beam(args)
         return
     import torch
     import torch.distributed as dist

@@ -73,6 +73,15 @@ extern "C" {
 #define GENEO_COARSE_NK 2          /* global near-kernel G: one gradient column per interior
                                       vertex (Sec. 4, variants AS-NK and AS-NK-GenEO) */
 
+#define GENEO_PENCIL_FILTERED 0    /* GEVP "tauthresholdAS", eq. "eigAtildeBAS" (Sec. 3.2):
+                                      (I - xi_0j)^T D_j A_j D_j (I - xi_0j) V = lambda A_j^Neu V,
+                                      coarse vectors R_j^T D_j (I - xi_0j) V */
+#define GENEO_PENCIL_CLASSICAL 1   /* the classical GenEO pencil of the remark in Sec. 3.2,
+                                      eq. "eigGenEOClassis": D_j A_j D_j V = lambda A_j^Neu V,
+                                      coarse vectors R_j^T D_j V; for comparison: it has many
+                                      gradient-driven eigenvalues above the threshold, most of
+                                      them dependent on the split near-kernel columns */
+
 #define GENEO_TAU_RECIPROCAL 0     /* select lambda > 1/tau */
 #define GENEO_TAU_PAPER 1          /* select lambda > tau (GEVP "tauthresholdAS" literally) */
 
@@ -143,6 +152,7 @@ typedef struct {
                                 zero in exact arithmetic, corrects the rounding drift of
                                 Z^T r_k).  0: x0 = 0 and the literal four-step apply.
                                 Switchable later with geneo_use_balanced. */
+  int32_t geneo_pencil;      /* GENEO_PENCIL_FILTERED (default) or GENEO_PENCIL_CLASSICAL */
 } geneo_options;
 
 typedef struct {
@@ -238,6 +248,19 @@ int geneo_solve(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol, 
  * NOT_CONVERGED (some solve reached maxit) or BREAKDOWN. */
 int geneo_solve_refined(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol,
                         int32_t maxit, int32_t nref, geneo_solve_info *info, void *stream);
+
+/* Right-preconditioned restarted GMRES(restart) on A x = b from x = 0 with
+ * M^-1_AS,2, the Krylov method of the paper's experiments (Sec. 4: right
+ * preconditioning minimises ||b - A x|| itself, whatever the preconditioner);
+ * stops when ||b - A x|| <= tol ||b|| (the Arnoldi estimate, confirmed on the
+ * true residual at the end of a cycle) or after maxit iterations in all.
+ * Keeps 2 restart + 1 vectors of n doubles in the context (allocated at the
+ * first call with a larger restart).  b_dev, x_dev device [n], not aliased;
+ * info->iters counts Arnoldi steps, info->relres is the true relative
+ * residual.  Synchronises `stream` once per iteration.  Returns OK,
+ * NOT_CONVERGED or BREAKDOWN. */
+int geneo_solve_gmres(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol,
+                      int32_t maxit, int32_t restart, geneo_solve_info *info, void *stream);
 
 /* on = 1 / 0: later PCG solves of the context use the balanced form / the
  * literal form (see geneo_options.balanced).  geneo_apply_preconditioner

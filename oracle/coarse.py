@@ -182,14 +182,22 @@ def xi_projector_curl(mesh, w, dec, i, Gi):
     return Gi @ sla.solve(S, GtA, assume_a='pos')
 
 
-def local_gevp(mesh, w, A, AT, dec, j):
-    """Dense solve of GEVP "tauthresholdAS" (eq. "eigAtildeBAS") on Omega_j."""
+def local_gevp(mesh, w, A, AT, dec, j, pencil="filtered"):
+    """Dense solve of GEVP "tauthresholdAS" (eq. "eigAtildeBAS") on Omega_j;
+    pencil="classical" solves the unfiltered GEVP of the remark in Sec. 3.2,
+    eq. "eigGenEOClassis": D_j A_j D_j V = lambda A_j^Neu V."""
     Ai = local_dirichlet(A, dec, j)
     Aneu = local_neumann(mesh, AT, dec, j)
     Gi, _ = local_gradient(mesh, dec, j)
-    xi = xi_projector_curl(mesh, w, dec, j, Gi)
-    Ixi = np.eye(len(Ai)) - xi
     Dj = dec.D[j]
+    if pencil == "classical":
+        xi = np.zeros((len(Ai), len(Ai)))
+        Ixi = np.eye(len(Ai))
+    elif pencil == "filtered":
+        xi = xi_projector_curl(mesh, w, dec, j, Gi)
+        Ixi = np.eye(len(Ai)) - xi
+    else:
+        raise ValueError(pencil)
     L = Ixi.T @ (Dj[:, None] * Ai * Dj[None, :]) @ Ixi
     L = 0.5 * (L + L.T)
     lam, V = sla.eigh(L, Aneu)
@@ -215,13 +223,14 @@ def tau_paper(tau, convention="reciprocal"):
     raise ValueError(convention)
 
 
-def geneo_columns(mesh, w, A, AT, dec, tau_p, gevps=None):
+def geneo_columns(mesh, w, A, AT, dec, tau_p, gevps=None, pencil="filtered"):
     """Columns R_j^T D_j (I - xi_0j) V_jk for lambda_jk > tau_p, per subdomain
-    in descending lambda order.  Returns (cols, gevps)."""
+    in descending lambda order (R_j^T D_j V_jk for the classical pencil, whose
+    xi is zero).  Returns (cols, gevps)."""
     cols = []
     out = []
     for j in range(dec.nsub):
-        g = gevps[j] if gevps is not None else local_gevp(mesh, w, A, AT, dec, j)
+        g = gevps[j] if gevps is not None else local_gevp(mesh, w, A, AT, dec, j, pencil)
         out.append(g)
         sel = np.nonzero(g.lam > tau_p)[0]
         Ixi = np.eye(len(g.Ai)) - g.xi

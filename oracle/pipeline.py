@@ -32,7 +32,7 @@ class OracleProblem:
 
 
 def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
-                  pou="boolean"):
+                  pou="boolean", pencil="filtered"):
     mesh = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active,
                       natural=getattr(w, "natural", None))
     A = assemble_A(mesh, w)
@@ -52,7 +52,7 @@ def build_problem(w, *, coarse="snk", geneo=True, tau_convention="reciprocal",
     gcols, gevps = ([], None)
     E = None
     if geneo:
-        gcols, gevps = geneo_columns(mesh, w, A, AT, dec, tp)
+        gcols, gevps = geneo_columns(mesh, w, A, AT, dec, tp, pencil=pencil)
         if gcols:
             E = coarse_matrix(mesh, w, assemble_Z(n, cols + gcols))
             keep = independent_geneo(E, len(cols))

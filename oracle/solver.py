@@ -144,6 +144,66 @@ def pcg(A, b, Minv, tol=1e-8, maxit=1000, x0=None):
     return PCGResult(x, maxit, hist[-1], hist)
 
 
+def gmres_right(A, b, Minv, tol=1e-6, maxit=1000, restart=100):
+    """Right-preconditioned restarted GMRES from x0 = 0 (Sec. 4: the paper's
+    Krylov method): x_k = x0 + M^-1 V_k y_k with y_k minimising
+    ||beta e_1 - H_k y|| over the Arnoldi basis V_k of A M^-1 (modified
+    Gram-Schmidt, Givens rotations).  Stops when the true-residual estimate
+    |g_{k+1}| <= tol ||b||, confirmed on b - A x at the end of a cycle.
+    Returns PCGResult (iters = Arnoldi steps)."""
+    n = b.shape[0]
+    x = np.zeros(n)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return PCGResult(x, 0, 0.0, [0.0])
+    its, hist = 0, []
+    while its < maxit:
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        hist.append(beta / nb)
+        if beta <= tol * nb:
+            return PCGResult(x, its, beta / nb, hist)
+        m = restart
+        V = np.zeros((m + 1, n))
+        Zs = np.zeros((m, n))
+        H = np.zeros((m + 1, m))
+        V[0] = r / beta
+        g = np.zeros(m + 1)
+        g[0] = beta
+        cs, sn = np.zeros(m), np.zeros(m)
+        k = 0
+        for j in range(m):
+            if its >= maxit:
+                break
+            Zs[j] = Minv(V[j])
+            w = A @ Zs[j]
+            for i in range(j + 1):
+                H[i, j] = V[i] @ w
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                a, c = H[i, j], H[i + 1, j]
+                H[i, j], H[i + 1, j] = cs[i] * a + sn[i] * c, -sn[i] * a + cs[i] * c
+            rho = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j], H[j + 1, j] = rho, 0.0
+            g[j + 1], g[j] = -sn[j] * g[j], cs[j] * g[j]
+            its += 1
+            k = j + 1
+            hist.append(abs(g[j + 1]) / nb)
+            if abs(g[j + 1]) <= tol * nb:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + Zs[:k].T @ y
+        if abs(g[k]) <= tol * nb:
+            rel = np.linalg.norm(b - A @ x) / nb
+            if rel <= tol or its >= maxit:
+                return PCGResult(x, its, rel, hist)
+    return PCGResult(x, its, np.linalg.norm(b - A @ x) / nb, hist)
+
+
 def direct_solve(A, b):
     return spla.spsolve(sp.csc_matrix(A), b)
 

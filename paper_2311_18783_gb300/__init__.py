@@ -8,8 +8,8 @@ no CPU fallback.
 """
 from .api import (GeneoError, Mlp, Options, Solver, compose, load_library, shard_problems,
                   PREC_FP64, PREC_FP32, PREC_BF16, COARSE_NONE, COARSE_SNK, COARSE_NK,
-                  TAU_RECIPROCAL, TAU_PAPER)
+                  TAU_RECIPROCAL, TAU_PAPER, PENCIL_FILTERED, PENCIL_CLASSICAL)
 
 __all__ = ["GeneoError", "Mlp", "Options", "Solver", "compose", "load_library", "shard_problems",
            "PREC_FP64", "PREC_FP32", "PREC_BF16", "COARSE_NONE", "COARSE_SNK", "COARSE_NK",
-           "TAU_RECIPROCAL", "TAU_PAPER"]
+           "TAU_RECIPROCAL", "TAU_PAPER", "PENCIL_FILTERED", "PENCIL_CLASSICAL"]

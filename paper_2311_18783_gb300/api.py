@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libgeneo.so")
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 COARSE_NONE, COARSE_SNK, COARSE_NK = 0, 1, 2
 TAU_RECIPROCAL, TAU_PAPER = 0, 1
+PENCIL_FILTERED, PENCIL_CLASSICAL = 0, 1
 NOT_CONVERGED = 1
 
 
@@ -41,7 +42,8 @@ class Options(C.Structure):
                 ("coarse_dense", C.c_int32), ("coarse_leaf", C.c_int32),
                 ("use_graph", C.c_int32), ("gradient_shift", C.c_int32),
                 ("keep_eigvecs", C.c_int32), ("warm_start", C.c_void_p),
-                ("lobpcg_neumann", C.c_int32), ("balanced", C.c_int32)]
+                ("lobpcg_neumann", C.c_int32), ("balanced", C.c_int32),
+                ("geneo_pencil", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -91,6 +93,8 @@ _SIGS = {
     "geneo_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int32, C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_use_balanced": (C.c_int, [C.c_void_p, C.c_int32]),
+    "geneo_solve_gmres": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
+                                    C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                    C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_segments": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
@@ -388,6 +392,15 @@ class Solver:
         info = SolveInfo()
         st = _check(_LIB.geneo_solve_refined(self._ctx, _ptr(b), _ptr(x), tol, maxit, nref,
                                              C.byref(info), _stream(stream)))
+        return {"status": st, "iters": info.iters, "relres": info.relres,
+                "seconds": info.seconds}
+
+    def solve_gmres(self, b, x, tol=1e-6, maxit=1000, restart=100, stream=None):
+        """Right-preconditioned GMRES(restart) from x = 0; relres is the true
+        relative residual."""
+        info = SolveInfo()
+        st = _check(_LIB.geneo_solve_gmres(self._ctx, _ptr(b), _ptr(x), tol, maxit, restart,
+                                           C.byref(info), _stream(stream)))
         return {"status": st, "iters": info.iters, "relres": info.relres,
                 "seconds": info.seconds}
 

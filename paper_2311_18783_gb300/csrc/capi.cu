@@ -122,6 +122,8 @@ static int check_setup_args(const geneo_problem *p, const geneo_options *opt, ge
     return fail(GENEO_ERR_INVALID_ARG, "lobpcg_neumann must be 0 or 1");
   if (o.balanced != 0 && o.balanced != 1)
     return fail(GENEO_ERR_INVALID_ARG, "balanced must be 0 or 1");
+  if (o.geneo_pencil != GENEO_PENCIL_FILTERED && o.geneo_pencil != GENEO_PENCIL_CLASSICAL)
+    return fail(GENEO_ERR_INVALID_ARG, "unknown GenEO pencil");
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
       (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
@@ -284,6 +286,16 @@ int geneo_solve_refined(geneo_ctx *c, const double *b, double *x, double tol, in
   if (nref < 0 || nref > 16) return fail(GENEO_ERR_INVALID_ARG, "nref must be in 0..16");
   if (b == x) return fail(GENEO_ERR_INVALID_ARG, "b and x must not alias");
   return guarded([&]() { return geneo::pcg_refined(c, b, x, tol, maxit, nref, info, as_stream(s)); });
+}
+
+int geneo_solve_gmres(geneo_ctx *c, const double *b, double *x, double tol, int32_t maxit,
+                      int32_t restart, geneo_solve_info *info, void *s) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
+  if (!c || !b || !x) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0) || maxit < 1) return fail(GENEO_ERR_INVALID_ARG, "tol must be > 0, maxit >= 1");
+  if (restart < 1 || restart > 1000) return fail(GENEO_ERR_INVALID_ARG, "restart must be in 1..1000");
+  if (b == x) return fail(GENEO_ERR_INVALID_ARG, "b and x must not alias");
+  return guarded([&]() { return geneo::gmres(c, b, x, tol, maxit, restart, info, as_stream(s)); });
 }
 
 int geneo_use_balanced(geneo_ctx *c, int32_t on) {

@@ -106,6 +106,8 @@ struct geneo_ctx {
   geneo::DevBuf<double> p_r, p_z, p_p, p_q, scal, partials;
   geneo::DevBuf<double> h_b, h_x;  // device copies used by geneo_solve_host
   geneo::DevBuf<double> ref_r, ref_d;  // refinement: accurate residual and correction
+  geneo::DevBuf<double> gm_V, gm_Z;    // GMRES: Krylov basis and preconditioned basis
+  int gm_cap = 0;
   geneo::DevBuf<int> d_err;
   double *h_scal = nullptr;  // pinned host mirror of the PCG scalars
 

@@ -524,10 +524,16 @@ static void xi_apply(Lobpcg &L, const double *x, double *out, int k, int mode) {
   }
 }
 
+static bool classical_pencil(const Lobpcg &L) {
+  return L.c->opt.geneo_pencil == GENEO_PENCIL_CLASSICAL;
+}
+
 // Y <- Y - G S_B^-1 G^T B Y: the B-orthogonal projection away from the
-// gradients, where the eigenvectors of the GEVP live (for g = G c in the
-// null space of L, g^T L v = 0 = lambda g^T B v)
+// gradients, where the eigenvectors of the filtered GEVP live (for g = G c
+// in the null space of L, g^T L v = 0 = lambda g^T B v).  The classical
+// pencil has no such null space: no projection.
 static void project_gradients_B(Lobpcg &L, double *Y, int k) {
+  if (classical_pencil(L)) return;
   k_gtA_curl<<<grid_for(L.op.nv * k, 128), 128, 0, L.s>>>(
       L.op.ctp_n.p, L.op.ctt_n.p, L.op.ct_n.p, L.op.lidx_n.p, L.op.tcurl.p, L.op.tmass.p, L.op.col_sub.p, L.op.col_out.p,
       L.c->loc.d_voff.p, L.op.nv, k, L.vlen, L.op.vlenS, Y, L.U1.p);
@@ -539,9 +545,17 @@ static void project_gradients_B(Lobpcg &L, double *Y, int k) {
                                                     L.vlen, L.op.vlenS, L.U2.p, Y, Y, 1, nullptr);
 }
 
-// LY = (I - xi)^T D A D (I - xi) Y  for a block of k columns
+// LY = (I - xi)^T D A D (I - xi) Y  for a block of k columns (Sec. 3.2,
+// eq. "eigAtildeBAS"), or D A D Y for the classical pencil of the remark in
+// Sec. 3.2 (eq. "eigGenEOClassis")
 static void apply_L(Lobpcg &L, const double *Y, double *LY, int k) {
   const int64_t tot = L.vlen * k;
+  if (classical_pencil(L)) {
+    k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.op.dmask.p, k, L.vlen, Y, L.T2.p);
+    apply_sparse(L, L.op.aval, L.T2.p, L.T1.p, k);         // T1 = A D Y
+    k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.op.dmask.p, k, L.vlen, L.T1.p, LY);
+    return;
+  }
   xi_apply(L, Y, L.T1.p, k, 1);                        // T1 = (I - xi) Y
   k_dscale<<<grid_for(L.vlen, 256), 256, 0, L.s>>>(L.op.dmask.p, k, L.vlen, L.T1.p, L.T2.p);
   apply_sparse(L, L.op.aval, L.T2.p, L.T1.p, k);           // T1 = A D (I - xi) Y
@@ -1205,7 +1219,11 @@ void geneo_eigenvectors(geneo_ctx *c) {
     GENEO_CUDA(cudaMemsetAsync(L.T2.p, 0, sizeof(double) * L.vlen * k, s));
     GENEO_CUDA(cudaMemcpyAsync(L.T2.p, L.Q.p + (int64_t)c0 * L.vlen, sizeof(double) * L.vlen * kk,
                                cudaMemcpyDeviceToDevice, s));
-    xi_apply(L, L.T2.p, L.T1.p, k, 1);
+    if (classical_pencil(L))  // R_j^T D_j V
+      GENEO_CUDA(cudaMemcpyAsync(L.T1.p, L.T2.p, sizeof(double) * L.vlen * k,
+                                 cudaMemcpyDeviceToDevice, s));
+    else  // R_j^T D_j (I - xi_j) V
+      xi_apply(L, L.T2.p, L.T1.p, k, 1);
     k_dscale<<<grid_for(L.vlen, 256), 256, 0, s>>>(L.op.dmask.p, kk, L.vlen, L.T1.p,
                                                    V.p + (int64_t)c0 * L.vlen);
   }

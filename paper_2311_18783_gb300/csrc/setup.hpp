@@ -115,6 +115,9 @@ int pcg(geneo_ctx *c, const double *b, double *x, double tol, int maxit, geneo_s
 // precision) residuals; info->relres is the accurate relative residual
 int pcg_refined(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int nref,
                 geneo_solve_info *info, cudaStream_t s);
+// right-preconditioned restarted GMRES(restart) with M^-1_AS,2
+int gmres(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int restart,
+          geneo_solve_info *info, cudaStream_t s);
 // one PCG per independent component (contiguous unknown ranges), same launches
 int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit,
                  geneo_solve_info *info, cudaStream_t s);

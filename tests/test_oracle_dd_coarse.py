@@ -459,3 +459,35 @@ def test_refined_direct_solve_against_high_precision():
     assert err(direct_solve(A, b)) > 1e-8
     assert err(x1) <= 1e-8
     assert hist[-1] <= 1e-8
+
+
+def test_gmres_right_minimises_the_residual():
+    """Right-preconditioned GMRES (Sec. 4's Krylov method): after k steps
+    from x0 = 0, x_k minimises ||b - A x|| over the preconditioned Krylov
+    space M^-1 K_k(A M^-1, b).  Checked against a dense least-squares solve
+    over an explicit basis of that space, for every k up to convergence, and
+    the solve reaches the direct solution."""
+    from oracle.solver import gmres_right
+    w = small(n=(5, 4, 4), parts=(2, 2, 1), overlap=1, gamma=1e-2)
+    prob = build_problem(w)
+    A = prob.A.toarray()
+    b = prob.b[0]
+    Minv = np.array([prob.M.apply(e) for e in np.eye(len(b))]).T
+    AM = A @ Minv
+    for k in (1, 3, 6, 10):
+        r = gmres_right(prob.A, b, prob.M.apply, tol=1e-300, maxit=k, restart=50)
+        K = np.empty((len(b), k))
+        v = b / np.linalg.norm(b)
+        for j in range(k):  # orthonormal Krylov basis (two Gram-Schmidt passes)
+            for _ in range(2):
+                v = v - K[:, :j] @ (K[:, :j].T @ v)
+            K[:, j] = v / np.linalg.norm(v)
+            v = AM @ K[:, j]
+        y, *_ = np.linalg.lstsq(AM @ K, b, rcond=None)
+        best = np.linalg.norm(b - AM @ K @ y)
+        assert r.iters == k
+        assert abs(np.linalg.norm(b - A @ r.x) - best) <= 1e-8 * np.linalg.norm(b)
+    r = gmres_right(prob.A, b, prob.M.apply, tol=1e-10)
+    x = direct_solve(prob.A, b)
+    assert r.relres <= 1e-10
+    assert np.linalg.norm(r.x - x) <= 1e-6 * np.linalg.norm(x)
