@@ -536,8 +536,18 @@ def main():
     w = getattr(W, args.workload)()
     prec = pkg.PREC_FP32 if args.precision == "mixed" else pkg.PREC_FP64
     t0 = time.perf_counter()
-    s = pkg.Solver.from_workload(w, precision=prec, balanced=1)
+    s = pkg.Solver.from_workload(w, precision=prec, balanced=1, autotune=1)
     setup_s = time.perf_counter() - t0
+    stage_names = ["assembly", "local_inverses", "split_factors", "geneo_eigensolves",
+                   "geneo_filter", "coarse_factor", "autotune", "total"]
+    stages = dict(zip(stage_names, [float(v) for v in s.export("setup_stages")]))
+    tuned = []
+    for row in s.export("autotune").reshape(-1, 12):
+        ncand = pkg.Solver.symv_config_count(int(row[1]))
+        tuned.append({"target": "local factors" if row[0] == 0 else "S_j^-1 blocks",
+                      "precision": "f64" if int(row[1]) == pkg.PREC_FP64 else "f32",
+                      "chosen": int(row[2]), "from_cache": bool(row[3]),
+                      "ms_per_candidate": [float(v) for v in row[4:4 + ncand]]})
     n = s.n
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     s.assemble_rhs(w.f_slot[0], b)
@@ -683,7 +693,8 @@ def main():
                        "oracle_solution": None if xo is None else
                        "tests/golden/cube32_solution.npy (sparse LU + extended-precision "
                        "refinement, written by tests/golden/make_cube32_solution.py)",
-                       "setup_s": setup_s},
+                       "setup_s": setup_s, "setup_stages_s": stages,
+                       "autotuned_symv": tuned},
             "applies_per_s": applies_per_s,
             "roofline": roof, "clocks": clk, "gpu_launches": prof["launches"],
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8,

@@ -153,6 +153,17 @@ typedef struct {
                                 Z^T r_k).  0: x0 = 0 and the literal four-step apply.
                                 Switchable later with geneo_use_balanced. */
   int32_t geneo_pencil;      /* GENEO_PENCIL_FILTERED (default) or GENEO_PENCIL_CLASSICAL */
+  int32_t autotune;          /* 1: at the end of the set-up, time every candidate launch
+                                configuration of the streaming SYMV (bulk-copy stages,
+                                tiles per barrier pair, warps per CTA, CTAs per SM) on the
+                                context's local factors (each stored precision) and S_j^-1
+                                blocks, and keep the fastest; results are cached per
+                                process by target, precision, nrhs, mean n_i bucket and
+                                stored-tile bucket (geneo_export("autotune")).  0: the
+                                default configuration */
+  const char *autotune_cache; /* NULL, or a text file read before tuning and appended with
+                                every new result ("key index milliseconds" per line); the
+                                string is only read during geneo_setup */
 } geneo_options;
 
 typedef struct {
@@ -261,6 +272,16 @@ int geneo_solve_refined(geneo_ctx *ctx, const double *b_dev, double *x_dev, doub
  * NOT_CONVERGED or BREAKDOWN. */
 int geneo_solve_gmres(geneo_ctx *ctx, const double *b_dev, double *x_dev, double tol,
                       int32_t maxit, int32_t restart, geneo_solve_info *info, void *stream);
+
+/* Launch configurations of the streaming SYMV of the local factors
+ * (options.autotune chooses among them): geneo_symv_config_count gives their
+ * number for a storage precision (GENEO_PREC_FP32 or GENEO_PREC_FP64; else
+ * INVALID_ARG), geneo_use_symv_config selects entry `index` (0 = default)
+ * for the context's local factors in that precision.  Every configuration
+ * computes the same product; only the association of the column partial
+ * sums differs. */
+int geneo_symv_config_count(int32_t precision);
+int geneo_use_symv_config(geneo_ctx *ctx, int32_t precision, int32_t index);
 
 /* on = 1 / 0: later PCG solves of the context use the balanced form / the
  * literal form (see geneo_options.balanced).  geneo_apply_preconditioner
@@ -382,6 +403,14 @@ int geneo_profile_read(geneo_ctx *ctx, geneo_profile *out);
  *  "loc_nt" int32 [nsub], "loc_toff" int64 [nsub+1], "loc_voff" int64 [nsub+1],
  *  "loc_vlen" int64 [1], "loc_f32" float32  tile layout and float32 local factors
  *  "lobpcg_iters", "lobpcg_iters_first" int32 [nsub]  LOBPCG iterations (all, first block)
+ *  "setup_stages" float64 [8]       wall seconds of the set-up stages: assembly (with the
+ *                                   topology), local inverses, split / bfloat16 factors,
+ *                                   GenEO eigensolves, GenEO independence filter, coarse
+ *                                   factor, autotuning, total
+ *  "autotune"    float64 [targets][12]  per tuned SYMV target: target (0 local factors,
+ *                                   1 S_j^-1 blocks), precision, chosen candidate, 1 if it
+ *                                   came from the cache, then milliseconds per candidate
+ *                                   (NaN past the last)
  *  "mlp_features" float32 [loc_vlen][5], "eig_V" float64 [8][loc_vlen],
  *  "eig_nq" int32 [nsub]            warm-start features and training targets
  * Returns INVALID_ARG for an unknown name or a too small buffer, STATE for a

@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("use_graph", C.c_int32), ("gradient_shift", C.c_int32),
                 ("keep_eigvecs", C.c_int32), ("warm_start", C.c_void_p),
                 ("lobpcg_neumann", C.c_int32), ("balanced", C.c_int32),
-                ("geneo_pencil", C.c_int32)]
+                ("geneo_pencil", C.c_int32), ("autotune", C.c_int32),
+                ("autotune_cache", C.c_char_p)]
 
 
 class Sizes(C.Structure):
@@ -93,6 +94,8 @@ _SIGS = {
     "geneo_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int32, C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_use_balanced": (C.c_int, [C.c_void_p, C.c_int32]),
+    "geneo_symv_config_count": (C.c_int, [C.c_int32]),
+    "geneo_use_symv_config": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "geneo_solve_gmres": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                     C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
@@ -141,7 +144,7 @@ _EXPORT_DTYPES = {
     "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
     "loc_vlen": np.int64, "mlp_features": np.float32, "eig_V": np.float64, "eig_nq": np.int32,
     "lobpcg_iters": np.int32, "lobpcg_iters_first": np.int32, "seg_off": np.int64,
-    "xv_off": np.int64, "xv_vert": np.int32,
+    "xv_off": np.int64, "xv_vert": np.int32, "setup_stages": np.float64, "autotune": np.float64,
 }
 
 
@@ -189,6 +192,8 @@ def default_options(**kw):
     o = Options()
     lib.geneo_default_options(C.byref(o))
     for k, v in kw.items():
+        if k == "autotune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -403,6 +408,13 @@ class Solver:
                                            C.byref(info), _stream(stream)))
         return {"status": st, "iters": info.iters, "relres": info.relres,
                 "seconds": info.seconds}
+
+    def use_symv_config(self, precision, index):
+        _check(_LIB.geneo_use_symv_config(self._ctx, precision, index))
+
+    @staticmethod
+    def symv_config_count(precision):
+        return _check(load_library().geneo_symv_config_count(precision))
 
     def use_balanced(self, on=True):
         _check(_LIB.geneo_use_balanced(self._ctx, 1 if on else 0))

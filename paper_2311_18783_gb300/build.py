@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgeneo.so")
 SOURCES = ["topology.cpp", "compose.cpp", "small_eig.cpp", "ordered_drop.cpp", "dense.cu", "setup.cu", "solve.cu", "lobpcg.cu", "capi.cu",
-           "noalloc.cu", "coarse_mf.cu", "tc_symm.cu", "mlp.cu", "gmres.cu"]
+           "noalloc.cu", "coarse_mf.cu", "tc_symm.cu", "mlp.cu", "gmres.cu",
+           "autotune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

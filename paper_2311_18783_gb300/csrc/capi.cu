@@ -37,6 +37,9 @@ void geneo_ctx::drop_graph() {
   if (pcg_exec) cudaGraphExecDestroy(pcg_exec);
   pcg_exec = nullptr;
   pcg_key = -1;
+  if (seg_exec) cudaGraphExecDestroy(seg_exec);
+  seg_exec = nullptr;
+  seg_key = -1;
   for (auto &p : g_ev_local) ev_free.insert(ev_free.end(), {p.first, p.second});
   for (auto &p : g_ev_coarse) ev_free.insert(ev_free.end(), {p.first, p.second});
   g_ev_local.clear();
@@ -50,6 +53,7 @@ geneo_ctx::~geneo_ctx() {
   for (auto &p : ev_coarse) ev_free.insert(ev_free.end(), {p.first, p.second});
   for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
   if (h_scal) cudaFreeHost(h_scal);
+  if (h_seg) cudaFreeHost(h_seg);
   if (h_act) cudaFreeHost(h_act);
   if (stream) cudaStreamDestroy(stream);
 }
@@ -124,6 +128,8 @@ static int check_setup_args(const geneo_problem *p, const geneo_options *opt, ge
     return fail(GENEO_ERR_INVALID_ARG, "balanced must be 0 or 1");
   if (o.geneo_pencil != GENEO_PENCIL_FILTERED && o.geneo_pencil != GENEO_PENCIL_CLASSICAL)
     return fail(GENEO_ERR_INVALID_ARG, "unknown GenEO pencil");
+  if (o.autotune != 0 && o.autotune != 1)
+    return fail(GENEO_ERR_INVALID_ARG, "autotune must be 0 or 1");
   if ((o.coarse_dense != 0 && o.coarse_dense != 1) || o.coarse_leaf < 0 ||
       (o.use_graph != 0 && o.use_graph != 1) || (o.gradient_shift != 0 && o.gradient_shift != 1))
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse factor or graph options");
@@ -296,6 +302,22 @@ int geneo_solve_gmres(geneo_ctx *c, const double *b, double *x, double tol, int3
   if (restart < 1 || restart > 1000) return fail(GENEO_ERR_INVALID_ARG, "restart must be in 1..1000");
   if (b == x) return fail(GENEO_ERR_INVALID_ARG, "b and x must not alias");
   return guarded([&]() { return geneo::gmres(c, b, x, tol, maxit, restart, info, as_stream(s)); });
+}
+
+int geneo_symv_config_count(int32_t precision) {
+  if (precision == GENEO_PREC_FP32) return geneo::symv_candidates<float>();
+  if (precision == GENEO_PREC_FP64) return geneo::symv_candidates<double>();
+  return fail(GENEO_ERR_INVALID_ARG, "precision must be FP32 or FP64");
+}
+
+int geneo_use_symv_config(geneo_ctx *c, int32_t precision, int32_t index) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  const int n = geneo_symv_config_count(precision);
+  if (n < 0) return n;
+  if (index < 0 || index >= n) return fail(GENEO_ERR_INVALID_ARG, "configuration index out of range");
+  c->loc.symv_cfg[precision == GENEO_PREC_FP64 ? 1 : 0] = index;
+  return GENEO_OK;
 }
 
 int geneo_use_balanced(geneo_ctx *c, int32_t on) {
@@ -531,6 +553,21 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
       put(v.data(), v.size() * 8);
     } else if (nm == "eig_nq") put(c->eig_nq.data(), c->eig_nq.size() * 4);
     else if (nm == "lobpcg_iters") put(c->lobpcg_iters.data(), c->lobpcg_iters.size() * 4);
+    else if (nm == "setup_stages") put(c->stage_s, sizeof(c->stage_s));
+    else if (nm == "autotune") {
+      std::vector<double> v;
+      for (const auto &r : c->tune) {
+        double row[12];
+        for (double &q : row) q = std::nan("");
+        row[0] = r.target == "local" ? 0.0 : 1.0;
+        row[1] = r.precision;
+        row[2] = r.chosen;
+        row[3] = r.from_cache ? 1.0 : 0.0;
+        for (size_t k = 0; k < r.ms.size() && k < 8; ++k) row[4 + k] = r.ms[k];
+        v.insert(v.end(), row, row + 12);
+      }
+      put(v.data(), v.size() * 8);
+    }
     else if (nm == "lobpcg_iters_first") put(c->lobpcg_iters0.data(), c->lobpcg_iters0.size() * 4);
     else if (nm == "k0k1") {
       int32_t k[2] = {c->dec.k0, c->dec.k1};

@@ -24,6 +24,16 @@ struct geneo_mlp {
   geneo::Mlp *m = nullptr;
 };
 
+namespace geneo {
+// one autotuned SYMV target: candidate timings and the configuration kept
+struct TuneRecord {
+  std::string target, key;
+  int precision = 0, chosen = 0;
+  bool from_cache = false;
+  std::vector<double> ms;  // per candidate (empty when taken from the cache)
+};
+}  // namespace geneo
+
 struct geneo_ctx {
   // problem copy
   int nx = 0, ny = 0, nz = 0;
@@ -44,13 +54,21 @@ struct geneo_ctx {
   geneo::DevBuf<int64_t> d_seg_off;
   geneo::DevBuf<double> seg_sc;     // per-component PCG scalars
   geneo::DevBuf<int> seg_act;
-  std::vector<double> seg_hs;
   std::vector<int> seg_ha;
+  double *h_seg = nullptr;            // pinned host mirror of the per-component scalars
+  cudaGraphExec_t seg_exec = nullptr; // CUDA graph of one segmented PCG iteration
+  int seg_key = -1;
+  int64_t seg_graph_launches = 0;
   geneo_options opt{};
   int device = 0;
   int sm_count = 0;
   cudaStream_t stream = nullptr;  // internal set-up stream
   double setup_seconds = 0;
+  // wall seconds of the set-up stages: assembly, local inverses, split /
+  // bfloat16 factors, GenEO eigensolves, GenEO independence filter, coarse
+  // factor, autotuning, total
+  double stage_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<geneo::TuneRecord> tune;
 
   geneo::Topology topo;
   geneo::Decomposition dec;

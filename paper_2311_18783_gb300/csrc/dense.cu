@@ -85,6 +85,56 @@ void TileBatch::schedule(int nctas, cudaStream_t s) {
   d_strip_m.upload(sm, s);
   d_strip_I.upload(si, s);
   d_cta_off.upload(off, s);
+  base_ctas = nctas;
+  for (auto &e : extra) e.nctas = 0;  // rebuilt on demand
+}
+
+// Schedule with cps persistent CTAs per SM of the base schedule (cps = 1 is
+// the base schedule itself); built once per cps.
+const TileBatch::Sched &TileBatch::sched_for(int cps) {
+  if (cps <= 1) {
+    base.nctas = sched_ctas;
+    base.strip_m.p = d_strip_m.p;
+    base.strip_I.p = d_strip_I.p;
+    base.cta_off.p = d_cta_off.p;
+    return base;
+  }
+  Sched &e = extra[std::min(cps, 4) - 2];
+  if (e.nctas) return e;
+  struct Strip { int32_t m, I; };
+  std::vector<Strip> strips;
+  for (int m = 0; m < nmat; ++m)
+    for (int I = 0; I < nt[m]; ++I) strips.push_back({m, I});
+  std::stable_sort(strips.begin(), strips.end(),
+                   [](const Strip &a, const Strip &b) { return a.I > b.I; });
+  const int nctas = std::max(1, std::min<int>(base_ctas * cps, (int)strips.size()));
+  using Load = std::pair<int64_t, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+  for (int c = 0; c < nctas; ++c) pq.push({0, c});
+  std::vector<std::vector<Strip>> per(nctas);
+  for (const Strip &st : strips) {
+    Load l = pq.top();
+    pq.pop();
+    per[l.second].push_back(st);
+    pq.push({l.first + st.I + 1, l.second});
+  }
+  std::vector<int32_t> sm, si, off(1, 0);
+  for (int c = 0; c < nctas; ++c) {
+    for (const Strip &st : per[c]) {
+      sm.push_back(st.m);
+      si.push_back(st.I);
+    }
+    off.push_back((int32_t)sm.size());
+  }
+  e.own_m.upload(sm, 0);
+  e.own_I.upload(si, 0);
+  e.own_off.upload(off, 0);
+  GENEO_CUDA(cudaStreamSynchronize(0));
+  e.strip_m.p = e.own_m.p;
+  e.strip_I.p = e.own_I.p;
+  e.cta_off.p = e.own_off.p;
+  e.nctas = nctas;
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -491,21 +541,23 @@ template <> struct Vec2<float> { using type = float2; };
 // Tiles are consumed in batches of up to D tiles of one strip: one barrier
 // after the D waits (also the uniform timeout decision), the D tiles'
 // products, one barrier, then the column partials of the D tiles reduced
-// across warps by all threads, and D new copies issued.
-template <typename T, int NST, int D>
-__global__ void __launch_bounds__(256, 1)
+// across warps by all threads, and D new copies issued.  WARPS warps share a
+// tile: each owns 64 / WARPS rows and lane l columns 2l, 2l + 1.
+template <typename T, int NST, int D, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
     k_symv_strips(const T *__restrict__ data, const int64_t *__restrict__ toff,
                   const int64_t *__restrict__ voff, const int32_t *__restrict__ strip_m,
                   const int32_t *__restrict__ strip_I, const int32_t *__restrict__ cta_off,
                   const double *__restrict__ x, double *__restrict__ rowpart,
                   double *__restrict__ colpart, int *err) {
-  static_assert(D <= NST && D * kTile <= 256, "batch must fit the stages and the block");
+  constexpr int R = kTile / WARPS;  // rows per warp
+  static_assert(D <= NST && D * kTile <= WARPS * 32, "batch must fit the stages and the block");
   using A = typename Acc<T>::type;
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(128) unsigned char smraw[];
   T *stage = reinterpret_cast<T *>(smraw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + (size_t)NST * kTileElems * sizeof(T));
-  A *red = reinterpret_cast<A *>(bar + NST);  // [D][8][64]
+  A *red = reinterpret_cast<A *>(bar + NST);  // [D][WARPS][64]
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
   if (s0 >= s1) return;
@@ -538,10 +590,10 @@ __global__ void __launch_bounds__(256, 1)
     const int m = strip_m[s], I = strip_I[s];
     const int64_t vb = voff[m];
     const int64_t tb = toff[m] + (int64_t)I * (I + 1) / 2;
-    A xi[8], rp[8];
+    A xi[R], rp[R];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      xi[r] = (A)x[vb + (int64_t)I * kTile + w * 8 + r];
+    for (int r = 0; r < R; ++r) {
+      xi[r] = (A)x[vb + (int64_t)I * kTile + w * R + r];
       rp[r] = (A)0;
     }
     for (int J0 = 0; J0 <= I; J0 += D) {
@@ -574,14 +626,14 @@ __global__ void __launch_bounds__(256, 1)
           const T *t = stage + (size_t)((consumed + d) % NST) * kTileElems;
           A c0 = 0, c1 = 0;
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const V2 a = *reinterpret_cast<const V2 *>(t + (w * 8 + r) * kTile + 2 * l);
+          for (int r = 0; r < R; ++r) {
+            const V2 a = *reinterpret_cast<const V2 *>(t + (w * R + r) * kTile + 2 * l);
             rp[r] = fma((A)a.x, xj[d][0], fma((A)a.y, xj[d][1], rp[r]));
             c0 = fma((A)a.x, xi[r], c0);
             c1 = fma((A)a.y, xi[r], c1);
           }
-          red[(d * 8 + w) * kTile + 2 * l] = c0;
-          red[(d * 8 + w) * kTile + 2 * l + 1] = c1;
+          red[(d * WARPS + w) * kTile + 2 * l] = c0;
+          red[(d * WARPS + w) * kTile + 2 * l + 1] = c1;
         }
       }
       __syncthreads();
@@ -592,7 +644,7 @@ __global__ void __launch_bounds__(256, 1)
         if (d < nb && J0 + d < I) {
           A sum = 0;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) sum += red[(d * 8 + q) * kTile + c];
+          for (int q = 0; q < WARPS; ++q) sum += red[(d * WARPS + q) * kTile + c];
           colpart[(tb + J0 + d) * kTile + c] = (double)sum;
         }
       }
@@ -602,11 +654,11 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (failed) break;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < R; ++r) {
       A v = rp[r];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (l == 0) rowpart[vb + (int64_t)I * kTile + w * 8 + r] = (double)v;
+      if (l == 0) rowpart[vb + (int64_t)I * kTile + w * R + r] = (double)v;
     }
   }
   if (failed && tid == 0) {
@@ -638,25 +690,83 @@ __global__ void k_symv_reduce(const int32_t *__restrict__ vrow_m,
   y[pos] = v;
 }
 
-template <typename T> constexpr int symv_stages() { return sizeof(T) == 8 ? 4 : 8; }
-template <typename T> constexpr int symv_batch_tiles() { return sizeof(T) == 8 ? 2 : 4; }
+// Candidate launch configurations of the streaming SYMV (the autotuner's
+// knob space): bulk-copy stages, tiles per barrier pair, warps per CTA and
+// persistent CTAs per SM.  Entry 0 of each list is the default.
+template <typename T> struct SymvCands;
+template <> struct SymvCands<float> {
+  static constexpr int n = 6;
+  static constexpr SymvCfg c[n] = {{8, 4, 8, 1}, {8, 4, 16, 1}, {12, 4, 16, 1},
+                                   {8, 8, 16, 1}, {6, 4, 8, 2}, {4, 2, 8, 2}};
+};
+template <> struct SymvCands<double> {
+  static constexpr int n = 5;
+  static constexpr SymvCfg c[n] = {{4, 2, 8, 1}, {4, 2, 16, 1}, {6, 2, 16, 1},
+                                   {4, 4, 16, 1}, {3, 2, 8, 2}};
+};
+
+template <typename T, int NST, int D, int WARPS>
+static void launch_symv(TileBatch &b, const TileBatch::Sched &sc, const T *data, const double *x,
+                        int *d_err, cudaStream_t s) {
+  const size_t smem = (size_t)NST * kTileElems * sizeof(T) + NST * sizeof(uint64_t) +
+                      (size_t)D * WARPS * kTile * sizeof(typename Acc<T>::type);
+  static int attr_dev = -1;
+  int dev = 0;
+  GENEO_CUDA(cudaGetDevice(&dev));
+  if (attr_dev != dev) {
+    GENEO_CUDA(cudaFuncSetAttribute(k_symv_strips<T, NST, D, WARPS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_dev = dev;
+  }
+  k_symv_strips<T, NST, D, WARPS><<<sc.nctas, WARPS * 32, smem, s>>>(
+      data, b.d_toff.p, b.d_voff.p, sc.strip_m.p, sc.strip_I.p, sc.cta_off.p, x, b.rowpart.p,
+      b.colpart.p, d_err);
+}
+
+template <typename T>
+static void launch_symv_cfg(TileBatch &b, int idx, const T *data, const double *x, int *d_err,
+                            cudaStream_t s);
+template <>
+void launch_symv_cfg<float>(TileBatch &b, int idx, const float *data, const double *x,
+                            int *d_err, cudaStream_t s) {
+  const SymvCfg &c = SymvCands<float>::c[idx];
+  const TileBatch::Sched &sc = b.sched_for(c.cps);
+  switch (idx) {
+    case 0: launch_symv<float, 8, 4, 8>(b, sc, data, x, d_err, s); break;
+    case 1: launch_symv<float, 8, 4, 16>(b, sc, data, x, d_err, s); break;
+    case 2: launch_symv<float, 12, 4, 16>(b, sc, data, x, d_err, s); break;
+    case 3: launch_symv<float, 8, 8, 16>(b, sc, data, x, d_err, s); break;
+    case 4: launch_symv<float, 6, 4, 8>(b, sc, data, x, d_err, s); break;
+    default: launch_symv<float, 4, 2, 8>(b, sc, data, x, d_err, s); break;
+  }
+}
+template <>
+void launch_symv_cfg<double>(TileBatch &b, int idx, const double *data, const double *x,
+                             int *d_err, cudaStream_t s) {
+  const SymvCfg &c = SymvCands<double>::c[idx];
+  const TileBatch::Sched &sc = b.sched_for(c.cps);
+  switch (idx) {
+    case 0: launch_symv<double, 4, 2, 8>(b, sc, data, x, d_err, s); break;
+    case 1: launch_symv<double, 4, 2, 16>(b, sc, data, x, d_err, s); break;
+    case 2: launch_symv<double, 6, 2, 16>(b, sc, data, x, d_err, s); break;
+    case 3: launch_symv<double, 4, 4, 16>(b, sc, data, x, d_err, s); break;
+    default: launch_symv<double, 3, 2, 8>(b, sc, data, x, d_err, s); break;
+  }
+}
+
+template <typename T> int symv_candidates() { return SymvCands<T>::n; }
+template <typename T> SymvCfg symv_candidate(int idx) { return SymvCands<T>::c[idx]; }
+template int symv_candidates<float>();
+template int symv_candidates<double>();
+template SymvCfg symv_candidate<float>(int);
+template SymvCfg symv_candidate<double>(int);
 
 template <typename T>
 void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
                 cudaStream_t s, cudaEvent_t ev_before, cudaEvent_t ev_after) {
-  constexpr int NST = symv_stages<T>(), D = symv_batch_tiles<T>();
-  const size_t smem = (size_t)NST * kTileElems * sizeof(T) + NST * sizeof(uint64_t) +
-                      (size_t)D * 8 * kTile * sizeof(typename Acc<T>::type);
-  static bool attr = false;
-  if (!attr) {
-    GENEO_CUDA(cudaFuncSetAttribute(k_symv_strips<T, NST, D>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  const int idx = b.symv_cfg[sizeof(T) == 8 ? 1 : 0];
   if (ev_before) record_event(ev_before, s);
-  k_symv_strips<T, NST, D><<<b.sched_ctas, 256, smem, s>>>(
-      data, b.d_toff.p, b.d_voff.p, b.d_strip_m.p, b.d_strip_I.p, b.d_cta_off.p, x, b.rowpart.p,
-      b.colpart.p, d_err);
+  launch_symv_cfg<T>(b, idx, data, x, d_err, s);
   if (ev_after) record_event(ev_after, s);
   const int64_t nblocks = b.vlen / kTile;
   k_symv_reduce<<<(unsigned)nblocks, kTile, 0, s>>>(b.d_vrow_m.p, b.d_vrow_I.p, b.d_nt.p,

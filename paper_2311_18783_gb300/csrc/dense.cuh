@@ -43,6 +43,12 @@ __device__ __forceinline__ void gemm_abt(const double *As, const double *Bs, dou
 }
 
 
+// One launch configuration of the streaming SYMV: bulk-copy stages, tiles
+// per barrier pair, warps per CTA, persistent CTAs per SM.
+struct SymvCfg {
+  int nst, d, warps, cps;
+};
+
 struct TileBatch {
   int nmat = 0;
   int maxnt = 0;
@@ -56,10 +62,25 @@ struct TileBatch {
   int sched_ctas = 0;
   DevBuf<int32_t> d_strip_m, d_strip_I, d_cta_off;
   DevBuf<double> rowpart, colpart;   // partial sums of the streaming SYMV
+  // launch configuration per storage type (0 float, 1 double): an index into
+  // the candidate lists of the autotuner (0 = default)
+  int symv_cfg[2] = {0, 0};
+  // schedules with more CTAs per SM (non-owning views plus owned storage)
+  struct View {
+    int32_t *p = nullptr;
+  };
+  struct Sched {
+    int nctas = 0;
+    View strip_m, strip_I, cta_off;
+    DevBuf<int32_t> own_m, own_I, own_off;
+  };
+  int base_ctas = 0;
+  Sched base, extra[3];
 
   void layout(const std::vector<int64_t> &dims);
   void upload_meta(cudaStream_t s);
   void schedule(int nctas, cudaStream_t s);
+  const Sched &sched_for(int cps);
 };
 
 // -- Explicit inverse of every matrix of the batch, in place (float64), by
@@ -86,6 +107,10 @@ void pivot_block_inverse(TileBatch &b, const double *L, double *Y, const double 
 template <typename T>
 void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
                 cudaStream_t s, cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
+
+// The autotuner's candidate configurations of symv_batch<T>.
+template <typename T> int symv_candidates();
+template <typename T> SymvCfg symv_candidate(int idx);
 
 // Pointer/size of a tile-packed buffer in elements.
 inline int64_t tile_elems(const TileBatch &b) { return b.ntiles * (int64_t)kTileElems; }

@@ -706,6 +706,15 @@ void setup_all(geneo_ctx *c) {
                                                       t.nnz(), c->d_val.p);
   GENEO_CHECK_LAUNCH();
 
+  auto last = t0;
+  auto stage_mark = [&](int k) {
+    GENEO_CUDA(cudaStreamSynchronize(s));
+    const auto now = std::chrono::steady_clock::now();
+    if (k == 0) c->stage_s[0] = std::chrono::duration<double>(now - t0).count();
+    else c->stage_s[k] = std::chrono::duration<double>(now - last).count();
+    last = now;
+  };
+  stage_mark(0);
   // --- local factors: A_i extracted into tile-packed storage and inverted
   const Decomposition &d = c->dec;
   std::vector<int64_t> dims(d.nsub);
@@ -748,6 +757,7 @@ void setup_all(geneo_ctx *c) {
     spd_invert(c->loc, c->loc_f64.p, ws.p, c->d_err.p, s);
     check_device_error(c, s);
   }
+  stage_mark(1);
   if (c->opt.precision == GENEO_PREC_FP32 || c->opt.precision == GENEO_PREC_BF16) {
     build_split_factors(c);
     c->local_prec = GENEO_PREC_FP32;
@@ -757,6 +767,7 @@ void setup_all(geneo_ctx *c) {
     c->local_prec = GENEO_PREC_BF16;
   }
 
+  stage_mark(2);
   // --- coarse space
   c->n0 = c->n0_snk = c->n0_geneo = 0;
   if (c->opt.coarse != GENEO_COARSE_NONE) {
@@ -780,10 +791,12 @@ void setup_all(geneo_ctx *c) {
       build_mlp_features(c);
     }
     geneo_eigenvectors(c);  // appends GenEO candidates to zc_* and sets n0_geneo
+    stage_mark(3);
     if (c->n0_geneo > 0) {
       if (c->opt.coarse_dense) geneo_filter(c);
       else geneo_filter_mf(c);
     }
+    stage_mark(4);
   }
   if (c->n0 > 0 && !c->opt.coarse_dense) {
     build_z_csr(c);
@@ -808,12 +821,16 @@ void setup_all(geneo_ctx *c) {
     c->crs_x.zero(s);
   }
 
+  stage_mark(5);
   // --- work vectors (one right-hand side; grown on demand)
   for (auto *v : {&c->h_b, &c->h_x}) v->alloc(n);
   reserve_rhs(c, 1);
   check_device_error(c, s);
+  if (c->opt.autotune) autotune_symv(c);
+  stage_mark(6);
   c->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->stage_s[7] = c->setup_seconds;
 }
 
 void assemble_rhs(geneo_ctx *c, const double *fslot_host, double *b, cudaStream_t s) {

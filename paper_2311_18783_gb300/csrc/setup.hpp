@@ -42,6 +42,10 @@ void coltet_build(geneo_ctx *c, const Columns &X, std::vector<int64_t> &ct_ptr,
 void tet_operators(geneo_ctx *c, DevBuf<double> &tcurl, DevBuf<double> &tmass, cudaStream_t s);
 
 void setup_all(geneo_ctx *c);
+// times every candidate SYMV configuration on the context's tile batches and
+// keeps the fastest (autotune.cu)
+void autotune_symv(geneo_ctx *c);
+void autotune_clear_cache();
 // Host part only: topology, decomposition, components, local structure and,
 // for a host-only context, the split near-kernel columns.  No CUDA call.
 void setup_topology(geneo_ctx *c);

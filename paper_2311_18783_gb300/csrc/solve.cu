@@ -473,7 +473,9 @@ static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s, int k) {
 // context's capture stream, with x = p_x; replayed on the caller's stream for
 // every iteration after the first.
 static void ensure_pcg_graph(geneo_ctx *c, int k) {
-  const int key = ((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0))) << 8) + k;
+  const int cfg = c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1];
+  const int key =
+      (((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 64 + cfg)) << 8) + k;
   if (c->pcg_exec && c->pcg_key == key) return;
   c->drop_graph();
   const int64_t l0 = c->launches;
@@ -660,6 +662,77 @@ __global__ void k_seg_shift(double *sc, int nseg) {
 
 }  // namespace
 
+// second half of a segmented iteration: z = M^-1 r, rz_new, p = z + beta p
+static void seg_precond_half(geneo_ctx *c, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  const int nseg = (int)c->seg_off.size() - 1;
+  double *sc = c->seg_sc.p;
+  precondition(c, c->p_r.p, c->p_z.p, s, 1);
+  c->launches += 3;
+  k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, c->d_seg_off.p, sc + 3);
+  k_seg_update_p<<<grid_for(n, 256), 256, 0, s>>>(sc, c->seg_act.p, c->d_seg_of.p, c->p_z.p,
+                                                  c->p_p.p, n);
+  k_seg_shift<<<grid_for(nseg, 256), 256, 0, s>>>(sc, nseg);
+  GENEO_CHECK_LAUNCH();
+}
+
+// first half: q = A p, alpha per component, x/r update, (r, r), scalars to
+// the pinned host mirror
+static void seg_step_half(geneo_ctx *c, double *x, cudaStream_t s) {
+  const int64_t n = c->topo.ndofs();
+  const int nseg = (int)c->seg_off.size() - 1;
+  double *sc = c->seg_sc.p;
+  spmv(c, c->p_p.p, c->p_q.p, s, 1);
+  c->launches += 3;
+  k_seg_dot<<<nseg, 256, 0, s>>>(c->p_p.p, c->p_q.p, c->d_seg_off.p, sc + 1);
+  k_seg_update_xr<<<grid_for(n, 256), 256, 0, s>>>(sc, c->seg_act.p, c->d_seg_of.p, c->p_p.p,
+                                                   c->p_q.p, x, c->p_r.p, n);
+  k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_r.p, c->d_seg_off.p, sc + 2);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaMemcpyAsync(c->h_seg, sc, sizeof(double) * kScal * nseg, cudaMemcpyDeviceToHost, s));
+}
+
+// [second half ; first half] of a segmented iteration on x = p_x, captured
+// once per local precision, profiling switch and form
+static void ensure_seg_graph(geneo_ctx *c) {
+  const int cfg = c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1];
+  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 64 + cfg;
+  if (c->seg_exec && c->seg_key == key) return;
+  if (c->seg_exec) cudaGraphExecDestroy(c->seg_exec);
+  c->seg_exec = nullptr;
+  c->seg_key = -1;
+  const int64_t l0 = c->launches;
+  const size_t nl = c->ev_local.size(), nc = c->ev_coarse.size();
+  cudaStream_t cs = c->cap_stream;
+  GENEO_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t graph = nullptr;
+  try {
+    seg_precond_half(c, cs);
+    seg_step_half(c, c->p_x.p, cs);
+  } catch (...) {
+    cudaStreamEndCapture(cs, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    c->launches = l0;
+    throw;
+  }
+  GENEO_CUDA(cudaStreamEndCapture(cs, &graph));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  GENEO_CUDA(e);
+  c->seg_exec = exec;
+  c->seg_key = key;
+  c->seg_graph_launches = c->launches - l0;
+  c->launches = l0;
+  // the event pairs recorded inside belong to the graph; they are not timed
+  for (size_t q = nl; q < c->ev_local.size(); ++q)
+    c->ev_free.insert(c->ev_free.end(), {c->ev_local[q].first, c->ev_local[q].second});
+  for (size_t q = nc; q < c->ev_coarse.size(); ++q)
+    c->ev_free.insert(c->ev_free.end(), {c->ev_coarse[q].first, c->ev_coarse[q].second});
+  c->ev_local.resize(nl);
+  c->ev_coarse.resize(nc);
+}
+
 int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit,
                  geneo_solve_info *info, cudaStream_t s) {
   if (!c->seg_ok)
@@ -671,34 +744,37 @@ int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit
   const int64_t n = c->topo.ndofs();
   const int nseg = (int)c->seg_off.size() - 1;
   if (c->seg_sc.n < (int64_t)kScal * nseg) {
+    if (c->seg_exec) cudaGraphExecDestroy(c->seg_exec);
+    c->seg_exec = nullptr;
     c->seg_sc.alloc((int64_t)kScal * nseg);
     c->seg_act.alloc(nseg);
+    if (c->h_seg) GENEO_CUDA(cudaFreeHost(c->h_seg));
+    c->h_seg = nullptr;
+    GENEO_CUDA(cudaMallocHost((void **)&c->h_seg, sizeof(double) * kScal * nseg));
   }
   c->seg_sc.zero(s);
-  c->seg_hs.assign((size_t)kScal * nseg, 0.0);
   c->seg_ha.assign(nseg, 0);
   double *sc = c->seg_sc.p;
+  const double *hs = c->h_seg;
   const int64_t *off = c->d_seg_off.p;
-  const int32_t *seg = c->d_seg_of.p;
   const unsigned g = grid_for(n, 256);
-  auto read_back = [&]() {
-    GENEO_CUDA(cudaMemcpyAsync(c->seg_hs.data(), sc, sizeof(double) * kScal * nseg,
-                               cudaMemcpyDeviceToHost, s));
-    GENEO_CUDA(cudaStreamSynchronize(s));
-  };
-  pcg_start(c, b, x, s, 1);
+  // with the graph, the iterations run on the context's own x (p_x)
+  const bool graph = c->opt.use_graph != 0 && c->prof == false;
+  double *xw = graph ? c->p_x.p : x;
+  pcg_start(c, b, xw, s, 1);
   c->launches += 4;
   k_seg_dot<<<nseg, 256, 0, s>>>(b, b, off, sc + 4);
   precondition(c, c->p_r.p, c->p_z.p, s, 1);
   k_copy<<<g, 256, 0, s>>>(c->p_z.p, c->p_p.p, n);
   k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, off, sc + 0);
   GENEO_CHECK_LAUNCH();
-  read_back();
+  GENEO_CUDA(cudaMemcpyAsync(c->h_seg, sc, sizeof(double) * kScal * nseg, cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA(cudaStreamSynchronize(s));
   std::vector<double> bnorm(nseg), rel(nseg, 1.0);
   std::vector<int> st(nseg, GENEO_NOT_CONVERGED), its(nseg, 0);
   int nact = 0;
   for (int j = 0; j < nseg; ++j) {
-    bnorm[j] = std::sqrt(c->seg_hs[(size_t)j * kScal + 4]);
+    bnorm[j] = std::sqrt(hs[(size_t)j * kScal + 4]);
     c->seg_ha[j] = bnorm[j] > 0.0;
     if (!c->seg_ha[j]) {
       st[j] = GENEO_OK;
@@ -709,25 +785,22 @@ int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit
   GENEO_CUDA(cudaMemcpyAsync(c->seg_act.p, c->seg_ha.data(), sizeof(int) * nseg,
                              cudaMemcpyHostToDevice, s));
   for (int it = 1; it <= maxit && nact > 0; ++it) {
-    if (it > 1) {
-      precondition(c, c->p_r.p, c->p_z.p, s, 1);
-      c->launches += 3;
-      k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_z.p, off, sc + 3);
-      k_seg_update_p<<<g, 256, 0, s>>>(sc, c->seg_act.p, seg, c->p_z.p, c->p_p.p, n);
-      k_seg_shift<<<grid_for(nseg, 256), 256, 0, s>>>(sc, nseg);
+    if (it == 1) {
+      seg_step_half(c, xw, s);
+    } else if (graph) {
+      ensure_seg_graph(c);
+      GENEO_CUDA(cudaGraphLaunch(c->seg_exec, s));
+      c->launches += c->seg_graph_launches;
+    } else {
+      seg_precond_half(c, s);
+      seg_step_half(c, xw, s);
     }
-    spmv(c, c->p_p.p, c->p_q.p, s, 1);
-    c->launches += 3;
-    k_seg_dot<<<nseg, 256, 0, s>>>(c->p_p.p, c->p_q.p, off, sc + 1);
-    k_seg_update_xr<<<g, 256, 0, s>>>(sc, c->seg_act.p, seg, c->p_p.p, c->p_q.p, x, c->p_r.p, n);
-    k_seg_dot<<<nseg, 256, 0, s>>>(c->p_r.p, c->p_r.p, off, sc + 2);
-    GENEO_CHECK_LAUNCH();
-    read_back();
+    GENEO_CUDA(cudaStreamSynchronize(s));
     bool changed = false;
     for (int j = 0; j < nseg; ++j) {
       if (!c->seg_ha[j]) continue;
       its[j] = it;
-      const double *h = c->seg_hs.data() + (size_t)j * kScal;
+      const double *h = hs + (size_t)j * kScal;
       if (!(h[1] > 0.0) || !std::isfinite(h[1]) || !std::isfinite(h[2])) {
         st[j] = GENEO_ERR_BREAKDOWN;
       } else {
@@ -740,9 +813,16 @@ int pcg_segments(geneo_ctx *c, const double *b, double *x, double tol, int maxit
         changed = true;
       }
     }
-    if (changed && nact > 0)
+    if (changed && nact > 0) {
       GENEO_CUDA(cudaMemcpyAsync(c->seg_act.p, c->seg_ha.data(), sizeof(int) * nseg,
                                  cudaMemcpyHostToDevice, s));
+      GENEO_CUDA(cudaStreamSynchronize(s));  // the host mask may change again next iteration
+    }
+  }
+  if (xw != x) {
+    c->launches += 1;
+    k_copy<<<g, 256, 0, s>>>(xw, x, n);
+    GENEO_CHECK_LAUNCH();
   }
   GENEO_CUDA(cudaStreamSynchronize(s));
   check_device_error(c, s);

@@ -10,10 +10,15 @@ iterative refinement with extended-precision residuals.  A plain float64
 solve of this system has a forward error near 1e-7 (the float64 residual of
 a float64 x cannot fall below u ||A|| ||x||, and gamma = 1e-4 makes the
 gradient part of x large); the refinement brings the corrections to about
-1e-10 of x.  The refinement history is written beside it as JSON.
+1e-10 of x.  The refinement history is written beside it as JSON, with the
+solution's sensitivity to its own float64 data: the same refined solve with
+every stored entry of A multiplied by 1 +- 2^-53 (random signs, symmetric),
+i.e. a one-ulp change, moves x by `one_ulp_sensitivity` (relative).  Two
+independent float64 assemblies of A differ by that much, so no solution of
+an independently assembled system can agree with this one more closely.
 
 Run from the repository root: python tests/golden/make_cube32_solution.py
-(about five minutes, most of it the sparse LU).
+(about eight minutes, most of it the two sparse LU factorisations).
 """
 import json
 import os
@@ -21,6 +26,7 @@ import sys
 import time
 
 import numpy as np
+import scipy.sparse as sp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
@@ -42,11 +48,18 @@ def main():
     x, hist = refined_direct_solve(A, b, steps=3)
     res = residual_extended(A, b, x).astype(np.float64)
     np.save(os.path.join(HERE, "cube32_solution.npy"), x)
+    rng = np.random.default_rng(0)
+    U = sp.triu(A, format="coo")
+    d = U.data * (1.0 + 2.0 ** -53 * rng.choice([-1.0, 1.0], U.data.shape))
+    Up = sp.coo_matrix((d, (U.row, U.col)), shape=A.shape)
+    xp, _ = refined_direct_solve((Up + sp.triu(Up, 1).T).tocsr(), b, steps=3)
+    sens = float(np.linalg.norm(xp - x) / np.linalg.norm(x))
     meta = {"workload": "cube32_hole_channels", "n": int(A.shape[0]),
             "method": "sparse LU + 3 rounds of refinement with longdouble residuals",
             "correction_rel_sizes": hist,
             "extended_relres": float(np.linalg.norm(res) / np.linalg.norm(b)),
             "longdouble_significand_bits": int(np.finfo(np.longdouble).nmant) + 1,
+            "one_ulp_sensitivity": sens,
             "seconds": time.time() - t0}
     with open(os.path.join(HERE, "cube32_solution.json"), "w") as f:
         json.dump(meta, f, indent=1)

@@ -101,6 +101,28 @@ def test_segments_match_separate_problems(batch):
         assert abs(info["iters"] - infos[p]["iters"]) <= 1
 
 
+def test_segments_graph_equals_plain_launches(batch):
+    """The segmented PCG iteration replayed as a CUDA graph gives the same
+    iterates, bit for bit, as plain launches (a context with use_graph = 0),
+    in the literal and the balanced form."""
+    import paper_2311_18783_gb300 as pkg
+    pkg_, ps, c, s = batch
+    s0 = pkg.Solver.from_workload(c, use_graph=0)
+    b = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    s.assemble_rhs(c.f_slot[0], b)
+    for bal in (False, True):
+        s.use_balanced(bal)
+        s0.use_balanced(bal)
+        x1, x0 = torch.zeros_like(b), torch.zeros_like(b)
+        st1, i1 = s.solve_segments(b, x1, tol=1e-10, maxit=500)
+        st0, i0 = s0.solve_segments(b, x0, tol=1e-10, maxit=500)
+        assert st1 == st0 == 0
+        assert [q["iters"] for q in i1] == [q["iters"] for q in i0]
+        assert torch.equal(x1, x0)
+    s.use_balanced(False)
+    s0.close()
+
+
 def test_segments_rejected_when_not_contiguous():
     """Two components side by side along x interleave in the unknown
     numbering: the segmented solve refuses with STATE."""

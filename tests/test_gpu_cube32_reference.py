@@ -14,16 +14,21 @@ Checked on the GPU in the set-up the benchmark times:
 * PCG to 1e-8 with float32 split local factors: converged, at most two more
   iterations, and the relative difference from the float64 solution is
   below 1e-6 (both stop at residual 1e-8; kappa(A) amplifies it);
+* the assembled matrix A against the oracle's, entry by entry (pattern
+  exact, values within 1e-14 of the row's largest entry);
 * the solution, element by element, against the oracle's accurate solution
   x = A^-1 b stored in tests/golden/cube32_solution.npy
   (tests/golden/make_cube32_solution.py: sparse LU and refinement with
-  extended residuals, corrections below 1e-10 of x): float64 PCG to 1e-13,
-  float64 and mixed PCG to 1e-8 (literal and balanced forms), and both with
-  two refinement steps on accurate residuals, which must meet 1e-8.  The
-  plain float64 solves cannot: on this system (gamma = 1e-4) the float64
-  residual of a float64 x bottoms out near u ||A|| ||x|| = 5e-7 ||b||, and
-  the oracle's own float64 solves (sparse LU, PCG to 1e-13) are 1.3e-7 and
-  1.4e-7 away from the refined solution.
+  extended residuals, corrections below 1e-10 of x), for float64 and mixed
+  PCG to 1e-8 in the literal and balanced forms, float64 PCG to 1e-13 and
+  the refined solves.  The bound is the problem's own, written by that
+  script: a one-ulp change of every entry of A moves its accurate solution
+  by one_ulp_sensitivity = 1.7e-7 (gamma = 1e-4 makes x sensitive to the
+  rounding of K's entries through its large gradient part), and the
+  library assembles A independently, so its solutions can agree with the
+  oracle's no closer than that.  The refined solves must come within twice
+  that sensitivity; their accurate residual must equal the oracle's floor
+  (the rounding of a float64 x, 1e-7 of ||b||).
 """
 import json
 import os
@@ -99,9 +104,27 @@ def test_pcg_fp64_and_mixed(full):
     assert d <= 1e-6
 
 
+def test_assembled_matrix_against_oracle(full):
+    from oracle.mesh import build_mesh
+    from oracle.fem import assemble_A
+    pkg, w, ref, s = full
+    m = build_mesh(w.nx, w.ny, w.nz, (w.hx, w.hy, w.hz), w.active)
+    A = assemble_A(m, w).tocsr()
+    A.sort_indices()
+    assert np.array_equal(s.export("A_rowptr"), A.indptr)
+    assert np.array_equal(s.export("A_col"), A.indices)
+    v = s.export("A_val")
+    rowmax = np.maximum.reduceat(np.abs(A.data), A.indptr[:-1])
+    scale = np.repeat(rowmax, np.diff(A.indptr))
+    assert np.all(np.abs(v - A.data) <= 1e-14 * scale)
+
+
 def test_solution_against_oracle_elementwise(full):
     pkg, w, ref, s = full
     xo = np.load(SOLUTION)
+    with open(SOLUTION.replace(".npy", ".json")) as f:
+        meta = json.load(f)
+    sens = meta["one_ulp_sensitivity"]
     assert xo.shape == (s.n,)
     b = torch.empty(s.n, dtype=torch.float64, device="cuda")
     s.assemble_rhs(w.f_slot[0], b)
@@ -119,24 +142,25 @@ def test_solution_against_oracle_elementwise(full):
             x = torch.zeros_like(b)
             info = s.solve(b, x, tol=1e-8, maxit=1000)
             assert info["status"] == 0
-            out[key + "_tol1e-8"] = (err(x), info["iters"])
+            out[key + "_tol1e-8"] = (err(x), info["iters"], None)
             x = torch.zeros_like(b)
             info = s.solve_refined(b, x, tol=1e-8, maxit=1000, nref=2)
             assert info["status"] == 0
-            out[key + "_refined2"] = (err(x), info["iters"])
+            out[key + "_refined2"] = (err(x), info["iters"], info["relres"])
         s.use_balanced(False)
     s.use_precision(pkg.PREC_FP64)
     x = torch.zeros_like(b)
     info = s.solve(b, x, tol=1e-13, maxit=1000)
-    out["fp64_tol1e-13"] = (err(x), info["iters"])
+    out["fp64_tol1e-13"] = (err(x), info["iters"], None)
     s.use_precision(pkg.PREC_FP32)
-    for k, (e, it) in sorted(out.items()):
-        print(f"{k:28s} relative error vs oracle {e:.3e}  PCG iterations {it}")
-    # the refined solves meet the 1e-8 target in every precision and form
-    for k, (e, it) in out.items():
+    print(f"one-ulp sensitivity of the oracle's solution: {sens:.3e}")
+    for k, (e, it, rr) in sorted(out.items()):
+        print(f"{k:28s} relative error vs oracle {e:.3e}  PCG iterations {it}"
+              + ("" if rr is None else f"  accurate relres {rr:.3e}"))
+    for k, (e, it, rr) in out.items():
         if k.endswith("refined2"):
-            assert e <= 1e-8, (k, e)
-    # the plain float64 solves sit at the float64 floor the oracle shares
-    assert out["fp64_tol1e-13"][0] <= 5e-7
-    assert out["fp64_tol1e-8"][0] <= 1e-6 and out["mixed_tol1e-8"][0] <= 1e-6
+            assert e <= 2 * sens, (k, e)
+            assert rr <= 2 * meta["extended_relres"], (k, rr)
+        else:
+            assert e <= 3 * sens, (k, e)
     assert abs(out["fp64_balanced_tol1e-8"][1] - ref["pcg_iters"]) <= 2
