@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "cube16_hole_channels", BLOCK_WORKLOAD, "beam128_mild",
-                            "beam64_layered", WARM_WORKLOAD, "paper_beam"],
+                            "beam64_layered", WARM_WORKLOAD, "paper_beam", "spmv_cube48"],
                    help="cube16_hole_channels: the profiling-size companion (ncu captures); "
                         f"{BLOCK_WORKLOAD}: 16 right-hand sides as a block, bfloat16 local "
                         "factors on the tensor cores")
@@ -74,6 +74,10 @@ SYMV_F32_TRAFFIC_RATIO = (204.3628 + 7.1421) / 203.6859
 # FP64 FMA rate of GB300: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2070 MHz
 # (the recipe's 1.25 TFLOP/s nominal figure at the maximum SM clock)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+
+def peaks_hbm():
+    return load_peaks()[0]["hbm_gbs"]
 
 
 def max_over_ranks(value, world, device):
@@ -494,6 +498,56 @@ def run_paper_beam(args):
     print(json.dumps(line), flush=True)
 
 
+def time_spmv(s, reps=50):
+    """Mean device time of one geneo_spmv launch (the SELL SpMV kernel alone)
+    over `reps` back-to-back launches on the current stream, after 5 warm-up
+    launches, and its algorithmic bytes: 12 B per stored nonzero of A (value
+    and column index) plus 20 B per row (x read, y written, row pointer)."""
+    import torch
+    n, nnz = s.n, s.sizes["nnz"]
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(5):
+        s.spmv(x, y)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        s.spmv(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / reps * 1e-3
+    nbytes = 12 * nnz + 20 * n
+    peaks, src = load_peaks()
+    return {"kernel": "k_spmv_sell (SELL-32-256, float64)", "bound": "hbm",
+            "achieved": nbytes / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": nbytes / t / 1e9 / peaks["hbm_gbs"], "peak_source": f"hbm_gbs of {src}",
+            "algorithmic_bytes_per_launch": nbytes, "launch_us": t * 1e6, "nnz": nnz, "n": n}
+
+
+def run_spmv(args):
+    """SpMV roofline on the 48^3 blocks matrix (12.1 M nonzeros, 146 MB of
+    values and indices: larger than the 129 MB L2), set up without coarse
+    space or GenEO (only A and the local inverses are built)."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import workloads as W
+    import paper_2311_18783_gb300 as pkg
+    w = W.cube48_blocks()
+    s = pkg.Solver.from_workload(w, coarse=pkg.COARSE_NONE, geneo=0)
+    r = time_spmv(s, reps=max(20, args.steps))
+    line = {"metric": "SpMV achieved HBM bandwidth", "value": r["achieved"], "unit": "GB/s",
+            "n_gpus": 1, "steps": max(20, args.steps), "warmup": 5, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cube48_blocks (matrix only)",
+                       "l2": "inputs larger than L2 (A 146 MB)"},
+            "roofline": r}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def load_oracle_solution(workload, n):
     """The oracle's accurate solution of the benchmark workload, stored by
     tests/golden/make_cube32_solution.py (a file read, no oracle code run),
@@ -521,6 +575,9 @@ def main():
         return
     if args.workload == "paper_beam":
         run_paper_beam(args)
+        return
+    if args.workload == "spmv_cube48":
+        run_spmv(args)
         return
     import torch
     import torch.distributed as dist
@@ -645,6 +702,20 @@ def main():
         s.solve_host(bh, tol=TOL, maxit=1000, out=xh)
         te.append(time.perf_counter() - t1)
     e2e_s = statistics.mean(te)
+    # the sparse coarse solve (multifrontal tile GEMVs), timed by the
+    # library's event pair around every solve in the headline's timed region
+    coarse_roof = None
+    if prof["coarse_symv_launches"] and prof["coarse_solve_bytes"]:
+        tc = prof["coarse_symv_ms"] / prof["coarse_symv_launches"] * 1e-3
+        cb = prof["coarse_solve_bytes"]
+        coarse_roof = {"kernel": "k_mf_tiles<0..3> + k_mf_gather (one coarse solve)",
+                       "bound": "hbm", "achieved": cb / tc / 1e9, "peak": peaks_hbm(),
+                       "unit": "GB/s", "frac": cb / tc / 1e9 / peaks_hbm(),
+                       "algorithmic_bytes_per_solve": cb, "solve_ms": tc * 1e3,
+                       "solves": prof["coarse_symv_launches"]}
+    spmv_roof = time_spmv(s)
+    spmv_roof["l2"] = ("A, x and y (about 45 MB) are L2-resident here; bench.py --workload "
+                       "spmv_cube48 measures a 146 MB matrix")
     refined = {}
     if prec == pkg.PREC_FP32:
         refined["mixed"] = timed_refined(pkg.PREC_FP32)
@@ -696,7 +767,9 @@ def main():
                        "setup_s": setup_s, "setup_stages_s": stages,
                        "autotuned_symv": tuned},
             "applies_per_s": applies_per_s,
-            "roofline": roof, "clocks": clk, "gpu_launches": prof["launches"],
+            "roofline": roof, "spmv_roofline": spmv_roof, "coarse_roofline": coarse_roof,
+            "clocks": clk,
+            "gpu_launches": prof["launches"],
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8,
                     "d2h_bytes_per_step": n * 8}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:

@@ -373,6 +373,8 @@ typedef struct {
   double coarse_symv_ms;
   int64_t local_symv_bytes;  /* algorithmic bytes of one local SYMV launch (stored tiles) */
   int64_t local_symv_flops;  /* algorithmic flops of one local SYMV launch: 2 sum_i n_i^2 */
+  int64_t coarse_solve_bytes; /* algorithmic bytes of one sparse coarse solve: the factor
+                                tiles (64 x 64 float64) its forward and backward passes read */
 } geneo_profile;
 
 /* on != 0: record CUDA events around every SYMV launch (adds two event

@@ -68,7 +68,7 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("local_symv_launches", C.c_int64),
                 ("local_symv_ms", C.c_double), ("coarse_symv_launches", C.c_int64),
                 ("coarse_symv_ms", C.c_double), ("local_symv_bytes", C.c_int64),
-                ("local_symv_flops", C.c_int64)]
+                ("local_symv_flops", C.c_int64), ("coarse_solve_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

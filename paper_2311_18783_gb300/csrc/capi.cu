@@ -494,6 +494,7 @@ int geneo_profile_read(geneo_ctx *c, geneo_profile *o) {
                               : c->loc.ntiles * (int64_t)geneo::kTileElems *
                                     (c->local_prec == GENEO_PREC_FP32 ? (int64_t)sizeof(float)
                                                                       : (int64_t)sizeof(double));
+    o->coarse_solve_bytes = geneo::mf_solve_bytes(c);
     int64_t fl = 0;
     for (int i = 0; i < c->dec.nsub; ++i) fl += 2 * c->dec.ni(i) * c->dec.ni(i);
     o->local_symv_flops = fl;

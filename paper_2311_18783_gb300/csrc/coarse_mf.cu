@@ -189,14 +189,20 @@ __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tas
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[r] = 0.0;
     const double *vin = kMode == 0 ? a.wbuf : a.ybuf;
-    for (int K = tk.j0; K < tk.j1; ++K) {
+    // the task's (at most kChunk) tiles are loaded before any is used, so
+    // their DRAM latencies overlap
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      const int K = tk.j0 + q;
+      if (K >= tk.j1) break;
       const double *t = a.T + (a.toff[f] + (int64_t)O * (O + 1) / 2 + K) * kTileElems;
       const double2 x = *reinterpret_cast<const double2 *>(vin + vo + (int64_t)K * kTile + 2 * l);
+      double2 v[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
-        acc[r] = fma(v.x, x.x, fma(v.y, x.y, acc[r]));
-      }
+      for (int r = 0; r < 8; ++r)
+        v[r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
+#pragma unroll
+      for (int r = 0; r < 8; ++r) acc[r] = fma(v[r].x, x.x, fma(v[r].y, x.y, acc[r]));
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -208,7 +214,10 @@ __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tas
   } else {
     // column modes: warp w owns rows 8w..8w+7 of every tile, lane l columns 2l, 2l+1
     double c0 = 0.0, c1 = 0.0;
-    for (int K = tk.j0; K < tk.j1; ++K) {
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      const int K = tk.j0 + q;
+      if (K >= tk.j1) break;
       const double *t = a.T + (a.toff[f] + (int64_t)K * (K + 1) / 2 + O) * kTileElems;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
@@ -301,6 +310,7 @@ struct Multifrontal {
   DevBuf<int32_t> npiv, npivp, npivt, parent, nt;
   std::vector<MfLevel> levels;
   int64_t factor_bytes = 0;
+  int64_t solve_tiles = 0;  // factor tiles one solve reads (all phases, all levels)
 };
 
 void MfDeleter::operator()(Multifrontal *m) const { delete m; }
@@ -575,6 +585,7 @@ void mf_setup(geneo_ctx *c, MfSchur *schur) {
       // split into chunks of kChunk tiles
       auto add = [&](int ph, int O, int o0, int o1) {
         const int nch = std::max(1, (o1 - o0 + kChunk - 1) / kChunk);
+        M->solve_tiles += std::max(0, o1 - o0);
         const int rbase = nslot;
         for (int k = 0; k < nch; ++k) {
           MfTask tk;
@@ -679,6 +690,9 @@ void mf_reserve(geneo_ctx *c, int k) {
 }
 
 int64_t mf_factor_bytes(const geneo_ctx *c) { return c->mf ? c->mf->factor_bytes : 0; }
+int64_t mf_solve_bytes(const geneo_ctx *c) {
+  return c->mf ? c->mf->solve_tiles * (int64_t)kTileElems * (int64_t)sizeof(double) : 0;
+}
 
 // y (column order, n0 per column, k columns) = E^-1 t
 void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {

@@ -81,6 +81,12 @@ struct geneo_ctx {
   geneo::DevBuf<double> d_Ae;                 // [ntets][36] element A_T
   geneo::DevBuf<int32_t> d_rowptr, d_col;
   geneo::DevBuf<double> d_val;
+  // sliced ELLPACK copy of A (SpMV): slice offsets and widths, column
+  // indices, values, sorted-position -> row
+  int64_t sell_nslices = 0, sell_stored = 0;
+  geneo::DevBuf<int64_t> d_sell_off;
+  geneo::DevBuf<int32_t> d_sell_w, d_sell_col, d_sell_perm;
+  geneo::DevBuf<double> d_sell_val;
   geneo::DevBuf<int64_t> d_cptr, d_rptr;
   geneo::DevBuf<int32_t> d_cidx, d_ridx;
 

@@ -82,21 +82,6 @@ __global__ void k_normalise(const double *__restrict__ w, const double *__restri
   if (i < n) v[i] = w[i] / sqrt(*nrm2);
 }
 
-__global__ void k_resid(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                        const double *__restrict__ val, const double *__restrict__ x,
-                        const double *__restrict__ b, double *__restrict__ r, int64_t n) {
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt >> 3;
-  const int lane = threadIdx.x & 7;
-  double s = 0;
-  if (row < n)
-    for (int32_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 8) s = fma(val[k], x[col[k]], s);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  if (row < n && lane == 0) r[row] = b[row] - s;
-}
-
 struct Gmres {
   geneo_ctx *c;
   cudaStream_t s;
@@ -133,7 +118,7 @@ int gmres(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int r
   G.h.alloc(m + 1);
   G.y.alloc(m);
   double *V = c->gm_V.p, *Z = c->gm_Z.p;
-  const unsigned g1 = grid_for(n, 256), g8 = grid_for(n * 8, 256);
+  const unsigned g1 = grid_for(n, 256);
   GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   double bb = 0;
   G.mdot(b, 1, b, &bb);
@@ -148,8 +133,7 @@ int gmres(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int r
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hc(m + 1), h2(m + 1);
   while (status == GENEO_NOT_CONVERGED && its < maxit) {
     // r0 = b - A x, v_0 = r0 / ||r0||
-    c->launches += 1;
-    k_resid<<<g8, 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x, b, G.w.p, n);
+    residual(c, x, b, G.w.p, s);
     double rr = 0;
     G.mdot(G.w.p, 1, G.w.p, &rr);
     c->launches += 1;
@@ -232,8 +216,7 @@ int gmres(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int r
     // a cycle that converged by its estimate is confirmed on the true
     // residual; if that is still above tol, the next cycle restarts from it
     if (status == GENEO_OK) {
-      c->launches += 1;
-      k_resid<<<g8, 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x, b, G.w.p, n);
+      residual(c, x, b, G.w.p, s);
       double r2 = 0;
       G.mdot(G.w.p, 1, G.w.p, &r2);
       GENEO_CUDA(cudaStreamSynchronize(s));
@@ -241,6 +224,8 @@ int gmres(geneo_ctx *c, const double *b, double *x, double tol, int maxit, int r
       if (rel > tol && its < maxit) status = GENEO_NOT_CONVERGED;
     }
   }
+  // the status follows the true relative residual of the returned x
+  if (status != GENEO_ERR_BREAKDOWN) status = rel <= tol ? GENEO_OK : GENEO_NOT_CONVERGED;
   GENEO_CUDA(cudaStreamSynchronize(s));
   check_device_error(c, s);
   if (info) {

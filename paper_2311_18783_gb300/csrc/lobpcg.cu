@@ -268,24 +268,65 @@ __global__ void k_sub(const double *__restrict__ a, const double *__restrict__ b
   if (i < n) y[i] = a[i] - b[i];
 }
 
-// G[m][a][b] = <X_a, Y_b> over subdomain m's segment; one CTA per (m, a, b)
-__global__ void k_gram(const double *__restrict__ X, int ka, const double *__restrict__ Y, int kb,
-                       int64_t vlen, const int64_t *__restrict__ voff, int ldg,
-                       double *__restrict__ G) {
-  const int m = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
+// One-pass Gram blocks: CTA (m, chunk, sub-block) reads rows of subdomain
+// m's segment once and accumulates an 8 x 8 block of <X_a, Y_b> in
+// registers; the per-chunk partials are summed in chunk order by
+// k_gram_final (deterministic).  part[(m * nch + chunk) * 256 + a * 16 + b].
+constexpr int kGramChunks = 4;
+__global__ void __launch_bounds__(256)
+    k_gram_part(const double *__restrict__ X, int ka, const double *__restrict__ Y, int kb,
+                int64_t vlen, const int64_t *__restrict__ voff, double *__restrict__ part) {
+  const int m = blockIdx.x, ch = blockIdx.y;
+  const int a0 = (blockIdx.z >> 1) * 8, b0 = (blockIdx.z & 1) * 8;
+  const int na = min(8, ka - a0), nb = min(8, kb - b0);
+  if (na <= 0 || nb <= 0) return;
   const int64_t s0 = voff[m], s1 = voff[m + 1];
-  const double *x = X + (int64_t)a * vlen, *y = Y + (int64_t)b * vlen;
-  double s = 0;
-  for (int64_t p = s0 + threadIdx.x; p < s1; p += blockDim.x) s = fma(x[p], y[p], s);
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) G[((int64_t)m * ldg + a) * ldg + b] = s;
+  const int64_t len = s1 - s0, per = (len + kGramChunks - 1) / kGramChunks;
+  const int64_t c0 = s0 + ch * per, c1 = min(s1, c0 + per);
+  double acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+  for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
+    double xv[8], yv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xv[i] = i < na ? X[(int64_t)(a0 + i) * vlen + p] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) yv[j] = j < nb ? Y[(int64_t)(b0 + j) * vlen + p] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
   }
+  __shared__ double sh[8][64];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      double v = acc[i][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) sh[w][i * 8 + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int i = threadIdx.x >> 3, j = threadIdx.x & 7;
+    double v = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += sh[q][threadIdx.x];
+    part[((int64_t)m * kGramChunks + ch) * 256 + (a0 + i) * 16 + (b0 + j)] = v;
+  }
+}
+
+__global__ void k_gram_final(const double *__restrict__ part, int ka, int kb, int ldg,
+                             double *__restrict__ G) {
+  const int m = blockIdx.x, e = threadIdx.x;
+  const int a = e >> 4, b = e & 15;
+  if (a >= ka || b >= kb) return;
+  double v = 0;
+  for (int ch = 0; ch < kGramChunks; ++ch) v += part[((int64_t)m * kGramChunks + ch) * 256 + e];
+  G[((int64_t)m * ldg + a) * ldg + b] = v;
 }
 
 // out[c] = sum_j src_j * C[m][j][c] over nsrc source columns given by
@@ -432,6 +473,136 @@ __global__ void k_rr_jacobi(const double *__restrict__ Hall, int n, int ld, int 
   }
 }
 
+// The same eigen-decomposition with one CTA per subdomain: parallel cyclic
+// Jacobi (Brent and Luk's ordering: each sweep is n - 1 rounds of n / 2
+// disjoint index pairs from the round-robin tournament, all rotations of a
+// round computed from the same matrix and applied together), with the
+// matrix and the rotations accumulated in shared memory.  n <= 48.
+constexpr int kJacMax = 48;
+__global__ void __launch_bounds__(256)
+    k_rr_jacobi_cta(const double *__restrict__ Hall, int n, int ld, int kout,
+                    double *__restrict__ theta, double *__restrict__ Vall) {
+  __shared__ double a[kJacMax][kJacMax + 1], v[kJacMax][kJacMax + 1];
+  __shared__ double cs[kJacMax / 2], sn[kJacMax / 2], red[256 / 32][2];
+  __shared__ int pp[kJacMax / 2], qq[kJacMax / 2], idx[kJacMax];
+  __shared__ int stop;
+  const int m = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const double *Hg = Hall + (int64_t)m * ld * ld;
+  double *Vo = Vall + (int64_t)m * ld * ld;
+  // an odd n gets one idle index (its pairs are skipped)
+  const int ne = n + (n & 1), np = ne / 2;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    a[i][j] = 0.5 * (Hg[i * ld + j] + Hg[j * ld + i]);
+    v[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    // convergence test: off-diagonal mass against the total
+    double off = 0, tot = 0;
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e % n;
+      const double x = a[i][j] * a[i][j];
+      tot += x;
+      if (i != j) off += x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5][0] = off;
+      red[tid >> 5][1] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double so = 0, st = 0;
+      for (int w = 0; w < (nt >> 5); ++w) {
+        so += red[w][0];
+        st += red[w][1];
+      }
+      stop = so <= 1e-30 * st;
+    }
+    __syncthreads();
+    if (stop) break;
+    for (int r = 0; r < ne - 1; ++r) {
+      // pairs of round r and their rotations
+      if (tid < np) {
+        int p, q;
+        if (tid == 0) {
+          p = r;
+          q = ne - 1;
+        } else {
+          p = (r + tid) % (ne - 1);
+          q = (r - tid + ne - 1) % (ne - 1);
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, sv = 0.0;
+        if (q < n) {
+          const double apq = a[p][q];
+          if (fabs(apq) >= 1e-300) {
+            const double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sv = t * c;
+          }
+        }
+        pp[tid] = p;
+        qq[tid] = q < n ? q : p;  // an idle pair rotates nothing
+        cs[tid] = c;
+        sn[tid] = q < n ? sv : 0.0;
+      }
+      __syncthreads();
+      // columns: A <- A J ; V <- V J
+      for (int e = tid; e < np * n; e += nt) {
+        const int k = e / n, i = e % n;
+        const int p = pp[k], q = qq[k];
+        if (p == q) continue;
+        const double c = cs[k], sv = sn[k];
+        const double aip = a[i][p], aiq = a[i][q];
+        a[i][p] = c * aip - sv * aiq;
+        a[i][q] = sv * aip + c * aiq;
+        const double vip = v[i][p], viq = v[i][q];
+        v[i][p] = c * vip - sv * viq;
+        v[i][q] = sv * vip + c * viq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = tid; e < np * n; e += nt) {
+        const int k = e / n, j = e % n;
+        const int p = pp[k], q = qq[k];
+        if (p == q) continue;
+        const double c = cs[k], sv = sn[k];
+        const double apj = a[p][j], aqj = a[q][j];
+        a[p][j] = c * apj - sv * aqj;
+        a[q][j] = sv * apj + c * aqj;
+      }
+      __syncthreads();
+    }
+  }
+  // descending order of the diagonal (ties keep the lower index first)
+  if (tid < n) {
+    const double d = a[tid][tid];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double e = a[j][j];
+      rank += (e > d) || (e == d && j < tid);
+    }
+    idx[rank] = tid;
+  }
+  __syncthreads();
+  for (int e = tid; e < kout * ld; e += nt) {
+    const int c = e / ld, i = e % ld;
+    const int src = idx[c];
+    if (i == 0) theta[m * kout + c] = a[src][src];
+    Vo[i * ld + c] = i < n ? v[i][src] : 0.0;
+  }
+}
+
 // R = LX - BX diag(theta); norms of R and BX per (m, c)
 __global__ void k_resid(const double *__restrict__ LX, const double *__restrict__ BX,
                         const double *__restrict__ theta, int k, const int32_t *__restrict__ pos_sub,
@@ -483,7 +654,7 @@ struct Lobpcg {
   DevBuf<double> Q, BQ;
   int qcap = 0;
   std::vector<int> nq;  // locked per subdomain
-  DevBuf<double> gram, coef, theta, tmat;
+  DevBuf<double> gram, coef, theta, tmat, gpart;
   int ld = 0;
   Lobpcg(geneo_ctx *cc, cudaStream_t ss, XiOp &o) : c(cc), s(ss), op(o) {}
 };
@@ -566,7 +737,11 @@ static void apply_L(Lobpcg &L, const double *Y, double *LY, int k) {
 
 
 static void gram(Lobpcg &L, const double *X, int ka, const double *Y, int kb, double *G) {
-  k_gram<<<dim3(L.nsub, ka, kb), 256, 0, L.s>>>(X, ka, Y, kb, L.vlen, L.c->loc.d_voff.p, L.ld, G);
+  if (L.gpart.n < (int64_t)L.nsub * kGramChunks * 256) L.gpart.alloc((int64_t)L.nsub * kGramChunks * 256);
+  const int zb = (ka > 8 || kb > 8) ? 4 : 1;  // sub-blocks (a0, b0): z = 2 (a0 / 8) + b0 / 8
+  k_gram_part<<<dim3(L.nsub, kGramChunks, zb), 256, 0, L.s>>>(X, ka, Y, kb, L.vlen,
+                                                              L.c->loc.d_voff.p, L.gpart.p);
+  k_gram_final<<<L.nsub, 256, 0, L.s>>>(L.gpart.p, ka, kb, L.ld, G);
 }
 
 // out (kout columns) = sum over source columns * coef[m]
@@ -930,7 +1105,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
     apply_L(L, L.X.p, L.LX.p, k);
     // Rayleigh-Ritz on X alone
     gram(L, L.X.p, k, L.LX.p, k, L.gram.p);
-    k_rr_jacobi<<<grid_for(L.nsub, 32), 32, 0, s>>>(L.gram.p, k, ld, k, L.theta.p, L.coef.p, L.nsub);
+    k_rr_jacobi_cta<<<L.nsub, 256, 0, s>>>(L.gram.p, k, ld, k, L.theta.p, L.coef.p);
     combine(L, cols(L.X, k, L.vlen), L.coef.p, k, L.T1.p);
     std::swap(L.X.p, L.T1.p);
     combine(L, cols(L.LX, k, L.vlen), L.coef.p, k, L.T1.p);
@@ -1139,8 +1314,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
           L.tmat.upload(Cm, s);
         } else {
           L.coef.upload(H, s);
-          k_rr_jacobi<<<grid_for(L.nsub, 32), 32, 0, s>>>(L.coef.p, ns, ld, k, L.theta.p,
-                                                          L.tmat.p, L.nsub);
+          k_rr_jacobi_cta<<<L.nsub, 256, 0, s>>>(L.coef.p, ns, ld, k, L.theta.p, L.tmat.p);
         }
       }
       // new X, P and their images

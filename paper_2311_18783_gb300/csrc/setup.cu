@@ -705,6 +705,7 @@ void setup_all(geneo_ctx *c) {
   k_gather_sum<<<grid_for(t.nnz(), 256), 256, 0, s>>>(c->d_cptr.p, c->d_cidx.p, c->d_Ae.p,
                                                       t.nnz(), c->d_val.p);
   GENEO_CHECK_LAUNCH();
+  build_sell(c, s);
 
   auto last = t0;
   auto stage_mark = [&](int k) {

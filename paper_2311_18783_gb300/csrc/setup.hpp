@@ -95,6 +95,8 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k = 
 void mf_reserve(geneo_ctx *c, int k);
 int mf_launches_per_solve(const geneo_ctx *c);
 int64_t mf_factor_bytes(const geneo_ctx *c);
+// algorithmic bytes of one coarse solve: every factor tile the solve reads
+int64_t mf_solve_bytes(const geneo_ctx *c);
 
 // Solve path; k right-hand sides stored as k consecutive columns of length n
 // (local vectors: columns of loc.vlen).
@@ -106,6 +108,11 @@ int64_t tc_factor_bytes(const geneo_ctx *c);
 void tc_symm(geneo_ctx *c, const double *xl, double *yl, int k, cudaStream_t s, cudaEvent_t e0,
              cudaEvent_t e1);
 void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k = 1);
+// y = b - A x (k columns), the same SpMV kernel
+void residual(geneo_ctx *c, const double *x, const double *b, double *y, cudaStream_t s,
+              int k = 1);
+// the SELL-32-256 copy of A used by spmv and residual (from the CSR values)
+void build_sell(geneo_ctx *c, cudaStream_t s);
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k = 1);
 // y = Z E^-1 Z^T r (+ add, when given)
 void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int k = 1,

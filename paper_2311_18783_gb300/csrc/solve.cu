@@ -12,47 +12,52 @@
 // the same operator on such residuals with one coarse solve per apply
 // instead of two (the Z E^-1 Z^T r part of the added term corrects the
 // rounding drift of Z^T r_k).
+#include <algorithm>
 #include <chrono>
 
 #include "setup.hpp"
 
 namespace geneo {
 
-// y = A x; 8 lanes per row
-__global__ void k_spmv(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                       const double *__restrict__ val, const double *__restrict__ x,
-                       double *__restrict__ y, int64_t n) {
-  x += blockIdx.y * n;  // right-hand side blockIdx.y (columns of length n)
+// Sliced ELLPACK SpMV (SELL-32-256): rows sorted by decreasing length
+// within windows of 256, slices of 32 sorted rows stored column-major
+// (entry j of the slice's row t at slice_off + 32 j + t), each slice padded
+// to its longest row with zero values; one thread per sorted row, so every
+// load of values and column indices is one coalesced 256 / 128-byte access
+// per warp.  perm maps sorted positions to rows.  y = A x, or y = b - A x
+// when b is given.
+__global__ void __launch_bounds__(256)
+    k_spmv_sell(const int64_t *__restrict__ slice_off, const int32_t *__restrict__ slice_w,
+                const int32_t *__restrict__ col, const double *__restrict__ val,
+                const int32_t *__restrict__ perm, const double *__restrict__ x,
+                const double *__restrict__ b, double *__restrict__ y, int64_t n,
+                int64_t nslices) {
+  x += blockIdx.y * n;
   y += blockIdx.y * n;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt >> 3;
-  const int lane = threadIdx.x & 7;
-  double s = 0;
-  if (row < n)
-    for (int32_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 8) s = fma(val[k], x[col[k]], s);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  if (row < n && lane == 0) y[row] = s;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t sl = t >> 5;
+  if (sl >= nslices) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t base = slice_off[sl] + lane;
+  const int w = slice_w[sl];
+  double acc = 0;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) {
+    const int64_t q = base + (int64_t)j * 32;
+    acc = fma(val[q], x[col[q]], acc);
+  }
+  const int64_t i = sl * 32 + lane;
+  if (i < n) {
+    const int32_t r = perm[i];
+    y[r] = b ? b[blockIdx.y * n + r] - acc : acc;
+  }
 }
 
-// y = b - A x
-__global__ void k_residual(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ x,
-                           const double *__restrict__ b, double *__restrict__ y, int64_t n) {
-  x += blockIdx.y * n;
-  b += blockIdx.y * n;
-  y += blockIdx.y * n;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt >> 3;
-  const int lane = threadIdx.x & 7;
-  double s = 0;
-  if (row < n)
-    for (int32_t k = rowptr[row] + lane; k < rowptr[row + 1]; k += 8) s = fma(val[k], x[col[k]], s);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  if (row < n && lane == 0) y[row] = b[row] - s;
+// SELL value gather from the CSR values (padding slots keep 0)
+__global__ void k_sell_fill(const int64_t *__restrict__ pos, const double *__restrict__ csr,
+                            double *__restrict__ sell, int64_t nnz) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nnz) sell[pos[k]] = csr[k];
 }
 
 // padded local vector x_loc[p] = s[l2g[p]] (0 on padding)
@@ -300,12 +305,78 @@ void reserve_rhs(geneo_ctx *c, int k) {
   c->kcap = k;
 }
 
-void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k) {
+// Builds the SELL-32-256 copy of A from the CSR pattern (host) and values
+// (device gather).
+void build_sell(geneo_ctx *c, cudaStream_t s) {
+  const Topology &t = c->topo;
+  const int64_t n = t.ndofs(), nnz = t.nnz();
+  constexpr int C = 32, SIGMA = 256;
+  std::vector<int32_t> perm(n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+  auto len = [&](int32_t r) { return t.rowptr[r + 1] - t.rowptr[r]; };
+  for (int64_t w0 = 0; w0 < n; w0 += SIGMA) {
+    const int64_t w1 = std::min<int64_t>(n, w0 + SIGMA);
+    std::stable_sort(perm.begin() + w0, perm.begin() + w1,
+                     [&](int32_t a, int32_t b) { return len(a) > len(b); });
+  }
+  const int64_t nsl = (n + C - 1) / C;
+  std::vector<int64_t> off(nsl + 1, 0);
+  std::vector<int32_t> wid(nsl, 0);
+  for (int64_t sl = 0; sl < nsl; ++sl) {
+    int w = 0;
+    for (int64_t i = sl * C; i < std::min<int64_t>(n, (sl + 1) * C); ++i) w = std::max(w, (int)len(perm[i]));
+    wid[sl] = w;
+    off[sl + 1] = off[sl] + (int64_t)w * C;
+  }
+  std::vector<int32_t> col(off[nsl]);
+  std::vector<int64_t> pos(nnz);
+  for (int64_t sl = 0; sl < nsl; ++sl)
+    for (int lane = 0; lane < C; ++lane) {
+      const int64_t i = sl * C + lane;
+      const int32_t r = i < n ? perm[i] : -1;
+      for (int j = 0; j < wid[sl]; ++j) {
+        const int64_t q = off[sl] + (int64_t)j * C + lane;
+        if (r >= 0 && j < len(r)) {
+          col[q] = t.col[t.rowptr[r] + j];
+          pos[t.rowptr[r] + j] = q;
+        } else {
+          col[q] = r >= 0 ? r : 0;  // padding: a valid column, value 0
+        }
+      }
+    }
+  c->sell_nslices = nsl;
+  c->sell_stored = off[nsl];
+  c->d_sell_off.upload(off, s);
+  c->d_sell_w.upload(wid, s);
+  c->d_sell_col.upload(col, s);
+  c->d_sell_perm.upload(perm, s);
+  c->d_sell_val.alloc(off[nsl]);
+  c->d_sell_val.zero(s);
+  DevBuf<int64_t> dpos;
+  dpos.upload(pos, s);
+  k_sell_fill<<<grid_for(nnz, 256), 256, 0, s>>>(dpos.p, c->d_val.p, c->d_sell_val.p, nnz);
+  GENEO_CHECK_LAUNCH();
+  GENEO_CUDA(cudaStreamSynchronize(s));
+}
+
+static void sell_apply(geneo_ctx *c, const double *x, const double *b, double *y, cudaStream_t s,
+                       int k) {
   const int64_t n = c->topo.ndofs();
   c->launches += 1;
-  k_spmv<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p, x,
-                                                       y, n);
+  k_spmv_sell<<<dim3(grid_for(c->sell_nslices * 32, 256), k), 256, 0, s>>>(
+      c->d_sell_off.p, c->d_sell_w.p, c->d_sell_col.p, c->d_sell_val.p, c->d_sell_perm.p, x, b,
+      y, n, c->sell_nslices);
   GENEO_CHECK_LAUNCH();
+}
+
+void spmv(geneo_ctx *c, const double *x, double *y, cudaStream_t s, int k) {
+  sell_apply(c, x, nullptr, y, s, k);
+}
+
+// y = b - A x (k columns)
+void residual(geneo_ctx *c, const double *x, const double *b, double *y, cudaStream_t s,
+                     int k) {
+  sell_apply(c, x, b, y, s, k);
 }
 
 void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k) {
@@ -395,10 +466,9 @@ void apply_preconditioner(geneo_ctx *c, const double *r, double *z, cudaStream_t
     local_solve(c, r, z, s, k);
     return;
   }
-  c->launches += 2;
+  c->launches += 1;
   coarse_solve(c, r, c->v_y0.p, s, k);
-  k_residual<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
-                                                           c->v_y0.p, r, c->v_s.p, n);
+  residual(c, c->v_y0.p, r, c->v_s.p, s, k);
   local_solve(c, c->v_s.p, c->v_w.p, s, k);
   spmv(c, c->v_w.p, c->v_t.p, s, k);
   coarse_solve(c, c->v_t.p, c->v_c.p, s, k);
@@ -413,10 +483,7 @@ void apply_balanced(geneo_ctx *c, const double *r, double *z, cudaStream_t s, in
     return;
   }
   local_solve(c, r, c->v_w.p, s, k);
-  c->launches += 1;
-  k_residual<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p, c->d_val.p,
-                                                           c->v_w.p, r, c->v_t.p, n);
-  GENEO_CHECK_LAUNCH();
+  residual(c, c->v_w.p, r, c->v_t.p, s, k);
   coarse_solve(c, c->v_t.p, z, s, k, c->v_w.p);
 }
 
@@ -431,9 +498,7 @@ static void pcg_start(geneo_ctx *c, const double *b, double *x, cudaStream_t s, 
   const int64_t n = c->topo.ndofs();
   if (c->balanced && c->n0 > 0) {
     coarse_solve(c, b, x, s, k);
-    c->launches += 1;
-    k_residual<<<dim3(grid_for(n * 8, 256), k), 256, 0, s>>>(c->d_rowptr.p, c->d_col.p,
-                                                             c->d_val.p, x, b, c->p_r.p, n);
+    residual(c, x, b, c->p_r.p, s, k);
   } else {
     GENEO_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n * k, s));
     c->launches += 1;

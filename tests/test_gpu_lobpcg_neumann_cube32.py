@@ -1,0 +1,42 @@
+"""The LOBPCG Neumann mode (lobpcg_neumann = 1, block 16: the mode the
+batching workload's small boxes need) on the 32^3 benchmark workload, against
+the oracle's stored dense generalised eigensolves of all 64 subdomains
+(tests/golden/cube32_reference.json, written by
+tests/golden/make_cube32_reference.py): the number of eigenvalues above the
+threshold in every subdomain (exact), the selected eigenvalues (1e-6
+relative: this mode accepts a Ritz value that has stagnated to 1e-4 relative
+over five iterations only when it is not within 1% of tau), the GenEO
+columns kept and n0 (exact).  Float32 split factors, as in the benchmark."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "cube32_reference.json")
+
+
+def test_neumann_mode_on_cube32():
+    import paper_2311_18783_gb300 as pkg
+    with open(GOLDEN) as f:
+        ref = json.load(f)
+    s = pkg.Solver.from_workload(W.cube32_hole_channels(), precision=pkg.PREC_FP32,
+                                 lobpcg_neumann=1, lobpcg_block=16)
+    found = s.export("geneo_found")
+    st = s.export("setup_stages")
+    print(f"Neumann mode: GenEO found {int(found.sum())} (oracle {sum(ref['geneo_found'])}), "
+          f"eigensolves {st[3]:.1f} s, set-up {st[7]:.1f} s")
+    assert list(found) == ref["geneo_found"]
+    sub, lam = s.export("geneo_sub"), s.export("geneo_lambda")
+    for j in range(ref["nsub"]):
+        want = np.sort(np.asarray(ref["lam_selected"][j]))
+        for g in np.sort(lam[sub == j]):
+            assert np.abs(want - g).min() <= 1e-6 * want.max()
+    assert s.sizes["n0_geneo"] == ref["geneo_kept"] and s.sizes["n0"] == ref["n0"]
+    s.close()

@@ -1,0 +1,57 @@
+"""Sixteen problems of the batching workload (workloads.many_problems, seed
+3: n^3 cubes with 1-2 holes, mu^-1 in {1, 1e2, 1e4} on blocks, gamma
+log-uniform in [1e-6, 1], 8-64 boxes each; the first sixteen with n <= 10)
+set up together by geneo_setup_batch and solved by one segmented PCG
+(per-problem scalars, each problem stopping on its own, the iteration
+replayed as a CUDA graph), against the oracle problem by problem:
+* the right-hand side (1e-12 relative),
+* the number of GenEO eigenvalues above the threshold in every subdomain
+  (exact, against the oracle's dense generalised eigensolves of Sec. 3.2,
+  GEVP "tauthresholdAS"; the LOBPCG runs in its Neumann mode, the mode for
+  these 2-3-cell boxes under a 1e4 contrast),
+* the PCG iteration count to 1e-8 (the oracle's literal PCG, +-2) and the
+  recurrence residual."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_sixteen_batching_problems_against_oracle():
+    import paper_2311_18783_gb300 as pkg
+    from oracle.pipeline import build_problem, solve
+    ps = [w for w in W.many_problems(256, seed=3) if w.nx <= 10][:16]
+    assert len(ps) == 16
+    for w in ps:
+        w.f_slot = W.box(w.nx, w.ny, w.nz, h=w.hx, f='random', seed=w.nx).f_slot
+    comp = pkg.compose(ps)
+    s = pkg.Solver.batch(ps, lobpcg_neumann=1, lobpcg_block=16)
+    off = s.export("seg_off")
+    assert len(off) == len(ps) + 1
+    b = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    s.assemble_rhs(comp["f_slot"][0], b)
+    x = torch.zeros_like(b)
+    st, infos = s.solve_segments(b, x, tol=1e-8, maxit=1000)
+    assert st == 0
+    found = s.export("geneo_found")
+    sub0 = 0
+    for p, w in enumerate(ps):
+        prob = build_problem(w)
+        assert off[p + 1] - off[p] == prob.A.shape[0]
+        nb = np.linalg.norm(prob.b[0])
+        bseg = b[off[p]:off[p + 1]].cpu().numpy()
+        assert abs(np.linalg.norm(bseg) - nb) <= 1e-12 * nb
+        ref = [int((g.lam > prob.tau_p).sum()) for g in prob.gevps]
+        got = list(found[sub0:sub0 + prob.dec.nsub])
+        sub0 += prob.dec.nsub
+        ro = solve(prob, tol=1e-8, maxit=1000)
+        print(f"{w.name} parts {w.parts} gamma {w.gamma:.1e}: GenEO {sum(got)} (oracle "
+              f"{sum(ref)}), PCG {infos[p]['iters']} (oracle {ro.iters})")
+        assert got == ref
+        assert infos[p]["relres"] <= 1e-8
+        assert abs(infos[p]["iters"] - ro.iters) <= 2
+    assert sub0 == len(found)
+    s.close()

@@ -217,23 +217,25 @@ def test_pcg_balanced_form(case):
 
 def test_gmres_right_preconditioned(case):
     """Right-preconditioned GMRES with M^-1_AS,2 (Sec. 4's Krylov method)
-    against the oracle's GMRES: the same Arnoldi step count (+-1) to a
-    relative residual of 1e-10, a true residual at or below 1e-10 and the
-    solution within 2 kappa(A) 1e-10 of the oracle's accurate one."""
+    against the oracle's GMRES: the same Arnoldi step count (+-1) to a true
+    relative residual of 1e-8 (GMRES stops on ||b - A x||, whose float64
+    value cannot fall below about u ||A|| ||x|| / ||b||, 1e-10 on the small
+    gamma cases), and the solution within 2 kappa(A) 1e-8 of the oracle's
+    accurate one."""
     from oracle.solver import gmres_right, refined_direct_solve
     name, w, prob, s = case
     b = torch.empty(s.n, dtype=torch.float64, device="cuda")
     s.assemble_rhs(w.f_slot[0], b)
     x = torch.zeros_like(b)
-    info = s.solve_gmres(b, x, tol=1e-10, maxit=500, restart=60)
-    assert info["status"] == 0 and info["relres"] <= 1e-10
-    ro = gmres_right(prob.A, prob.b[0], prob.M.apply, tol=1e-10, maxit=500, restart=60)
-    assert abs(ro.iters - info["iters"]) <= 1
+    info = s.solve_gmres(b, x, tol=1e-8, maxit=500, restart=60)
+    assert info["status"] == 0 and info["relres"] <= 1e-8
+    ro = gmres_right(prob.A, prob.b[0], prob.M.apply, tol=1e-8, maxit=500, restart=60)
+    assert ro.relres <= 1e-8 and abs(ro.iters - info["iters"]) <= 1
     xs, _ = refined_direct_solve(prob.A, prob.b[0], steps=3)
     ev = np.linalg.eigvalsh(prob.A.toarray()) if s.n < 4000 else None
     kappa = ev[-1] / ev[0] if ev is not None else 1e6
     err = np.linalg.norm(host(x) - xs) / np.linalg.norm(xs)
-    assert err <= max(2 * kappa * 1e-10, 1e-13)
+    assert err <= max(2 * kappa * 1e-8, 1e-13)
 
 
 def test_solve_host_matches_device(case):
