@@ -80,7 +80,9 @@ extern "C" {
                                       eq. "eigGenEOClassis": D_j A_j D_j V = lambda A_j^Neu V,
                                       coarse vectors R_j^T D_j V; for comparison: it has many
                                       gradient-driven eigenvalues above the threshold, most of
-                                      them dependent on the split near-kernel columns */
+                                      them dependent on the split near-kernel columns; its
+                                      LOBPCG search directions use the inverse of
+                                      A_j^Neu + 1e-10 diag(A_j^Neu) */
 
 #define GENEO_TAU_RECIPROCAL 0     /* select lambda > 1/tau */
 #define GENEO_TAU_PAPER 1          /* select lambda > tau (GEVP "tauthresholdAS" literally) */

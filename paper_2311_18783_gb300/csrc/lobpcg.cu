@@ -1064,10 +1064,15 @@ void geneo_eigenvectors(geneo_ctx *c) {
   L.theta.alloc((int64_t)L.nsub * k);
   L.nq.assign(L.nsub, 0);
   grow_q(L, 16);
-  // search-direction operator: A_j^-1, or (A_j^Neu + 1e-10 diag)^-1 for lobpcg_neumann
+  // search-direction operator: A_j^-1, or (A_j^Neu + 1e-10 diag)^-1 for
+  // lobpcg_neumann and for the classical pencil (whose top eigenvectors carry
+  // large components on the dofs outside the partition of unity's support,
+  // where only B = A_j^Neu couples them: with A_j^-1 directions the
+  // residuals stall near 1e-2 while the Ritz values settle)
   const bool neu = c->opt.lobpcg_neumann != 0;
+  const bool neu_dir = neu || c->opt.geneo_pencil == GENEO_PENCIL_CLASSICAL;
   DevBuf<double> neu_inv;
-  if (neu) {
+  if (neu_dir) {
     neu_inv.alloc(tile_elems(c->loc));
     tiles_init_padding(c->loc, neu_inv.p, s);
     k_neumann_tiles<<<dim3(64, L.nsub), 256, 0, s>>>(L.op.Noff.p, L.op.lrp.p, L.op.lcol.p,
@@ -1079,7 +1084,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
     spd_invert(c->loc, neu_inv.p, ws.p, c->d_err.p, s);
     check_device_error(c, s);
   }
-  const double *Tdir = neu ? neu_inv.p : c->loc_f64.p;
+  const double *Tdir = neu_dir ? neu_inv.p : c->loc_f64.p;
   const double tau = c->tau_p, tol = c->opt.lobpcg_tol;
   std::vector<uint8_t> done(L.nsub, 0);
   std::vector<std::vector<double>> lam_locked(L.nsub);
