@@ -754,6 +754,10 @@ def main():
         fp64_side = v64
         variants["fp64_literal"], _, _ = timed_variant(pkg.PREC_FP64, False, side, 1)
         variants["mixed_literal"], _, _ = timed_variant(pkg.PREC_FP32, False, side, 1)
+        # S_j^-1 of the split's gradient part in float32 as well
+        s.use_gradient_precision(pkg.PREC_FP32)
+        variants["mixed_grad32_balanced"], _, _ = timed_variant(pkg.PREC_FP32, True, side, 1)
+        s.use_gradient_precision(pkg.PREC_FP64)
     # headline: balanced form with the precision asked for, clocks sampled
     s.use_precision(prec)
     s.use_balanced(True)

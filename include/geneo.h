@@ -285,6 +285,17 @@ int geneo_solve_gmres(geneo_ctx *ctx, const double *b_dev, double *x_dev, double
 int geneo_symv_config_count(int32_t precision);
 int geneo_use_symv_config(geneo_ctx *ctx, int32_t precision, int32_t index);
 
+/* Storage precision of S_j^-1 in the gradient part G_j S_j^-1 G_j^T of the
+ * split local inverse (Sec. 2, eq. "inverseBw"), used by the FP32 split
+ * solves: GENEO_PREC_FP64 (default) or GENEO_PREC_FP32 (S_j^-1 rounded to
+ * float32, float32 accumulation).  S_j^-1 is SPD and its rounding stays in
+ * range(G_j), so the split inverse stays SPD: on ker G_j^T it equals C_j,
+ * elsewhere the gradient part adds a PSD term.  STATE unless the split
+ * factors were built (options.precision FP32 or BF16).  The float64 shifted
+ * inverse (options.gradient_shift) always applies its gradient term in
+ * float64. */
+int geneo_use_gradient_precision(geneo_ctx *ctx, int32_t precision);
+
 /* on = 1 / 0: later PCG solves of the context use the balanced form / the
  * literal form (see geneo_options.balanced).  geneo_apply_preconditioner
  * always applies the literal M^-1_AS,2. */

@@ -94,6 +94,7 @@ _SIGS = {
     "geneo_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int32, C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_use_balanced": (C.c_int, [C.c_void_p, C.c_int32]),
+    "geneo_use_gradient_precision": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_symv_config_count": (C.c_int, [C.c_int32]),
     "geneo_use_symv_config": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "geneo_solve_gmres": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
@@ -415,6 +416,9 @@ class Solver:
     @staticmethod
     def symv_config_count(precision):
         return _check(load_library().geneo_symv_config_count(precision))
+
+    def use_gradient_precision(self, precision):
+        _check(_LIB.geneo_use_gradient_precision(self._ctx, precision))
 
     def use_balanced(self, on=True):
         _check(_LIB.geneo_use_balanced(self._ctx, 1 if on else 0))

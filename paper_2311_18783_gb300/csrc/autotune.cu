@@ -144,6 +144,8 @@ void autotune_symv(geneo_ctx *c) {
   if (c->loc_f64.p) tune_one<double>(c, "local", GENEO_PREC_FP64, c->loc, c->loc_f64.p);
   if (c->xi && c->xi->s_inv.p) tune_one<double>(c, "gradient", GENEO_PREC_FP64, c->xi->sb,
                                                 c->xi->s_inv.p);
+  if (c->xi && c->xi->s_inv32.p) tune_one<float>(c, "gradient", GENEO_PREC_FP32, c->xi->sb,
+                                                 c->xi->s_inv32.p);
 }
 
 void autotune_clear_cache() {

@@ -320,6 +320,20 @@ int geneo_use_symv_config(geneo_ctx *c, int32_t precision, int32_t index) {
   return GENEO_OK;
 }
 
+int geneo_use_gradient_precision(geneo_ctx *c, int32_t precision) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (precision == GENEO_PREC_FP64) {
+    c->grad32 = false;
+    return GENEO_OK;
+  }
+  if (precision != GENEO_PREC_FP32) return fail(GENEO_ERR_INVALID_ARG, "precision must be FP32 or FP64");
+  if (!c->xi || !c->xi->s_inv32.p)
+    return fail(GENEO_ERR_STATE, "the split factors (options.precision FP32 or BF16) were not built");
+  c->grad32 = true;
+  return GENEO_OK;
+}
+
 int geneo_use_balanced(geneo_ctx *c, int32_t on) {
   if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
   if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");

@@ -1447,6 +1447,9 @@ void build_split_factors(geneo_ctx *c) {
   op.u2.alloc(op.vlenS);
   op.u1.zero(s);
   op.u2.zero(s);
+  // S_j^-1 in float32 as well, for geneo_use_gradient_precision
+  op.s_inv32.alloc(tile_elems(op.sb));
+  tiles_cast_f32(op.sb, op.s_inv.p, op.s_inv32.p, s);
   GENEO_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1467,9 +1470,18 @@ void split_gradient_apply(geneo_ctx *c, const double *xl, double *yl, cudaStream
   k_gt<<<grid_for(op.nv * k, 256), 256, 0, s>>>(op.sptr.p, op.srow.p, op.ssgn.p, op.vslot_sub.p,
                                                 op.xvoff.p, c->loc.d_voff.p, op.sb.d_voff.p, op.nv,
                                                 k, op.vlen, op.vlenS, xl, op.u1.p);
-  for (int j = 0; j < k; ++j)
-    symv_batch<double>(op.sb, op.s_inv.p, op.u1.p + j * op.vlenS, op.u2.p + j * op.vlenS,
-                       c->d_err.p, s);
+  // S_j^-1 in float32 when selected (not with the shift's scale): S_j^-1 is
+  // SPD and its rounding stays inside range(G_j), so the split inverse stays
+  // SPD (x^T C_j x > 0 on ker G_j^T, and the gradient part is PSD)
+  const bool f32 = c->grad32 && op.s_inv32.p && !scale;
+  for (int j = 0; j < k; ++j) {
+    if (f32)
+      symv_batch<float>(op.sb, op.s_inv32.p, op.u1.p + j * op.vlenS, op.u2.p + j * op.vlenS,
+                        c->d_err.p, s);
+    else
+      symv_batch<double>(op.sb, op.s_inv.p, op.u1.p + j * op.vlenS, op.u2.p + j * op.vlenS,
+                         c->d_err.p, s);
+  }
   k_g<<<grid_for(op.nslots * k, 256), 256, 0, s>>>(op.ghead.p, op.gtail.p, op.slot_sub.p,
                                                    op.Noff.p, c->loc.d_voff.p, op.sb.d_voff.p,
                                                    op.nslots, k, op.vlen, op.vlenS, op.u2.p,

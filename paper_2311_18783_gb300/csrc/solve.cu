@@ -538,9 +538,9 @@ static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s, int k) {
 // context's capture stream, with x = p_x; replayed on the caller's stream for
 // every iteration after the first.
 static void ensure_pcg_graph(geneo_ctx *c, int k) {
-  const int cfg = c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1];
+  const int cfg = (c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1]) * 2 + (c->grad32 ? 1 : 0);
   const int key =
-      (((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 64 + cfg)) << 8) + k;
+      (((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 128 + cfg)) << 8) + k;
   if (c->pcg_exec && c->pcg_key == key) return;
   c->drop_graph();
   const int64_t l0 = c->launches;
@@ -760,8 +760,8 @@ static void seg_step_half(geneo_ctx *c, double *x, cudaStream_t s) {
 // [second half ; first half] of a segmented iteration on x = p_x, captured
 // once per local precision, profiling switch and form
 static void ensure_seg_graph(geneo_ctx *c) {
-  const int cfg = c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1];
-  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 64 + cfg;
+  const int cfg = (c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1]) * 2 + (c->grad32 ? 1 : 0);
+  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 128 + cfg;
   if (c->seg_exec && c->seg_key == key) return;
   if (c->seg_exec) cudaGraphExecDestroy(c->seg_exec);
   c->seg_exec = nullptr;

@@ -18,6 +18,7 @@ struct XiOp {
   DevBuf<double> aval, nval, dmask;
   TileBatch sb;
   DevBuf<double> s_inv;   // S_j^-1,   S_j = G_j^T A_j G_j
+  DevBuf<float> s_inv32;  // S_j^-1 rounded to float32 (split local solves, optional)
   DevBuf<double> sn_inv;  // S_Bj^-1,  S_Bj = G_j^T A_j^Neu G_j (same layout)
   // column-tetrahedron lists of the local gradient columns (Dirichlet: all
   // tetrahedra touching N_j; Neumann: those of Omega_j) and per-entry local

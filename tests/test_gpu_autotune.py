@@ -53,7 +53,7 @@ def test_autotune_records_and_cache(tmp_path):
     cache = str(tmp_path / "symv_tune.txt")
     s = pkg.Solver.from_workload(w, precision=pkg.PREC_FP32, autotune=1, autotune_cache=cache)
     rows = s.export("autotune").reshape(-1, 12)
-    assert len(rows) == 3  # local float32, local float64, S_j^-1 float64
+    assert len(rows) == 4  # local float32 and float64, S_j^-1 float64 and float32
     for row in rows:
         prec = int(row[1])
         ncand = pkg.Solver.symv_config_count(prec)

@@ -148,6 +148,16 @@ def test_solution_against_oracle_elementwise(full):
             assert info["status"] == 0
             out[key + "_refined2"] = (err(x), info["iters"], info["relres"])
         s.use_balanced(False)
+    # float32 split with S_j^-1 in float32 too, balanced form
+    s.use_precision(pkg.PREC_FP32)
+    s.use_gradient_precision(pkg.PREC_FP32)
+    s.use_balanced(True)
+    x = torch.zeros_like(b)
+    info = s.solve(b, x, tol=1e-8, maxit=1000)
+    assert info["status"] == 0 and info["iters"] <= ref["pcg_iters"] + 2
+    out["mixed_grad32_balanced_tol1e-8"] = (err(x), info["iters"], None)
+    s.use_gradient_precision(pkg.PREC_FP64)
+    s.use_balanced(False)
     s.use_precision(pkg.PREC_FP64)
     x = torch.zeros_like(b)
     info = s.solve(b, x, tol=1e-13, maxit=1000)

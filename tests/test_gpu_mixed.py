@@ -86,3 +86,38 @@ def test_mixed_pcg(mcase):
     ev = np.linalg.eigvalsh(prob.A.toarray())
     err = np.linalg.norm(host(x) - xs) / np.linalg.norm(xs)
     assert err <= max(2 * (ev[-1] / ev[0]) * 1e-10, 1e-12)
+
+
+def test_gradient_part_in_float32(mcase):
+    """S_j^-1 rounded to float32 as well (geneo_use_gradient_precision): the
+    split local solve against the oracle's local solve within the float32
+    storage error of C_j and S_j^-1 relative to the gradient part, the
+    split inverse stays SPD (PCG converges), and PCG keeps the float64
+    iteration count (+-2) and the solution bound of the float32 split."""
+    import paper_2311_18783_gb300 as pkg
+    from oracle.solver import direct_solve
+    from test_gpu_parity import _kappa_local, U
+    name, w, prob, s = mcase
+    s.use_precision(pkg.PREC_FP32)
+    s.use_gradient_precision(pkg.PREC_FP32)
+    try:
+        r = np.random.default_rng(31).standard_normal(s.n)
+        out = torch.empty(s.n, dtype=torch.float64, device="cuda")
+        s.local_solve(dev(r), out)
+        ref = prob.M.local(r)
+        err = np.abs(host(out) - ref).max() / np.abs(ref).max()
+        assert err <= 1e-5 + 1e3 * _kappa_local(prob) * U, err
+        b = torch.empty(s.n, dtype=torch.float64, device="cuda")
+        s.assemble_rhs(w.f_slot[0], b)
+        x = torch.zeros_like(b)
+        i32 = s.solve(b, x, tol=1e-10, maxit=500)
+        s.use_gradient_precision(pkg.PREC_FP64)
+        x64 = torch.zeros_like(b)
+        i64 = s.solve(b, x64, tol=1e-10, maxit=500)
+        assert i32["status"] == 0 and abs(i32["iters"] - i64["iters"]) <= 2
+        xs = direct_solve(prob.A, prob.b[0])
+        ev = np.linalg.eigvalsh(prob.A.toarray())
+        e = np.linalg.norm(host(x) - xs) / np.linalg.norm(xs)
+        assert e <= max(2 * (ev[-1] / ev[0]) * 1e-10, 1e-12)
+    finally:
+        s.use_gradient_precision(pkg.PREC_FP64)
