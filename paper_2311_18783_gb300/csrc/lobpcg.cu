@@ -1240,10 +1240,20 @@ void geneo_eigenvectors(geneo_ctx *c) {
       bool all = true;
       for (int m = 0; m < L.nsub; ++m) all &= finished[m] != 0;
       if (all) break;
-      // W = T R (explicit local inverse), B-orthogonal to Q and X, B-orthonormal
+      // W = T R (explicit local inverse), B-orthogonal to Q and X, B-orthonormal.
+      // For the filtered pencil with the float32 split built, T = C_j in
+      // float32: the B-orthogonal projection that follows removes range(G_j),
+      // so P_B A_j^-1 R = P_B (G_j S_j^-1 G_j^T + C_j) R = P_B C_j R, and the
+      // float32 SYMV streams half the bytes of the float64 one, which is
+      // FP64-ALU-bound (a preconditioner of the eigensolve needs no float64)
+      const bool f32_dir = !neu_dir && c->loc_f32.p;
       for (int col = 0; col < k; ++col) {
-        symv_batch<double>(c->loc, Tdir, L.R.p + (int64_t)col * L.vlen,
-                           L.W.p + (int64_t)col * L.vlen, c->d_err.p, s);
+        if (f32_dir)
+          symv_batch<float>(c->loc, c->loc_f32.p, L.R.p + (int64_t)col * L.vlen,
+                            L.W.p + (int64_t)col * L.vlen, c->d_err.p, s);
+        else
+          symv_batch<double>(c->loc, Tdir, L.R.p + (int64_t)col * L.vlen,
+                             L.W.p + (int64_t)col * L.vlen, c->d_err.p, s);
       }
       project_gradients_B(L, L.W.p, k);
       apply_B(L, L.W.p, L.BW.p, k);

@@ -769,6 +769,10 @@ void setup_all(geneo_ctx *c) {
   }
 
   stage_mark(2);
+  // the SYMV autotuner runs before the eigensolves, which apply the local
+  // factors every LOBPCG iteration
+  if (c->opt.autotune) autotune_symv(c);
+  stage_mark(6);
   // --- coarse space
   c->n0 = c->n0_snk = c->n0_geneo = 0;
   if (c->opt.coarse != GENEO_COARSE_NONE) {
@@ -827,8 +831,6 @@ void setup_all(geneo_ctx *c) {
   for (auto *v : {&c->h_b, &c->h_x}) v->alloc(n);
   reserve_rhs(c, 1);
   check_device_error(c, s);
-  if (c->opt.autotune) autotune_symv(c);
-  stage_mark(6);
   c->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->stage_s[7] = c->setup_seconds;
