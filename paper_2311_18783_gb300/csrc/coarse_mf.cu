@@ -183,65 +183,86 @@ __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tas
   __shared__ double vec[kTile];
   __shared__ int last;
   const int64_t vo = a.voff[f];
+  const int nk = tk.j1 - tk.j0;  // tiles of this task, at most kChunk
   if (kMode <= 1) {
-    // row modes: warp w owns rows 8w..8w+7, lane l columns 2l, 2l+1
+    // row modes: warp w owns rows 8w..8w+7, lane l columns 2l, 2l+1.  All of
+    // the task's tiles are loaded (predicated) before the first use, so
+    // their DRAM latencies overlap
+    const double *vin = kMode == 0 ? a.wbuf : a.ybuf;
+    double2 v[kChunk][8], x[kChunk];
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      const int K = tk.j0 + q;
+      if (q < nk) {
+        const double *t = a.T + (a.toff[f] + (int64_t)O * (O + 1) / 2 + K) * kTileElems;
+        x[q] = *reinterpret_cast<const double2 *>(vin + vo + (int64_t)K * kTile + 2 * l);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          v[q][r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
+      }
+    }
     double acc[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[r] = 0.0;
-    const double *vin = kMode == 0 ? a.wbuf : a.ybuf;
-    // the task's (at most kChunk) tiles are loaded before any is used, so
-    // their DRAM latencies overlap
 #pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      const int K = tk.j0 + q;
-      if (K >= tk.j1) break;
-      const double *t = a.T + (a.toff[f] + (int64_t)O * (O + 1) / 2 + K) * kTileElems;
-      const double2 x = *reinterpret_cast<const double2 *>(vin + vo + (int64_t)K * kTile + 2 * l);
-      double2 v[8];
+    for (int q = 0; q < kChunk; ++q)
+      if (q < nk)
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        v[r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
-#pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r] = fma(v[r].x, x.x, fma(v[r].y, x.y, acc[r]));
-    }
+        for (int r = 0; r < 8; ++r) acc[r] = fma(v[q][r].x, x[q].x, fma(v[q][r].y, x[q].y, acc[r]));
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      double v = acc[r];
+      double vv = acc[r];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (l == 0) vec[w * 8 + r] = v;
+      for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+      if (l == 0) vec[w * 8 + r] = vv;
     }
   } else {
-    // column modes: warp w owns rows 8w..8w+7 of every tile, lane l columns 2l, 2l+1
-    double c0 = 0.0, c1 = 0.0;
+    // column modes: warp w owns rows 8w..8w+7 of every tile, lane l columns
+    // 2l, 2l+1.  The input entries of the task's rows are staged in shared
+    // memory first (phase 2 gathers them through the update-row map, all in
+    // parallel), and the tiles are loaded (predicated) before the first use
+    __shared__ double xs[kChunk * kTile];
+    for (int e = threadIdx.x; e < nk * kTile; e += blockDim.x) {
+      const int64_t row = (int64_t)tk.j0 * kTile + e;
+      double xv;
+      if (kMode == 2) {
+        const int64_t u = row - a.npivp[f];
+        xv = (u >= 0 && u < a.nupd[f]) ? a.xpos[a.upos[a.uoff[f] + u]] : 0.0;
+      } else {
+        xv = a.tbuf[vo + row];
+      }
+      xs[e] = xv;
+    }
+    double2 v[kChunk][8];
 #pragma unroll
     for (int q = 0; q < kChunk; ++q) {
       const int K = tk.j0 + q;
-      if (K >= tk.j1) break;
-      const double *t = a.T + (a.toff[f] + (int64_t)K * (K + 1) / 2 + O) * kTileElems;
+      if (q < nk) {
+        const double *t = a.T + (a.toff[f] + (int64_t)K * (K + 1) / 2 + O) * kTileElems;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int64_t row = (int64_t)K * kTile + w * 8 + r;
-        double x;
-        if (kMode == 2) {
-          const int64_t u = row - a.npivp[f];
-          x = (u >= 0 && u < a.nupd[f]) ? a.xpos[a.upos[a.uoff[f] + u]] : 0.0;
-        } else {
-          x = a.tbuf[vo + row];
-        }
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
-        c0 = fma(v.x, x, c0);
-        c1 = fma(v.y, x, c1);
+        for (int r = 0; r < 8; ++r)
+          v[q][r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
       }
     }
+    __syncthreads();
+    double c0 = 0.0, c1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q)
+      if (q < nk)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const double xv = xs[q * kTile + w * 8 + r];
+          c0 = fma(v[q][r].x, xv, c0);
+          c1 = fma(v[q][r].y, xv, c1);
+        }
     red[w][2 * l] = c0;
     red[w][2 * l + 1] = c1;
     __syncthreads();
     if (threadIdx.x < kTile) {
-      double v = 0.0;
+      double vv = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v += red[q][threadIdx.x];
-      vec[threadIdx.x] = v;
+      for (int q = 0; q < 8; ++q) vv += red[q][threadIdx.x];
+      vec[threadIdx.x] = vv;
     }
   }
   __syncthreads();

@@ -88,10 +88,10 @@ __global__ void k_prolong(const int64_t *__restrict__ ptr, const int64_t *__rest
 // have a few entries, GenEO columns one per dof of their subdomain
 __global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zrow,
                      const double *__restrict__ zval, const double *__restrict__ r,
-                     double *__restrict__ t, int64_t n0, int64_t n) {
+                     double *__restrict__ t, int64_t ncols, int64_t n0, int64_t n) {
   const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int l = threadIdx.x & 31;
-  if (a >= n0) return;
+  if (a >= ncols) return;
   r += blockIdx.y * n;
   t += blockIdx.y * n0;
   double s = 0;
@@ -99,6 +99,29 @@ __global__ void k_zt(const int64_t *__restrict__ zptr, const int32_t *__restrict
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (l == 0) t[a] = s;
+}
+
+// t[a] = (Z^T r)_a for the long columns a >= a0 (the GenEO columns, one
+// entry per dof of their subdomain): one CTA per column
+__global__ void k_zt_long(const int64_t *__restrict__ zptr, const int32_t *__restrict__ zrow,
+                          const double *__restrict__ zval, const double *__restrict__ r,
+                          double *__restrict__ t, int64_t a0, int64_t n0, int64_t n) {
+  const int64_t a = a0 + blockIdx.x;
+  r += blockIdx.y * n;
+  t += blockIdx.y * n0;
+  double s = 0;
+  for (int64_t k = zptr[a] + threadIdx.x; k < zptr[a + 1]; k += blockDim.x)
+    s = fma(zval[k], r[zrow[k]], s);
+  __shared__ double sh[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w];
+    t[a] = v;
+  }
 }
 
 // y[e] = (Z u)_e (+ add[e] when add is given), one row per thread (CSR)
@@ -441,9 +464,20 @@ void coarse_solve(geneo_ctx *c, const double *r, double *y, cudaStream_t s, int 
     e1 = c->ev_take();
     c->ev_coarse.push_back({e0, e1});
   }
-  c->launches += 2;
-  k_zt<<<dim3(grid_for(n0 * 32, 256), k), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p,
-                                                       c->d_zc_val.p, r, c->crs_x.p, n0, n);
+  // short columns (split near-kernel) a warp each, long ones (GenEO) a CTA each
+  const int64_t nshort = c->n0_snk, nlong = n0 - c->n0_snk;
+  c->launches += 1;
+  if (nshort > 0) {
+    c->launches += 1;
+    k_zt<<<dim3(grid_for(nshort * 32, 256), k), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p,
+                                                             c->d_zc_val.p, r, c->crs_x.p, nshort,
+                                                             n0, n);
+  }
+  if (nlong > 0) {
+    c->launches += 1;
+    k_zt_long<<<dim3((unsigned)nlong, k), 256, 0, s>>>(c->d_zc_ptr.p, c->d_zc_row.p,
+                                                       c->d_zc_val.p, r, c->crs_x.p, nshort, n0, n);
+  }
   if (c->mf) {
     c->launches += mf_launches_per_solve(c);
     if (e0) record_event(e0, s);
