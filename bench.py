@@ -687,6 +687,9 @@ def main():
                       "chosen": int(row[2]), "from_cache": bool(row[3]),
                       "ms_per_candidate": [float(v) for v in row[4:4 + ncand]]})
     n = s.n
+    if prec == pkg.PREC_FP32:
+        # mixed precision: C_j and S_j^-1 of the split local inverse in float32
+        s.use_gradient_precision(pkg.PREC_FP32)
     b = torch.empty(n, dtype=torch.float64, device="cuda")
     s.assemble_rhs(w.f_slot[0], b)
     x = torch.zeros_like(b)
@@ -754,10 +757,11 @@ def main():
         fp64_side = v64
         variants["fp64_literal"], _, _ = timed_variant(pkg.PREC_FP64, False, side, 1)
         variants["mixed_literal"], _, _ = timed_variant(pkg.PREC_FP32, False, side, 1)
-        # S_j^-1 of the split's gradient part in float32 as well
-        s.use_gradient_precision(pkg.PREC_FP32)
-        variants["mixed_grad32_balanced"], _, _ = timed_variant(pkg.PREC_FP32, True, side, 1)
+        # the split's gradient part with S_j^-1 in float64 (the headline keeps
+        # it in float32 as well)
         s.use_gradient_precision(pkg.PREC_FP64)
+        variants["mixed_grad64_balanced"], _, _ = timed_variant(pkg.PREC_FP32, True, side, 1)
+        s.use_gradient_precision(pkg.PREC_FP32)
     # headline: balanced form with the precision asked for, clocks sampled
     s.use_precision(prec)
     s.use_balanced(True)
@@ -842,6 +846,8 @@ def main():
             "config": {"workload": args.workload, "n": n, "nsub": s.sizes["nsub"],
                        "n0": s.sizes["n0"], "n0_geneo": s.sizes["n0_geneo"], "tol": TOL,
                        "form": "balanced (x0 = Z E^-1 Z^T b, one coarse solve per iteration)",
+                       "local_factors": ("float32 C_j and S_j^-1, float64 PCG and coarse solve"
+                                         if prec == pkg.PREC_FP32 else "float64"),
                        "coarse_factor_gb": s.sizes["coarse_factor_bytes"] / 1e9,
                        "pcg_iters": iters[-1], "precision": args.precision,
                        "l2": "inputs larger than L2 (local factors "

@@ -41,10 +41,25 @@ __global__ void __launch_bounds__(256)
   const int64_t base = slice_off[sl] + lane;
   const int w = slice_w[sl];
   double acc = 0;
-#pragma unroll 4
-  for (int j = 0; j < w; ++j) {
-    const int64_t q = base + (int64_t)j * 32;
-    acc = fma(val[q], x[col[q]], acc);
+  // chunks of 8 entries: the values and indices (streamed, not kept in L1)
+  // are loaded first, then the 8 gathers of x, so that each thread has 8
+  // independent loads in flight at every stage; the sum keeps the entry order
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    double v[8], xv[8];
+    int32_t ci[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (j0 + q < w) {
+        const int64_t e = base + (int64_t)(j0 + q) * 32;
+        v[q] = __ldcs(val + e);
+        ci[q] = __ldcs(col + e);
+      }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (j0 + q < w) xv[q] = __ldg(x + ci[q]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (j0 + q < w) acc = fma(v[q], xv[q], acc);
   }
   const int64_t i = sl * 32 + lane;
   if (i < n) {
