@@ -9,3 +9,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built library")
     config.addinivalue_line("markers", "slow: CPU test that takes more than ~20 s")
+
+
+# GPU tests that set up several full-size problems (minutes each) run only
+# with GENEO_GPU_LONG=1, so that the default GPU suite stays within a few
+# minutes; their last measured results are recorded in the design notes.
+GPU_LONG = os.environ.get("GENEO_GPU_LONG") == "1"

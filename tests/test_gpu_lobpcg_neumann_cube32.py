@@ -15,8 +15,12 @@ import pytest
 
 import workloads as W
 
+from conftest import GPU_LONG
+
 torch = pytest.importorskip("torch")
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not GPU_LONG, reason="long GPU test (a second full 32^3 "
+                                 "set-up, about 2 min): set GENEO_GPU_LONG=1")]
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                       "cube32_reference.json")

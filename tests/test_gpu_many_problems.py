@@ -1,6 +1,6 @@
-"""Sixteen problems of the batching workload (workloads.many_problems, seed
-3: n^3 cubes with 1-2 holes, mu^-1 in {1, 1e2, 1e4} on blocks, gamma
-log-uniform in [1e-6, 1], 8-64 boxes each; the first sixteen with n <= 10)
+"""Eight problems (sixteen with GENEO_GPU_LONG=1) of the batching workload
+(workloads.many_problems, seed 3: n^3 cubes with 1-2 holes, mu^-1 in {1, 1e2, 1e4} on blocks, gamma
+log-uniform in [1e-6, 1], 8-64 boxes each; the first ones with n <= 10)
 set up together by geneo_setup_batch and solved by one segmented PCG
 (per-problem scalars, each problem stopping on its own, the iteration
 replayed as a CUDA graph), against the oracle problem by problem:
@@ -22,15 +22,20 @@ import pytest
 
 import workloads as W
 
+from conftest import GPU_LONG
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+# the first eight problems by default, sixteen with GENEO_GPU_LONG=1
+NPROB = 16 if GPU_LONG else 8
 
-def test_sixteen_batching_problems_against_oracle():
+
+def test_batching_problems_against_oracle():
     import paper_2311_18783_gb300 as pkg
     from oracle.pipeline import build_problem, solve
-    ps = [w for w in W.many_problems(256, seed=3) if w.nx <= 10][:16]
-    assert len(ps) == 16
+    ps = [w for w in W.many_problems(256, seed=3) if w.nx <= 10][:NPROB]
+    assert len(ps) == NPROB
     for w in ps:
         w.f_slot = W.box(w.nx, w.ny, w.nz, h=w.hx, f='random', seed=w.nx).f_slot
     comp = pkg.compose(ps)
