@@ -67,12 +67,15 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# DRAM traffic of k_symv_strips<float, 8, 4> per algorithmic byte, from one ncu
-# capture on cube16_hole_channels: (204.36 MB read + 7.14 MB written) / 203.69 MB
-# of stored tiles.  Traffic scales with the stored tiles, so the full launch's
-# traffic is this ratio times its algorithmic bytes.  Set to None when the
-# kernel changes until it is captured again.
-SYMV_F32_TRAFFIC_RATIO = None  # the kernel became configurable; recapture pending
+# DRAM traffic of the float32 streaming SYMV per algorithmic byte, from one ncu
+# capture on cube16_hole_channels of the configuration the autotuner chose there
+# ({6 stages, 4 tiles per barrier, 8 warps, 2 CTAs per SM}; every configuration
+# reads each stored tile once and writes one float column partial per tile):
+# (204.64 MB read + 5.04 MB written) / 203.69 MB of stored tiles.  Traffic
+# scales with the stored tiles, so the full launch's traffic is this ratio
+# times its algorithmic bytes.  Set to None when the kernel changes until it is
+# captured again.
+SYMV_F32_TRAFFIC_RATIO = (204.6372 + 5.0365) / 203.6859  # (read + written) / stored tiles
 
 # FP64 FMA rate of GB300: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2070 MHz
 # (the recipe's 1.25 TFLOP/s nominal figure at the maximum SM clock)
@@ -803,8 +806,9 @@ def main():
                        "algorithmic_bytes_per_solve": cb, "solve_ms": tc * 1e3,
                        "solves": prof["coarse_symv_launches"]}
     spmv_roof = time_spmv(s)
-    spmv_roof["l2"] = ("A, x and y (about 45 MB) are L2-resident here; bench.py --workload "
-                       "spmv_cube48 measures a 146 MB matrix")
+    spmv_roof["l2"] = ("A, x and y take about 45 MB; the value and index loads carry an "
+                       "evict-first hint, so back-to-back launches re-read A; bench.py "
+                       "--workload spmv_cube48 measures a 146 MB matrix")
     refined = {}
     if prec == pkg.PREC_FP32:
         refined["mixed"] = timed_refined(pkg.PREC_FP32)
@@ -831,7 +835,8 @@ def main():
                 "traffic": (None if SYMV_F32_TRAFFIC_RATIO is None else
                             SYMV_F32_TRAFFIC_RATIO * prof["local_symv_bytes"]),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum on "
-                                  "cube16_hole_channels, scaled by stored tiles",
+                                  "cube16_hole_channels (autotuned configuration there), "
+                                  "scaled by stored tiles",
                 "algorithmic_bytes_per_launch": prof["local_symv_bytes"],
                 "launch_ms": t_launch * 1e3}
     applies_per_s = aggregate_rate(sum(iters) + len(iters), ms * args.steps / 1e3, world)
