@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                    help="mixed: float32 split local factors (headline) and float64 beside it")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--many-gb", type=float, default=120.0,
+    p.add_argument("--many-gb", type=float, default=24.0,
                    help="many_problems: memory budget for the local factors (float64 + float32)")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "cube16_hole_channels", BLOCK_WORKLOAD, "beam128_mild",
@@ -583,7 +583,10 @@ def run_many(args):
         take.append(w)
     comp = pkg.compose(take)
     t0 = time.perf_counter()
-    s = pkg.Solver.batch(take, precision=pkg.PREC_FP32, balanced=1, autotune=1)
+    # the default LOBPCG mode misses GenEO vectors on the 2-3-cell boxes of
+    # this workload (PCG then stalls); the Neumann mode finds the oracle's
+    s = pkg.Solver.batch(take, precision=pkg.PREC_FP32, balanced=1, autotune=1,
+                         lobpcg_neumann=1, lobpcg_block=16)
     setup_s = time.perf_counter() - t0
     b = torch.empty(s.n, dtype=torch.float64, device="cuda")
     s.assemble_rhs(comp["f_slot"][0], b)
@@ -750,6 +753,7 @@ def main():
 
     side = max(1, min(args.steps, 5))
     variants = {}
+    coarse_per_level_ms = None
     fp64_side = None
     if prec == pkg.PREC_FP32:
         # plain float64 factors on the same GPU, same problem and form
@@ -765,6 +769,14 @@ def main():
         s.use_gradient_precision(pkg.PREC_FP64)
         variants["mixed_grad64_balanced"], _, _ = timed_variant(pkg.PREC_FP32, True, side, 1)
         s.use_gradient_precision(pkg.PREC_FP32)
+        # the coarse solve as one launch per level and phase instead of one
+        # cooperative launch (identical results)
+        s.use_persistent_coarse(False)
+        variants["mixed_coarse_per_level"], _, pcl = timed_variant(pkg.PREC_FP32, True, side, 1,
+                                                                   True)
+        s.use_persistent_coarse(True)
+        if pcl["coarse_symv_launches"]:
+            coarse_per_level_ms = pcl["coarse_symv_ms"] / pcl["coarse_symv_launches"]
     # headline: balanced form with the precision asked for, clocks sampled
     s.use_precision(prec)
     s.use_balanced(True)
@@ -800,11 +812,22 @@ def main():
     if prof["coarse_symv_launches"] and prof["coarse_solve_bytes"]:
         tc = prof["coarse_symv_ms"] / prof["coarse_symv_launches"] * 1e-3
         cb = prof["coarse_solve_bytes"]
-        coarse_roof = {"kernel": "k_mf_tiles<0..3> + k_mf_gather (one coarse solve)",
+        coarse_roof = {"kernel": "k_mf_solve_persistent (one coarse solve, one cooperative "
+                                 "launch)",
                        "bound": "hbm", "achieved": cb / tc / 1e9, "peak": peaks_hbm(),
                        "unit": "GB/s", "frac": cb / tc / 1e9 / peaks_hbm(),
                        "algorithmic_bytes_per_solve": cb, "solve_ms": tc * 1e3,
-                       "solves": prof["coarse_symv_launches"]}
+                       "solves": prof["coarse_symv_launches"],
+                       "solve_ms_one_launch_per_level_and_phase": coarse_per_level_ms}
+    if coarse_roof is not None:
+        # per step of the last profiled single-launch coarse solve: kind (0
+        # permutation in, 1 gather, 2..5 tile phase 0..3, 6 permutation out),
+        # tree level, items, MB of factor tiles, microseconds (SM cycles of
+        # the first CTA at the median clock)
+        cs = np.asarray(s.export("coarse_steps"), dtype=np.float64).reshape(-1, 5)
+        mhz = clk.get("sm_mhz") or 2070.0
+        coarse_roof["steps"] = [[int(r[0]), int(r[1]), int(r[2]), round(r[3] / 1e6, 3),
+                                 round(r[4] / mhz, 2)] for r in cs]
     spmv_roof = time_spmv(s)
     spmv_roof["l2"] = ("A, x and y take about 45 MB; the value and index loads carry an "
                        "evict-first hint, so back-to-back launches re-read A; bench.py "

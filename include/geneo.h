@@ -301,6 +301,17 @@ int geneo_use_gradient_precision(geneo_ctx *ctx, int32_t precision);
  * always applies the literal M^-1_AS,2. */
 int geneo_use_balanced(geneo_ctx *ctx, int32_t on);
 
+/* Kernel shape of the sparse coarse solve y = E^-1 t (Sec. 2, E = Z^T A Z;
+ * multifrontal factor of the nested-dissection ordering).  on = 1 (default):
+ * the whole solve is one cooperative launch whose resident CTAs run the
+ * level-by-level steps separated by a bounded grid-wide barrier (a barrier
+ * that waits more than about two seconds makes the call return
+ * GENEO_ERR_TIMEOUT).  on = 0: one launch per level and phase.  Both compute
+ * the same operations in the same order and give identical results.  Where
+ * the device offers no cooperative launch, on = 1 behaves as on = 0.
+ * INVALID_ARG unless on is 0 or 1. */
+int geneo_use_persistent_coarse(geneo_ctx *ctx, int32_t on);
+
 /* Same solve with host buffers: copies b_host[n] to the device, solves, and
  * copies x back to x_host[n] before returning. */
 int geneo_solve_host(geneo_ctx *ctx, const double *b_host, double *x_host, double tol,
@@ -426,6 +437,14 @@ int geneo_profile_read(geneo_ctx *ctx, geneo_profile *out);
  *                                   1 S_j^-1 blocks), precision, chosen candidate, 1 if it
  *                                   came from the cache, then milliseconds per candidate
  *                                   (NaN past the last)
+ *  "coarse_steps" float64 [steps][5]  per step of the single-launch coarse solve
+ *                                   (geneo_use_persistent_coarse): kind (0 permutation in,
+ *                                   1 gather, 2..5 tile phase 0..3, 6 permutation out),
+ *                                   tree level (-1 for the permutations), items, factor
+ *                                   bytes read, SM cycles of the first CTA from the step's
+ *                                   start to the next one's in the last such solve run
+ *                                   with profiling on (zeros before one); empty without
+ *                                   a sparse coarse factor
  *  "mlp_features" float32 [loc_vlen][5], "eig_V" float64 [8][loc_vlen],
  *  "eig_nq" int32 [nsub]            warm-start features and training targets
  * Returns INVALID_ARG for an unknown name or a too small buffer, STATE for a

@@ -94,6 +94,7 @@ _SIGS = {
     "geneo_solve_refined": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       C.c_int32, C.c_int32, C.POINTER(SolveInfo), C.c_void_p]),
     "geneo_use_balanced": (C.c_int, [C.c_void_p, C.c_int32]),
+    "geneo_use_persistent_coarse": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_use_gradient_precision": (C.c_int, [C.c_void_p, C.c_int32]),
     "geneo_symv_config_count": (C.c_int, [C.c_int32]),
     "geneo_use_symv_config": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
@@ -145,7 +146,7 @@ _EXPORT_DTYPES = {
     "loc_f32": np.float32, "loc_nt": np.int32, "loc_toff": np.int64, "loc_voff": np.int64,
     "loc_vlen": np.int64, "mlp_features": np.float32, "eig_V": np.float64, "eig_nq": np.int32,
     "lobpcg_iters": np.int32, "lobpcg_iters_first": np.int32, "seg_off": np.int64,
-    "xv_off": np.int64, "xv_vert": np.int32, "setup_stages": np.float64, "autotune": np.float64,
+    "xv_off": np.int64, "xv_vert": np.int32, "setup_stages": np.float64, "autotune": np.float64, "coarse_steps": np.float64,
 }
 
 
@@ -422,6 +423,11 @@ class Solver:
 
     def use_balanced(self, on=True):
         _check(_LIB.geneo_use_balanced(self._ctx, 1 if on else 0))
+
+    def use_persistent_coarse(self, on=True):
+        """The coarse solve as one cooperative launch (True, default) or one
+        launch per level and phase (False); identical results."""
+        _check(_LIB.geneo_use_persistent_coarse(self._ctx, 1 if on else 0))
 
     def apply_preconditioner_block(self, R, Z, stream=None):
         """R, Z: CUDA float64 tensors [nrhs, n] (contiguous)."""

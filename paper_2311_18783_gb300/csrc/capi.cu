@@ -342,6 +342,14 @@ int geneo_use_balanced(geneo_ctx *c, int32_t on) {
   return GENEO_OK;
 }
 
+int geneo_use_persistent_coarse(geneo_ctx *c, int32_t on) {
+  if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (on != 0 && on != 1) return fail(GENEO_ERR_INVALID_ARG, "on must be 0 or 1");
+  c->mf_persist = on != 0;
+  return GENEO_OK;
+}
+
 int geneo_apply_preconditioner_block(geneo_ctx *c, const double *r, double *z, int32_t nrhs,
                                      void *s) {
   if (c && c->host_only) return fail(GENEO_ERR_STATE, "topology-only context");
@@ -569,6 +577,10 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
     } else if (nm == "eig_nq") put(c->eig_nq.data(), c->eig_nq.size() * 4);
     else if (nm == "lobpcg_iters") put(c->lobpcg_iters.data(), c->lobpcg_iters.size() * 4);
     else if (nm == "setup_stages") put(c->stage_s, sizeof(c->stage_s));
+    else if (nm == "coarse_steps") {
+      const std::vector<double> v = geneo::mf_step_profile(c);
+      put(v.data(), v.size() * 8);
+    }
     else if (nm == "autotune") {
       std::vector<double> v;
       for (const auto &r : c->tune) {

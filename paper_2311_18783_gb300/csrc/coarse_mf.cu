@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <numeric>
 
+#include "bulk.cuh"
 #include "setup.hpp"
 
 namespace geneo {
@@ -163,44 +164,67 @@ struct MfArgs {
   int64_t ldv, ldx, ldp, ldc;
 };
 
-// blockIdx.x = task * k + column: the k columns of a task run in adjacent
-// CTAs, so its tiles are read from DRAM once and from L2 for the others
+// Shared memory of one tile task.
+struct MfShared {
+  double red[8][kTile];
+  double vec[kTile];
+  double xs[kChunk * kTile];
+  int last;
+};
+
+// Offset (in tiles, from the factor's base) of tile q of a task.
 template <int kMode>
-__global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tasks, MfArgs a) {
-  const MfTask tk = tasks[blockIdx.x / a.k];
-  {
-    const int64_t col = blockIdx.x % a.k;
-    a.wbuf += col * a.ldv;
-    a.ybuf += col * a.ldv;
-    a.tbuf += col * a.ldv;
-    a.xpos += col * a.ldx;
-    a.part += col * a.ldp;
-    a.cnt += col * a.ldc;
+__device__ __forceinline__ int64_t mf_tile_index(const MfTask &tk, const MfArgs &a, int q) {
+  const int O = tk.I, K = tk.j0 + q;
+  return kMode <= 1 ? a.toff[tk.f] + (int64_t)O * (O + 1) / 2 + K
+                    : a.toff[tk.f] + (int64_t)K * (K + 1) / 2 + O;
+}
+
+// Factor tiles of a task into registers (warp w rows 8w..8w+7, lane l
+// columns 2l, 2l+1), all issued before any use so their DRAM latencies
+// overlap.  Reads only the factor and the front offsets, which no solve
+// writes.
+template <int kMode>
+__device__ __forceinline__ void mf_load(const MfTask &tk, const MfArgs &a, const double *T,
+                                        double2 (&v)[kChunk][8]) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nk = tk.j1 - tk.j0;  // tiles of this task, at most kChunk
+#pragma unroll
+  for (int q = 0; q < kChunk; ++q) {
+    if (q < nk) {
+      const double *t = T + mf_tile_index<kMode>(tk, a, q) * kTileElems;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        v[q][r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
+    }
   }
+}
+
+// The rest of a task for right-hand side `col`: input entries, the tile
+// GEMV, the split-K reduction and the output.  tile(q, r) gives the two
+// entries (row 8w + r, columns 2l, 2l + 1) of the task's tile q that thread
+// (warp w, lane l) multiplies.
+template <int kMode, class TileAt>
+__device__ __forceinline__ void mf_finish(const MfTask &tk, MfArgs a, int64_t col, TileAt tile,
+                                          MfShared &sh) {
+  a.wbuf += col * a.ldv;
+  a.ybuf += col * a.ldv;
+  a.tbuf += col * a.ldv;
+  a.xpos += col * a.ldx;
+  a.part += col * a.ldp;
+  a.cnt += col * a.ldc;
   const int f = tk.f, O = tk.I;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __shared__ double red[8][kTile];
-  __shared__ double vec[kTile];
-  __shared__ int last;
   const int64_t vo = a.voff[f];
-  const int nk = tk.j1 - tk.j0;  // tiles of this task, at most kChunk
+  const int nk = tk.j1 - tk.j0;
   if (kMode <= 1) {
-    // row modes: warp w owns rows 8w..8w+7, lane l columns 2l, 2l+1.  All of
-    // the task's tiles are loaded (predicated) before the first use, so
-    // their DRAM latencies overlap
+    // row modes: y_O = sum_K T(O, K) x_K
     const double *vin = kMode == 0 ? a.wbuf : a.ybuf;
-    double2 v[kChunk][8], x[kChunk];
+    double2 x[kChunk];
 #pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      const int K = tk.j0 + q;
-      if (q < nk) {
-        const double *t = a.T + (a.toff[f] + (int64_t)O * (O + 1) / 2 + K) * kTileElems;
-        x[q] = *reinterpret_cast<const double2 *>(vin + vo + (int64_t)K * kTile + 2 * l);
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          v[q][r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
-      }
-    }
+    for (int q = 0; q < kChunk; ++q)
+      if (q < nk)
+        x[q] = __ldcg(reinterpret_cast<const double2 *>(vin + vo + (int64_t)(tk.j0 + q) * kTile + 2 * l));
     double acc[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[r] = 0.0;
@@ -208,41 +232,31 @@ __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tas
     for (int q = 0; q < kChunk; ++q)
       if (q < nk)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) acc[r] = fma(v[q][r].x, x[q].x, fma(v[q][r].y, x[q].y, acc[r]));
+        for (int r = 0; r < 8; ++r) {
+          const double2 t = tile(q, r);
+          acc[r] = fma(t.x, x[q].x, fma(t.y, x[q].y, acc[r]));
+        }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       double vv = acc[r];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
-      if (l == 0) vec[w * 8 + r] = vv;
+      if (l == 0) sh.vec[w * 8 + r] = vv;
     }
   } else {
-    // column modes: warp w owns rows 8w..8w+7 of every tile, lane l columns
-    // 2l, 2l+1.  The input entries of the task's rows are staged in shared
-    // memory first (phase 2 gathers them through the update-row map, all in
-    // parallel), and the tiles are loaded (predicated) before the first use
-    __shared__ double xs[kChunk * kTile];
+    // column modes: y_O = sum_K T(K, O)^T x_K.  The input entries of the
+    // task's rows are staged in shared memory first (phase 2 gathers them
+    // through the update-row map, all in parallel)
     for (int e = threadIdx.x; e < nk * kTile; e += blockDim.x) {
       const int64_t row = (int64_t)tk.j0 * kTile + e;
       double xv;
       if (kMode == 2) {
         const int64_t u = row - a.npivp[f];
-        xv = (u >= 0 && u < a.nupd[f]) ? a.xpos[a.upos[a.uoff[f] + u]] : 0.0;
+        xv = (u >= 0 && u < a.nupd[f]) ? __ldcg(a.xpos + a.upos[a.uoff[f] + u]) : 0.0;
       } else {
-        xv = a.tbuf[vo + row];
+        xv = __ldcg(a.tbuf + vo + row);
       }
-      xs[e] = xv;
-    }
-    double2 v[kChunk][8];
-#pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      const int K = tk.j0 + q;
-      if (q < nk) {
-        const double *t = a.T + (a.toff[f] + (int64_t)K * (K + 1) / 2 + O) * kTileElems;
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          v[q][r] = __ldg(reinterpret_cast<const double2 *>(t + (w * 8 + r) * kTile + 2 * l));
-      }
+      sh.xs[e] = xv;
     }
     __syncthreads();
     double c0 = 0.0, c1 = 0.0;
@@ -251,50 +265,260 @@ __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tas
       if (q < nk)
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          const double xv = xs[q * kTile + w * 8 + r];
-          c0 = fma(v[q][r].x, xv, c0);
-          c1 = fma(v[q][r].y, xv, c1);
+          const double xv = sh.xs[q * kTile + w * 8 + r];
+          const double2 t = tile(q, r);
+          c0 = fma(t.x, xv, c0);
+          c1 = fma(t.y, xv, c1);
         }
-    red[w][2 * l] = c0;
-    red[w][2 * l + 1] = c1;
+    sh.red[w][2 * l] = c0;
+    sh.red[w][2 * l + 1] = c1;
     __syncthreads();
     if (threadIdx.x < kTile) {
       double vv = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) vv += red[q][threadIdx.x];
-      vec[threadIdx.x] = vv;
+      for (int q = 0; q < 8; ++q) vv += sh.red[q][threadIdx.x];
+      sh.vec[threadIdx.x] = vv;
     }
   }
   __syncthreads();
   if (tk.nch > 1) {
     if (threadIdx.x < kTile) {
-      a.part[(int64_t)tk.slot * kTile + threadIdx.x] = vec[threadIdx.x];
+      a.part[(int64_t)tk.slot * kTile + threadIdx.x] = sh.vec[threadIdx.x];
       __threadfence();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      last = atomicAdd(&a.cnt[tk.cnt], 1) == tk.nch - 1;
+      sh.last = atomicAdd(&a.cnt[tk.cnt], 1) == tk.nch - 1;
     }
     __syncthreads();
-    if (!last) return;
+    if (!sh.last) return;
     __threadfence();
     if (threadIdx.x < kTile) {
       double v = 0.0;
       for (int k = 0; k < tk.nch; ++k) v += __ldcg(a.part + (int64_t)(tk.rbase + k) * kTile + threadIdx.x);
-      vec[threadIdx.x] = v;
+      sh.vec[threadIdx.x] = v;
     }
     if (threadIdx.x == 0) a.cnt[tk.cnt] = 0;
     __syncthreads();
   }
   if (threadIdx.x < kTile) {
     const int64_t idx = (int64_t)O * kTile + threadIdx.x;
-    const double v = vec[threadIdx.x];
+    const double v = sh.vec[threadIdx.x];
     if (kMode == 0) a.ybuf[vo + idx] = v;
-    else if (kMode == 1) a.wbuf[vo + idx] -= v;
-    else if (kMode == 2) a.tbuf[vo + idx] = a.ybuf[vo + idx] - v;
+    else if (kMode == 1) a.wbuf[vo + idx] = __ldcg(a.wbuf + vo + idx) - v;
+    else if (kMode == 2) a.tbuf[vo + idx] = __ldcg(a.ybuf + vo + idx) - v;
     else if (idx < a.npiv[f]) a.xpos[a.first[f] + idx] = v;
   }
+}
+
+// One launch per (level, phase): blockIdx.x = task * k + column, so the k
+// columns of a task run in adjacent CTAs and its tiles are read from DRAM
+// once and from L2 for the others
+template <int kMode>
+__global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tasks, MfArgs a) {
+  __shared__ MfShared sh;
+  const MfTask tk = tasks[blockIdx.x / a.k];
+  double2 v[kChunk][8];
+  mf_load<kMode>(tk, a, a.T, v);
+  mf_finish<kMode>(tk, a, blockIdx.x % a.k, [&](int q, int r) { return v[q][r]; }, sh);
+}
+
+// ---- the whole solve in one cooperative launch
+//
+// The steps of the level-by-level solve (permutation in, per level the
+// gather and phases 0 and 1, per level downwards phases 2 and 3,
+// permutation out) run in order, separated by a grid-wide barrier; the CTAs
+// (all resident) stride over each step's items.  A CTA issues the tile loads
+// of its first task of a step before it waits at the barrier that ends the
+// step before, so those latencies overlap the barrier.  Every item computes
+// exactly what its launch of the level-by-level path computes, in the same
+// order, so both paths give identical results.  Vectors that a step
+// writes are read through L2 (ld.global.cg): a CTA's L1 may still hold a
+// line that another CTA has rewritten since (fronts adjacent in the
+// elimination order share lines of the solution vector).
+
+enum MfStepKind : int32_t { kStepPermIn = 0, kStepGather = 1, kStepTiles = 2, kStepPermOut = 6 };
+
+struct MfStep {
+  int32_t kind;  // MfStepKind; kStepTiles + p for tile phase p
+  int32_t ntask;
+  const MfTask *tasks;
+  const int32_t *rf, *rl;
+  const int64_t *gptr, *gidx;
+  int64_t nrows;
+};
+
+struct MfPersistArgs {
+  const MfStep *steps;
+  int nsteps;
+  MfArgs a;  // a.T unused: TL (phases 1, 2) and TY (phases 0, 3)
+  const double *TL, *TY;
+  const int64_t *pos, *first, *voff;
+  const int32_t *npiv;
+  const double *t;  // right-hand sides, column order, n0 each
+  double *y;        // solutions, column order
+  double *cpos;
+  int64_t n0, vlen;
+  unsigned *bar;    // [0] arrivals, [1] generation; zero at set-up
+  int *err;
+  long long *stamps;  // null, or clock64 of CTA 0 at every step start and at its end
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier (sense by generation count).  The generation is read
+// before arriving; it can only move once every CTA, this one included, has
+// arrived.  Thread 0 polls for about two seconds at most; past that the
+// kernel records kDevTimeout and every CTA leaves (false).
+__device__ __forceinline__ bool mf_grid_barrier(unsigned *bar, int *err, int &ok_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_u32(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(bar + 1) == g) {
+        if (clock64() - t0 > 4000000000LL) {
+          atomicCAS(err, kDevOk, kDevTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// Shared memory of the single-launch solve beyond MfShared: the task's
+// factor tiles and the mbarrier their bulk copies complete on.
+constexpr size_t kMfPersistSmem = (size_t)kChunk * kTileElems * sizeof(double) + 16;
+
+__device__ __forceinline__ void mf_stamp(const MfPersistArgs &p, int st) {
+  if (p.stamps && blockIdx.x == 0 && threadIdx.x == 0) p.stamps[st] = clock64();
+}
+
+template <int kMode>
+__device__ __forceinline__ bool mf_tile_step(const MfStep &S, int st, const MfPersistArgs &p,
+                                             bool sync, double *tiles, uint64_t *mbar,
+                                             uint32_t &parity, MfShared &sh, int &ok_sh) {
+  const int k = p.a.k;
+  const double *T = (kMode == 0 || kMode == 3) ? p.TY : p.TL;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nitems = S.ntask * k;  // at most 2^31 (tasks x 16 columns)
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int ti = it / k, col = it - ti * k;
+    const MfTask tk = S.tasks[ti];
+    const int nk = tk.j1 - tk.j0;
+    // the tile buffer is free: every thread passed the end of the last item
+    if (threadIdx.x == 0 && nk > 0) {
+      fence_proxy_async();  // the generic-proxy reads of the last item come first
+      mbar_expect_tx(mbar, (uint32_t)(nk * kTileElems * sizeof(double)));
+      for (int q = 0; q < nk; ++q)
+        bulk_g2s(tiles + q * kTileElems, T + mf_tile_index<kMode>(tk, p.a, q) * kTileElems,
+                 (uint32_t)(kTileElems * sizeof(double)), mbar);
+    }
+    if (sync) {
+      const bool ok = mf_grid_barrier(p.bar, p.err, ok_sh);
+      sync = false;
+      if (!ok) {
+        if (nk > 0) mbar_wait_bounded(mbar, parity);  // let the copies land
+        return false;
+      }
+      mf_stamp(p, st);
+    }
+    if (nk > 0) {
+      // every thread of the CTA takes the same decision
+      if (!__syncthreads_and(mbar_wait_bounded(mbar, parity))) {
+        if (threadIdx.x == 0) atomicCAS(p.err, kDevOk, kDevTimeout);
+        return false;
+      }
+      parity ^= 1u;
+    }
+    mf_finish<kMode>(tk, p.a, col,
+                     [&](int q, int r) {
+                       return *reinterpret_cast<const double2 *>(
+                           tiles + q * kTileElems + (w * 8 + r) * kTile + 2 * l);
+                     },
+                     sh);
+    __syncthreads();
+  }
+  if (sync) {
+    if (!mf_grid_barrier(p.bar, p.err, ok_sh)) return false;
+    mf_stamp(p, st);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256, 1) k_mf_solve_persistent(MfPersistArgs p) {
+  __shared__ MfShared sh;
+  __shared__ int ok_sh;
+  extern __shared__ __align__(128) unsigned char mf_dyn[];
+  double *tiles = reinterpret_cast<double *>(mf_dyn);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(mf_dyn + (size_t)kChunk * kTileElems * sizeof(double));
+  uint32_t parity = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int k = p.a.k;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  mf_stamp(p, 0);
+  for (int st = 0; st < p.nsteps; ++st) {
+    const MfStep S = p.steps[st];
+    const bool sync = st > 0;
+    if (S.kind >= kStepTiles && S.kind < kStepPermOut) {
+      bool ok = true;
+      switch (S.kind - kStepTiles) {
+        case 0: ok = mf_tile_step<0>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
+        case 1: ok = mf_tile_step<1>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
+        case 2: ok = mf_tile_step<2>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
+        default: ok = mf_tile_step<3>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
+      }
+      if (!ok) return;
+      continue;
+    }
+    if (sync) {
+      if (!mf_grid_barrier(p.bar, p.err, ok_sh)) return;
+      mf_stamp(p, st);
+    }
+    if (S.kind == kStepPermIn || S.kind == kStepPermOut) {
+      for (int col = 0; col < k; ++col) {
+        const int64_t co = (int64_t)col * p.n0;
+        for (int64_t i = gtid; i < p.n0; i += gthreads) {
+          if (S.kind == kStepPermIn) p.cpos[co + p.pos[i]] = p.t[co + i];
+          else p.y[co + i] = __ldcg(p.a.xpos + co + p.pos[i]);
+        }
+      }
+    } else {
+      // forward gather (k_mf_gather)
+      for (int col = 0; col < k; ++col) {
+        const double *cp = p.cpos + (int64_t)col * p.n0;
+        double *w = p.a.wbuf + (int64_t)col * p.vlen;
+        for (int64_t r = gtid; r < S.nrows; r += gthreads) {
+          const int f = S.rf[r], l = S.rl[r];
+          double v = l < p.npiv[f] ? __ldcg(cp + p.first[f] + l) : 0.0;
+          for (int64_t e = S.gptr[r]; e < S.gptr[r + 1]; ++e) v += __ldcg(w + S.gidx[e]);
+          w[p.voff[f] + l] = v;
+        }
+      }
+    }
+  }
+  mf_stamp(p, p.nsteps);
 }
 
 __global__ void k_perm(const int64_t *__restrict__ idx, const double *__restrict__ src,
@@ -319,6 +543,7 @@ struct MfLevel {
   int64_t nrows = 0;
   DevBuf<MfTask> task[4];                           // tile GEMV tasks per phase
   int ntask[4] = {0, 0, 0, 0};
+  int64_t ntiles[4] = {0, 0, 0, 0};                 // factor tiles each phase reads
 };
 
 struct Multifrontal {
@@ -332,6 +557,16 @@ struct Multifrontal {
   std::vector<MfLevel> levels;
   int64_t factor_bytes = 0;
   int64_t solve_tiles = 0;  // factor tiles one solve reads (all phases, all levels)
+  // the single-launch solve: its steps, barrier words and grid (0 CTAs:
+  // cooperative launches unavailable)
+  DevBuf<MfStep> steps;
+  int nsteps = 0;
+  DevBuf<unsigned> bar;
+  int persist_ctas = 0;
+  // per step: kind, level, items, factor bytes; and the SM clock of CTA 0
+  // at the start of every step of the last profiled solve
+  std::vector<double> step_info;
+  DevBuf<long long> stamps;
 };
 
 void MfDeleter::operator()(Multifrontal *m) const { delete m; }
@@ -607,6 +842,7 @@ void mf_setup(geneo_ctx *c, MfSchur *schur) {
       auto add = [&](int ph, int O, int o0, int o1) {
         const int nch = std::max(1, (o1 - o0 + kChunk - 1) / kChunk);
         M->solve_tiles += std::max(0, o1 - o0);
+        Lv.ntiles[ph] += std::max(0, o1 - o0);
         const int rbase = nslot;
         for (int k = 0; k < nch; ++k) {
           MfTask tk;
@@ -686,6 +922,73 @@ void mf_setup(geneo_ctx *c, MfSchur *schur) {
   check_device_error(c, s);
   mf_reserve(c, 1);
   M->factor_bytes = M->L.bytes() + M->Y.bytes();
+  // steps of the single-launch solve, in the order of the level-by-level one
+  {
+    std::vector<MfStep> st;
+    std::vector<double> &info = M->step_info;
+    auto note = [&](int kind, int lv, int64_t items, int64_t tiles) {
+      info.insert(info.end(), {(double)kind, (double)lv, (double)items,
+                               (double)tiles * kTileElems * sizeof(double)});
+    };
+    MfStep e{};
+    e.kind = kStepPermIn;
+    st.push_back(e);
+    note(kStepPermIn, -1, n0, 0);
+    for (int lv = 0; lv < nlev; ++lv) {
+      const MfLevel &Lv = M->levels[lv];
+      MfStep g{};
+      g.kind = kStepGather;
+      g.rf = Lv.rf.p;
+      g.rl = Lv.rl.p;
+      g.gptr = Lv.gptr.p;
+      g.gidx = Lv.gidx.p;
+      g.nrows = Lv.nrows;
+      if (Lv.nrows > 0) {
+        st.push_back(g);
+        note(kStepGather, lv, Lv.nrows, 0);
+      }
+      for (int ph = 0; ph < 2; ++ph)
+        if (Lv.ntask[ph]) {
+          MfStep t{};
+          t.kind = kStepTiles + ph;
+          t.ntask = Lv.ntask[ph];
+          t.tasks = Lv.task[ph].p;
+          st.push_back(t);
+          note(t.kind, lv, Lv.ntask[ph], Lv.ntiles[ph]);
+        }
+    }
+    for (int lv = nlev - 1; lv >= 0; --lv) {
+      const MfLevel &Lv = M->levels[lv];
+      for (int ph = 2; ph < 4; ++ph)
+        if (Lv.ntask[ph]) {
+          MfStep t{};
+          t.kind = kStepTiles + ph;
+          t.ntask = Lv.ntask[ph];
+          t.tasks = Lv.task[ph].p;
+          st.push_back(t);
+          note(t.kind, lv, Lv.ntask[ph], Lv.ntiles[ph]);
+        }
+    }
+    e.kind = kStepPermOut;
+    st.push_back(e);
+    note(kStepPermOut, -1, n0, 0);
+    M->stamps.alloc((int64_t)st.size() + 1);
+    M->stamps.zero(s);
+    M->steps.upload(st, s);
+    M->nsteps = (int)st.size();
+    M->bar.alloc(2);
+    M->bar.zero(s);
+    int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+    GENEO_CUDA(cudaGetDevice(&dev));
+    GENEO_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    GENEO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GENEO_CUDA(cudaFuncSetAttribute(k_mf_solve_persistent,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kMfPersistSmem));
+    GENEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mf_solve_persistent, 256,
+                                                             kMfPersistSmem));
+    M->persist_ctas = coop ? nsm * std::min(per_sm, 2) : 0;
+  }
   GENEO_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -721,12 +1024,29 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {
   TileBatch &fb = M.fb;
   const int64_t n0 = c->n0;
   if (k > M.kcap) throw Error(GENEO_ERR_STATE, "internal: coarse solve buffers too small");
-  k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, t, M.cpos.p, n0, 1);
   MfArgs al{M.npivt.p, M.npiv.p, M.npivp.p, M.nupd.p, M.first.p, M.uoff.p, M.upos.p,
             fb.d_toff.p, fb.d_voff.p, M.L.p, M.wbuf.p, M.ybuf.p, M.tbuf.p, M.xpos.p,
             M.part.p, M.cnt.p, k, fb.vlen, n0, (int64_t)M.nslot * kTile, M.ncnt};
   MfArgs ay = al;
   ay.T = M.Y.p;
+  if (c->mf_persist && M.persist_ctas > 0) {
+    MfPersistArgs pa{M.steps.p, M.nsteps, al, M.L.p, M.Y.p, M.pos.p, M.first.p, fb.d_voff.p,
+                     M.npiv.p, t, y, M.cpos.p, n0, fb.vlen, M.bar.p, c->d_err.p,
+                     c->prof ? M.stamps.p : nullptr};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)M.persist_ctas);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = kMfPersistSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GENEO_CUDA(cudaLaunchKernelEx(&cfg, k_mf_solve_persistent, pa));
+    return;
+  }
+  k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, t, M.cpos.p, n0, 1);
   const int nlev = (int)M.levels.size();
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M.levels[lv];
@@ -745,7 +1065,20 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {
   GENEO_CHECK_LAUNCH();
 }
 
+std::vector<double> mf_step_profile(const geneo_ctx *c) {
+  std::vector<double> out;
+  if (!c->mf) return out;
+  const Multifrontal &M = *c->mf;
+  const std::vector<long long> t = M.stamps.download(c->stream);
+  for (int i = 0; i < M.nsteps; ++i) {
+    out.insert(out.end(), M.step_info.begin() + 4 * i, M.step_info.begin() + 4 * i + 4);
+    out.push_back((double)(t[i + 1] - t[i]));
+  }
+  return out;
+}
+
 int mf_launches_per_solve(const geneo_ctx *c) {
+  if (c->mf_persist && c->mf->persist_ctas > 0) return 1;
   int n = 2;
   for (const MfLevel &Lv : c->mf->levels)
     n += 1 + (Lv.ntask[0] > 0) + (Lv.ntask[1] > 0) + (Lv.ntask[2] > 0) + (Lv.ntask[3] > 0);

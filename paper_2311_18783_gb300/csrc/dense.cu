@@ -6,6 +6,7 @@
 // inverses: every tile is read once per application and the work of all
 // subdomains is spread over all SMs.
 #include "dense.cuh"
+#include "bulk.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -489,48 +490,6 @@ void tiles_cast_f32(const TileBatch &b, const double *src, float *dst, cudaStrea
 // x 2 columns of a tile: row partials accumulate over the strip, column
 // partials (the mirrored upper triangle) are reduced across warps per tile.
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, "
-      "0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// bounded wait: about a second of polling at most
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > 4000000000LL) return false;
-  }
-  return true;
-}
-
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
@@ -671,6 +630,147 @@ __global__ void __launch_bounds__(WARPS * 32)
   }
 }
 
+// The same stream for NR right-hand sides at once (float32 tiles): every
+// tile is read once and applied to the NR columns x_c = x + c vlen.  For
+// each column, every product and sum is formed in the order of
+// k_symv_strips<float, *, *, WARPS>, so column c equals that kernel's result
+// bit for bit.  Row partials go to rowpart[c][vlen], column partials to
+// colpart[c][ntiles][64].
+template <int NST, int D, int WARPS, int NR>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_symv_strips_nr(const float *__restrict__ data, const int64_t *__restrict__ toff,
+                     const int64_t *__restrict__ voff, const int32_t *__restrict__ strip_m,
+                     const int32_t *__restrict__ strip_I, const int32_t *__restrict__ cta_off,
+                     const double *__restrict__ x, int64_t vlen, int64_t ntiles,
+                     double *__restrict__ rowpart, float *__restrict__ colpart, int *err) {
+  constexpr int R = kTile / WARPS;  // rows per warp
+  static_assert(D <= NST && D * kTile <= WARPS * 32, "batch must fit the stages and the block");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float *stage = reinterpret_cast<float *>(smraw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + (size_t)NST * kTileElems * sizeof(float));
+  float *red = reinterpret_cast<float *>(bar + NST);  // [D][NR][WARPS][64]
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
+  if (s0 >= s1) return;
+  if (tid == 0) {
+    for (int i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int ps = s0, pJ = 0;
+  long long issued = 0, consumed = 0;
+  auto issue = [&]() {
+    if (ps >= s1) return;
+    const int m = strip_m[ps], I = strip_I[ps];
+    const float *src = data + (toff[m] + (int64_t)I * (I + 1) / 2 + pJ) * kTileElems;
+    const int st = (int)(issued % NST);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[st], kTileElems * sizeof(float));
+    bulk_g2s(stage + (size_t)st * kTileElems, src, kTileElems * sizeof(float), &bar[st]);
+    ++issued;
+    if (++pJ > I) {
+      pJ = 0;
+      ++ps;
+    }
+  };
+  if (tid == 0)
+    for (int q = 0; q < NST; ++q) issue();
+  bool failed = false;
+  for (int s = s0; s < s1 && !failed; ++s) {
+    const int m = strip_m[s], I = strip_I[s];
+    const int64_t vb = voff[m];
+    const int64_t tb = toff[m] + (int64_t)I * (I + 1) / 2;
+    float xi[R][NR], rp[R][NR];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        xi[r][c] = (float)x[c * vlen + vb + (int64_t)I * kTile + w * R + r];
+        rp[r][c] = 0.0f;
+      }
+    for (int J0 = 0; J0 <= I; J0 += D) {
+      const int nb = min(D, I + 1 - J0);
+      float xj[D][2][NR];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int64_t e = vb + (int64_t)(J0 + d) * kTile + 2 * l;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+          xj[d][0][c] = d < nb ? (float)x[c * vlen + e] : 0.0f;
+          xj[d][1][c] = d < nb ? (float)x[c * vlen + e + 1] : 0.0f;
+        }
+      }
+      bool ok = true;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (d >= nb) break;
+        const long long q = consumed + d;
+        ok = ok && mbar_wait_bounded(&bar[(int)(q % NST)], (uint32_t)((q / NST) & 1));
+      }
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicCAS(err, kDevOk, kDevTimeout);
+        failed = true;
+        break;
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (d < nb) {
+          const float *t = stage + (size_t)((consumed + d) % NST) * kTileElems;
+          float c0[NR], c1[NR];
+#pragma unroll
+          for (int c = 0; c < NR; ++c) c0[c] = c1[c] = 0.0f;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 a = *reinterpret_cast<const float2 *>(t + (w * R + r) * kTile + 2 * l);
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+              rp[r][c] = fmaf(a.x, xj[d][0][c], fmaf(a.y, xj[d][1][c], rp[r][c]));
+              c0[c] = fmaf(a.x, xi[r][c], c0[c]);
+              c1[c] = fmaf(a.y, xi[r][c], c1[c]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < NR; ++c) {
+            red[((d * NR + c) * WARPS + w) * kTile + 2 * l] = c0[c];
+            red[((d * NR + c) * WARPS + w) * kTile + 2 * l + 1] = c1[c];
+          }
+        }
+      }
+      __syncthreads();
+      // column partials of the off-diagonal tiles, per column
+      for (int e = tid; e < D * NR * kTile; e += WARPS * 32) {
+        const int d = e / (NR * kTile), c = (e / kTile) % NR, j = e % kTile;
+        if (d < nb && J0 + d < I) {
+          float sum = 0.0f;
+#pragma unroll
+          for (int q = 0; q < WARPS; ++q) sum += red[((d * NR + c) * WARPS + q) * kTile + j];
+          colpart[(c * ntiles + tb + J0 + d) * kTile + j] = sum;
+        }
+      }
+      consumed += nb;
+      if (tid == 0)
+        for (int d = 0; d < nb; ++d) issue();
+    }
+    if (failed) break;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        float v = rp[r][c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) rowpart[c * vlen + vb + (int64_t)I * kTile + w * R + r] = (double)v;
+      }
+  }
+  if (failed && tid == 0) {
+    while (consumed < issued) {
+      const int st = (int)(consumed % NST);
+      mbar_wait_bounded(&bar[st], (uint32_t)((consumed / NST) & 1));
+      ++consumed;
+    }
+  }
+}
+
 // y[(m, I)] = rowpart[(m, I)] + sum_{K > I} colpart[(m, K, I)]; the column
 // partials are stored in the accumulation type of the SYMV (float for
 // float32 tiles: half the partial-sum traffic, no precision lost)
@@ -777,6 +877,55 @@ void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_
                                                     reinterpret_cast<const typename Acc<T>::type *>(b.colpart.p),
                                                     y, nblocks);
   GENEO_CHECK_LAUNCH();
+}
+
+template <int NST, int D, int WARPS>
+static void launch_symv_nr4(TileBatch &b, const TileBatch::Sched &sc, const float *data,
+                            const double *x, int *d_err, cudaStream_t s) {
+  constexpr int NR = 4;
+  const size_t smem = (size_t)NST * kTileElems * sizeof(float) + NST * sizeof(uint64_t) +
+                      (size_t)D * NR * WARPS * kTile * sizeof(float);
+  static int attr_dev = -1;
+  int dev = 0;
+  GENEO_CUDA(cudaGetDevice(&dev));
+  if (attr_dev != dev) {
+    GENEO_CUDA(cudaFuncSetAttribute(k_symv_strips_nr<NST, D, WARPS, NR>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_dev = dev;
+  }
+  k_symv_strips_nr<NST, D, WARPS, NR><<<sc.nctas, WARPS * 32, smem, s>>>(
+      data, b.d_toff.p, b.d_voff.p, sc.strip_m.p, sc.strip_I.p, sc.cta_off.p, x, b.vlen,
+      b.ntiles, b.rowpart_nr.p, b.colpart_nr.p, d_err);
+}
+
+void symv_batch_f32_cols(TileBatch &b, const float *data, const double *x, double *y, int nr,
+                         int *d_err, cudaStream_t s, cudaEvent_t ev_before,
+                         cudaEvent_t ev_after) {
+  constexpr int NR = 4;
+  // the warps per tile of the batch's float configuration fix the order of
+  // every sum, so the 4-column kernel takes the same
+  const int warps = SymvCands<float>::c[b.symv_cfg[0]].warps;
+  int c = 0;
+  if (nr >= NR) {
+    if (b.rowpart_nr.n < b.vlen * NR) b.rowpart_nr.alloc(b.vlen * NR);
+    if (b.colpart_nr.n < b.ntiles * (int64_t)kTile * NR) b.colpart_nr.alloc(b.ntiles * kTile * NR);
+  }
+  const int64_t nblocks = b.vlen / kTile;
+  for (; c + NR <= nr; c += NR) {
+    const double *xc = x + (int64_t)c * b.vlen;
+    if (c == 0 && ev_before) record_event(ev_before, s);
+    if (warps == 8) launch_symv_nr4<4, 2, 8>(b, b.sched_for(2), data, xc, d_err, s);
+    else launch_symv_nr4<4, 2, 16>(b, b.sched_for(1), data, xc, d_err, s);
+    if (c == 0 && ev_after) record_event(ev_after, s);
+    for (int q = 0; q < NR; ++q)
+      k_symv_reduce<<<(unsigned)nblocks, kTile, 0, s>>>(
+          b.d_vrow_m.p, b.d_vrow_I.p, b.d_nt.p, b.d_toff.p, b.d_voff.p,
+          b.rowpart_nr.p + (int64_t)q * b.vlen, b.colpart_nr.p + (int64_t)q * b.ntiles * kTile,
+          y + (int64_t)(c + q) * b.vlen, nblocks);
+    GENEO_CHECK_LAUNCH();
+  }
+  for (; c < nr; ++c)
+    symv_batch<float>(b, data, x + (int64_t)c * b.vlen, y + (int64_t)c * b.vlen, d_err, s);
 }
 
 template void symv_batch<double>(TileBatch &, const double *, const double *, double *, int *,

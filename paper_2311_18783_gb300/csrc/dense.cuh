@@ -62,6 +62,8 @@ struct TileBatch {
   int sched_ctas = 0;
   DevBuf<int32_t> d_strip_m, d_strip_I, d_cta_off;
   DevBuf<double> rowpart, colpart;   // partial sums of the streaming SYMV
+  DevBuf<double> rowpart_nr;         // the same for 4 columns at once (float32 tiles)
+  DevBuf<float> colpart_nr;
   // launch configuration per storage type (0 float, 1 double): an index into
   // the candidate lists of the autotuner (0 = default)
   int symv_cfg[2] = {0, 0};
@@ -107,6 +109,16 @@ void pivot_block_inverse(TileBatch &b, const double *L, double *Y, const double 
 template <typename T>
 void symv_batch(TileBatch &b, const T *data, const double *x, double *y, int *d_err,
                 cudaStream_t s, cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
+
+// y_c = blockdiag(A_m) x_c for nr columns of float32 tiles (x, y: nr padded
+// vectors of b.vlen, one after another).  Columns go through the stream four
+// at a time, each tile read once per group; column c equals
+// symv_batch<float>(x_c) bit for bit under the batch's float configuration.
+// ev_before / ev_after, when given, are recorded around the first group's
+// streaming kernel (nr >= 4).
+void symv_batch_f32_cols(TileBatch &b, const float *data, const double *x, double *y, int nr,
+                         int *d_err, cudaStream_t s, cudaEvent_t ev_before = nullptr,
+                         cudaEvent_t ev_after = nullptr);
 
 // The autotuner's candidate configurations of symv_batch<T>.
 template <typename T> int symv_candidates();

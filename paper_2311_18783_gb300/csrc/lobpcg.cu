@@ -1247,11 +1247,11 @@ void geneo_eigenvectors(geneo_ctx *c) {
       // float32 SYMV streams half the bytes of the float64 one, which is
       // FP64-ALU-bound (a preconditioner of the eigensolve needs no float64)
       const bool f32_dir = !neu_dir && c->loc_f32.p;
-      for (int col = 0; col < k; ++col) {
-        if (f32_dir)
-          symv_batch<float>(c->loc, c->loc_f32.p, L.R.p + (int64_t)col * L.vlen,
-                            L.W.p + (int64_t)col * L.vlen, c->d_err.p, s);
-        else
+      if (f32_dir) {
+        // four columns per pass over the float32 factors
+        symv_batch_f32_cols(c->loc, c->loc_f32.p, L.R.p, L.W.p, k, c->d_err.p, s);
+      } else {
+        for (int col = 0; col < k; ++col)
           symv_batch<double>(c->loc, Tdir, L.R.p + (int64_t)col * L.vlen,
                              L.W.p + (int64_t)col * L.vlen, c->d_err.p, s);
       }

@@ -94,6 +94,9 @@ void mf_setup(geneo_ctx *c, MfSchur *schur = nullptr);
 void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k = 1);
 void mf_reserve(geneo_ctx *c, int k);
 int mf_launches_per_solve(const geneo_ctx *c);
+// per step of the single-launch coarse solve: kind, level, items, factor bytes,
+// SM cycles of CTA 0 in the last profiled solve
+std::vector<double> mf_step_profile(const geneo_ctx *c);
 int64_t mf_factor_bytes(const geneo_ctx *c);
 // algorithmic bytes of one coarse solve: every factor tile the solve reads
 int64_t mf_solve_bytes(const geneo_ctx *c);

@@ -436,7 +436,7 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k
     GENEO_CHECK_LAUNCH();
     return;
   }
-  for (int j = 0; j < k; ++j) {
+  for (int j = 0; j < k;) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof) {
       e0 = c->ev_take();
@@ -445,11 +445,19 @@ void local_solve(geneo_ctx *c, const double *r, double *w, cudaStream_t s, int k
     }
     const double *xj = c->loc_x.p + j * vlen;
     double *yj = c->loc_y.p + j * vlen;
+    if (c->local_prec == GENEO_PREC_FP32 && k - j >= 4) {
+      // four columns per pass over the float32 factors (same bits per column)
+      c->launches += 5;
+      symv_batch_f32_cols(c->loc, c->loc_f32.p, xj, yj, 4, c->d_err.p, s, e0, e1);
+      j += 4;
+      continue;
+    }
     c->launches += 2;
     if (c->local_prec == GENEO_PREC_FP32)
       symv_batch<float>(c->loc, c->loc_f32.p, xj, yj, c->d_err.p, s, e0, e1);
     else
       symv_batch<double>(c->loc, c->loc_f64.p, xj, yj, c->d_err.p, s, e0, e1);
+    ++j;
   }
   if (c->local_prec == GENEO_PREC_FP32) {
     // split inverse: float32 C_j r_j plus the float64 gradient part
@@ -587,9 +595,10 @@ static void pcg_step_half(geneo_ctx *c, double *x, cudaStream_t s, int k) {
 // context's capture stream, with x = p_x; replayed on the caller's stream for
 // every iteration after the first.
 static void ensure_pcg_graph(geneo_ctx *c, int k) {
-  const int cfg = (c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1]) * 2 + (c->grad32 ? 1 : 0);
+  const int cfg = ((c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1]) * 2 + (c->grad32 ? 1 : 0)) * 2 +
+                  (c->mf_persist ? 1 : 0);
   const int key =
-      (((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 128 + cfg)) << 8) + k;
+      (((((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 256 + cfg)) << 8) + k;
   if (c->pcg_exec && c->pcg_key == key) return;
   c->drop_graph();
   const int64_t l0 = c->launches;
@@ -809,8 +818,9 @@ static void seg_step_half(geneo_ctx *c, double *x, cudaStream_t s) {
 // [second half ; first half] of a segmented iteration on x = p_x, captured
 // once per local precision, profiling switch and form
 static void ensure_seg_graph(geneo_ctx *c) {
-  const int cfg = (c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1]) * 2 + (c->grad32 ? 1 : 0);
-  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 128 + cfg;
+  const int cfg = ((c->loc.symv_cfg[0] * 8 + c->loc.symv_cfg[1]) * 2 + (c->grad32 ? 1 : 0)) * 2 +
+                  (c->mf_persist ? 1 : 0);
+  const int key = ((c->local_prec * 2 + (c->prof ? 1 : 0)) * 2 + (c->balanced ? 1 : 0)) * 256 + cfg;
   if (c->seg_exec && c->seg_key == key) return;
   if (c->seg_exec) cudaGraphExecDestroy(c->seg_exec);
   c->seg_exec = nullptr;

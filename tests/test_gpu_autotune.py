@@ -71,3 +71,27 @@ def test_autotune_records_and_cache(tmp_path):
     rows2 = s2.export("autotune").reshape(-1, 12)
     assert np.all(rows2[:, 3] == 1) and np.array_equal(rows2[:, 2], rows[:, 2])
     s2.close()
+
+
+def test_four_column_pass_equals_columns_under_every_configuration():
+    """A block apply of float32 local solves streams each tile once for four
+    columns (k_symv_strips_nr); with the warps per tile of the selected
+    configuration it keeps every sum in the single-column order, so each
+    column of a 6-column block equals its own single-column apply bit for
+    bit (columns 0-3 through the four-column kernel, 4-5 one at a time),
+    under 8- and 16-warp configurations alike."""
+    import paper_2311_18783_gb300 as pkg
+    w = _case()
+    s = pkg.Solver.from_workload(w, precision=pkg.PREC_FP32)
+    s.use_precision(pkg.PREC_FP32)
+    R = torch.as_tensor(np.random.default_rng(5).standard_normal((6, s.n)), device="cuda")
+    for i in range(pkg.Solver.symv_config_count(pkg.PREC_FP32)):
+        s.use_symv_config(pkg.PREC_FP32, i)
+        Z = torch.empty_like(R)
+        s.apply_preconditioner_block(R, Z)
+        for j in range(6):
+            z = torch.empty_like(R[j])
+            s.apply_preconditioner(R[j].contiguous(), z)
+            assert torch.equal(Z[j], z), (i, j)
+    s.use_symv_config(pkg.PREC_FP32, 0)
+    s.close()

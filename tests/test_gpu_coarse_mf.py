@@ -124,7 +124,8 @@ def test_coarse_backward_error(case):
 
 
 def test_coarse_solve_repeatable(case):
-    """The solve has no atomics: two calls give identical bits."""
+    """Split-K partials are summed in slot order, not by atomics on the
+    values: two calls give identical bits."""
     name, w, prob, s_mf, s_dn = case
     r = dev(np.random.default_rng(7).standard_normal(s_mf.n))
     a = torch.empty_like(r)
@@ -145,3 +146,56 @@ def test_pcg_iterations_match_dense(case):
     assert i1["status"] == 0 and i2["status"] == 0
     assert abs(i1["iters"] - i2["iters"]) <= 1
     assert rel(host(x1), host(x2)) <= 1e-7
+
+
+def test_single_launch_equals_level_launches(case):
+    """The coarse solve as one cooperative launch (grid barriers between the
+    level-by-level steps, factor tiles staged by bulk copies) computes every
+    tile task in the same order as one launch per level and phase: identical
+    bits, for one column and inside a block preconditioner apply of three
+    columns."""
+    name, w, prob, s_mf, s_dn = case
+    r = dev(np.random.default_rng(11).standard_normal(s_mf.n))
+    a = torch.empty_like(r)
+    b = torch.empty_like(r)
+    try:
+        s_mf.use_persistent_coarse(True)
+        s_mf.coarse_solve(r, a)
+        s_mf.use_persistent_coarse(False)
+        s_mf.coarse_solve(r, b)
+        assert torch.equal(a, b)
+        R = dev(np.random.default_rng(12).standard_normal((3, s_mf.n)))
+        Z1 = torch.empty_like(R)
+        Z2 = torch.empty_like(R)
+        s_mf.use_persistent_coarse(True)
+        s_mf.apply_preconditioner_block(R, Z1)
+        s_mf.use_persistent_coarse(False)
+        s_mf.apply_preconditioner_block(R, Z2)
+        assert torch.equal(Z1, Z2)
+    finally:
+        s_mf.use_persistent_coarse(True)
+
+
+def test_single_launch_pcg_graph(case):
+    """PCG replays its iteration as a CUDA graph whose key includes the
+    coarse kernel shape: switching between the two shapes gives the same
+    iterates bit for bit, in both PCG forms."""
+    name, w, prob, s_mf, s_dn = case
+    bvec = torch.empty(s_mf.n, dtype=torch.float64, device="cuda")
+    s_mf.assemble_rhs(w.f_slot[0], bvec)
+    try:
+        for balanced in (False, True):
+            s_mf.use_balanced(balanced)
+            xs, its = [], []
+            for persistent in (True, False, True):
+                s_mf.use_persistent_coarse(persistent)
+                x = torch.zeros_like(bvec)
+                info = s_mf.solve(bvec, x, tol=1e-10, maxit=500)
+                assert info["status"] == 0
+                xs.append(x)
+                its.append(info["iters"])
+            assert its[0] == its[1] == its[2]
+            assert torch.equal(xs[0], xs[1]) and torch.equal(xs[0], xs[2])
+    finally:
+        s_mf.use_persistent_coarse(True)
+        s_mf.use_balanced(False)
