@@ -632,6 +632,14 @@ def run_many(args):
     s.close()
 
 
+def coarse_single_launch(s):
+    """Whether the autotuner kept the single-launch shape of the coarse
+    solve (its row of the "autotune" export, target 2)."""
+    rows = s.export("autotune").reshape(-1, 12)
+    rows = rows[rows[:, 0] == 2]
+    return bool(len(rows) and rows[-1][2] == 1)
+
+
 def load_oracle_solution(workload, n):
     """The oracle's accurate solution of the benchmark workload, stored by
     tests/golden/make_cube32_solution.py (a file read, no oracle code run),
@@ -687,8 +695,9 @@ def main():
     stages = dict(zip(stage_names, [float(v) for v in s.export("setup_stages")]))
     tuned = []
     for row in s.export("autotune").reshape(-1, 12):
-        ncand = pkg.Solver.symv_config_count(int(row[1]))
-        tuned.append({"target": "local factors" if row[0] == 0 else "S_j^-1 blocks",
+        ncand = pkg.Solver.symv_config_count(int(row[1])) if row[0] < 2 else 2
+        tuned.append({"target": ["local factors", "S_j^-1 blocks",
+                                 "coarse solve (0 per level and phase, 1 one launch)"][int(row[0])],
                       "precision": "f64" if int(row[1]) == pkg.PREC_FP64 else "f32",
                       "chosen": int(row[2]), "from_cache": bool(row[3]),
                       "ms_per_candidate": [float(v) for v in row[4:4 + ncand]]})
@@ -753,7 +762,7 @@ def main():
 
     side = max(1, min(args.steps, 5))
     variants = {}
-    coarse_per_level_ms = None
+    coarse_other_ms = coarse_other_shape = coarse_steps = None
     fp64_side = None
     if prec == pkg.PREC_FP32:
         # plain float64 factors on the same GPU, same problem and form
@@ -769,14 +778,21 @@ def main():
         s.use_gradient_precision(pkg.PREC_FP64)
         variants["mixed_grad64_balanced"], _, _ = timed_variant(pkg.PREC_FP32, True, side, 1)
         s.use_gradient_precision(pkg.PREC_FP32)
-        # the coarse solve as one launch per level and phase instead of one
-        # cooperative launch (identical results)
-        s.use_persistent_coarse(False)
-        variants["mixed_coarse_per_level"], _, pcl = timed_variant(pkg.PREC_FP32, True, side, 1,
-                                                                   True)
-        s.use_persistent_coarse(True)
+        # the coarse solve in the shape the autotuner did not keep (one
+        # cooperative launch, or one launch per level and phase; identical
+        # results), with the per-step profile of the single launch
+        kept = coarse_single_launch(s)
+        s.use_persistent_coarse(not kept)
+        other, _, pcl = timed_variant(pkg.PREC_FP32, True, side, 1, True)
+        if not kept:
+            cs = np.asarray(s.export("coarse_steps"), dtype=np.float64).reshape(-1, 5)
+            coarse_steps = [[int(r[0]), int(r[1]), int(r[2]), round(r[3] / 1e6, 3),
+                             round(r[4] / 2070.0, 2)] for r in cs]
+        s.use_persistent_coarse(kept)
+        variants["mixed_coarse_single_launch" if not kept else "mixed_coarse_per_level"] = other
         if pcl["coarse_symv_launches"]:
-            coarse_per_level_ms = pcl["coarse_symv_ms"] / pcl["coarse_symv_launches"]
+            coarse_other_ms = pcl["coarse_symv_ms"] / pcl["coarse_symv_launches"]
+            coarse_other_shape = "one cooperative launch" if not kept else "per level and phase"
     # headline: balanced form with the precision asked for, clocks sampled
     s.use_precision(prec)
     s.use_balanced(True)
@@ -812,22 +828,25 @@ def main():
     if prof["coarse_symv_launches"] and prof["coarse_solve_bytes"]:
         tc = prof["coarse_symv_ms"] / prof["coarse_symv_launches"] * 1e-3
         cb = prof["coarse_solve_bytes"]
-        coarse_roof = {"kernel": "k_mf_solve_persistent (one coarse solve, one cooperative "
-                                 "launch)",
+        single = coarse_single_launch(s)
+        coarse_roof = {"kernel": ("k_mf_solve_persistent (one coarse solve, one cooperative "
+                                  "launch)") if single else
+                                 "k_mf_tiles<0..3> + k_mf_gather (one coarse solve)",
                        "bound": "hbm", "achieved": cb / tc / 1e9, "peak": peaks_hbm(),
                        "unit": "GB/s", "frac": cb / tc / 1e9 / peaks_hbm(),
                        "algorithmic_bytes_per_solve": cb, "solve_ms": tc * 1e3,
                        "solves": prof["coarse_symv_launches"],
-                       "solve_ms_one_launch_per_level_and_phase": coarse_per_level_ms}
+                       "other_shape": coarse_other_shape, "other_shape_solve_ms": coarse_other_ms}
     if coarse_roof is not None:
         # per step of the last profiled single-launch coarse solve: kind (0
         # permutation in, 1 gather, 2..5 tile phase 0..3, 6 permutation out),
         # tree level, items, MB of factor tiles, microseconds (SM cycles of
-        # the first CTA at the median clock)
-        cs = np.asarray(s.export("coarse_steps"), dtype=np.float64).reshape(-1, 5)
-        mhz = clk.get("sm_mhz") or 2070.0
-        coarse_roof["steps"] = [[int(r[0]), int(r[1]), int(r[2]), round(r[3] / 1e6, 3),
-                                 round(r[4] / mhz, 2)] for r in cs]
+        # the first CTA at 2070 MHz)
+        if coarse_steps is None and coarse_roof["kernel"].startswith("k_mf_solve_persistent"):
+            cs = np.asarray(s.export("coarse_steps"), dtype=np.float64).reshape(-1, 5)
+            coarse_steps = [[int(r[0]), int(r[1]), int(r[2]), round(r[3] / 1e6, 3),
+                             round(r[4] / 2070.0, 2)] for r in cs]
+        coarse_roof["single_launch_steps"] = coarse_steps
     spmv_roof = time_spmv(s)
     spmv_roof["l2"] = ("A, x and y take about 45 MB; the value and index loads carry an "
                        "evict-first hint, so back-to-back launches re-read A; bench.py "

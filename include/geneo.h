@@ -155,14 +155,16 @@ typedef struct {
                                 Z^T r_k).  0: x0 = 0 and the literal four-step apply.
                                 Switchable later with geneo_use_balanced. */
   int32_t geneo_pencil;      /* GENEO_PENCIL_FILTERED (default) or GENEO_PENCIL_CLASSICAL */
-  int32_t autotune;          /* 1: at the end of the set-up, time every candidate launch
+  int32_t autotune;          /* 1: before the eigensolves, time every candidate launch
                                 configuration of the streaming SYMV (bulk-copy stages,
                                 tiles per barrier pair, warps per CTA, CTAs per SM) on the
                                 context's local factors (each stored precision) and S_j^-1
-                                blocks, and keep the fastest; results are cached per
-                                process by target, precision, nrhs, mean n_i bucket and
-                                stored-tile bucket (geneo_export("autotune")).  0: the
-                                default configuration */
+                                blocks, and keep the fastest; after the coarse factor, time
+                                both shapes of the sparse coarse solve (one launch per
+                                level and phase, one cooperative launch) and keep the
+                                faster.  Results are cached per process by target,
+                                precision, nrhs and size buckets (geneo_export
+                                ("autotune")).  0: the default configurations */
   const char *autotune_cache; /* NULL, or a text file read before tuning and appended with
                                 every new result ("key index milliseconds" per line); the
                                 string is only read during geneo_setup */
@@ -302,14 +304,15 @@ int geneo_use_gradient_precision(geneo_ctx *ctx, int32_t precision);
 int geneo_use_balanced(geneo_ctx *ctx, int32_t on);
 
 /* Kernel shape of the sparse coarse solve y = E^-1 t (Sec. 2, E = Z^T A Z;
- * multifrontal factor of the nested-dissection ordering).  on = 1 (default):
+ * multifrontal factor of the nested-dissection ordering).  on = 1:
  * the whole solve is one cooperative launch whose resident CTAs run the
  * level-by-level steps separated by a bounded grid-wide barrier (a barrier
  * that waits more than about two seconds makes the call return
- * GENEO_ERR_TIMEOUT).  on = 0: one launch per level and phase.  Both compute
- * the same operations in the same order and give identical results.  Where
- * the device offers no cooperative launch, on = 1 behaves as on = 0.
- * INVALID_ARG unless on is 0 or 1. */
+ * GENEO_ERR_TIMEOUT).  on = 0 (default): one launch per level and phase.
+ * Both compute the same operations in the same order and give identical
+ * results; options.autotune times both on the context's factor and keeps the
+ * faster.  Where the device offers no cooperative launch, on = 1 behaves as
+ * on = 0.  INVALID_ARG unless on is 0 or 1. */
 int geneo_use_persistent_coarse(geneo_ctx *ctx, int32_t on);
 
 /* Same solve with host buffers: copies b_host[n] to the device, solves, and
@@ -433,10 +436,12 @@ int geneo_profile_read(geneo_ctx *ctx, geneo_profile *out);
  *                                   topology), local inverses, split / bfloat16 factors,
  *                                   GenEO eigensolves, GenEO independence filter, coarse
  *                                   factor, autotuning, total
- *  "autotune"    float64 [targets][12]  per tuned SYMV target: target (0 local factors,
- *                                   1 S_j^-1 blocks), precision, chosen candidate, 1 if it
- *                                   came from the cache, then milliseconds per candidate
- *                                   (NaN past the last)
+ *  "autotune"    float64 [targets][12]  per tuned target: target (0 local-factor SYMV,
+ *                                   1 S_j^-1 SYMV, 2 coarse solve shape with candidates
+ *                                   0 per level and phase, 1 one cooperative launch),
+ *                                   precision, chosen candidate, 1 if it came from the
+ *                                   cache, then milliseconds per candidate (NaN past the
+ *                                   last)
  *  "coarse_steps" float64 [steps][5]  per step of the single-launch coarse solve
  *                                   (geneo_use_persistent_coarse): kind (0 permutation in,
  *                                   1 gather, 2..5 tile phase 0..3, 6 permutation out),

@@ -11,7 +11,9 @@
 // per launch), the mean matrix size bucket (n_i rounded to a power of two)
 // and the stored-tile bucket; with options.autotune_cache set, the cache is
 // read from and appended to that text file ("key index milliseconds" per
-// line), so later set-ups of the same shapes skip the timing.
+// line), so later set-ups of the same shapes skip the timing.  The same
+// cache holds the choice between the two shapes of the sparse coarse solve
+// (autotune_coarse).
 #include <cmath>
 #include <cstdio>
 #include <fstream>
@@ -146,6 +148,70 @@ void autotune_symv(geneo_ctx *c) {
                                                 c->xi->s_inv.p);
   if (c->xi && c->xi->s_inv32.p) tune_one<float>(c, "gradient", GENEO_PREC_FP32, c->xi->sb,
                                                  c->xi->s_inv32.p);
+}
+
+void autotune_coarse(geneo_ctx *c) {
+  if (!mf_single_launch_available(c)) return;
+  std::ostringstream k;
+  k << "coarse/f64/nrhs1/n0_2^" << pow2_bucket((double)c->n0) << "/bytes2^"
+    << pow2_bucket((double)mf_solve_bytes(c));
+  TuneRecord rec;
+  rec.target = "coarse";
+  rec.key = k.str();
+  rec.precision = GENEO_PREC_FP64;
+  const char *path = c->opt.autotune_cache;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_cache_file(path);
+    auto it = g_tune_cache.find(rec.key);
+    if (it != g_tune_cache.end() && (it->second == 0 || it->second == 1)) {
+      c->mf_persist = it->second == 1;
+      rec.chosen = it->second;
+      rec.from_cache = true;
+      c->tune.push_back(rec);
+      return;
+    }
+  }
+  // candidate 0: one launch per level and phase, 1: one cooperative launch;
+  // five solves each on the context's own factor (right-hand side values do
+  // not change the work)
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  GENEO_CUDA(cudaEventCreate(&e0));
+  GENEO_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e300;
+  try {
+    for (int cand = 0; cand < 2; ++cand) {
+      c->mf_persist = cand == 1;
+      mf_solve(c, c->crs_x.p, c->crs_y.p, s, 1);  // warm-up
+      GENEO_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 5; ++r) mf_solve(c, c->crs_x.p, c->crs_y.p, s, 1);
+      GENEO_CUDA(cudaEventRecord(e1, s));
+      GENEO_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      GENEO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      rec.ms.push_back(ms / 5);
+      if (ms / 5 < best_ms) {
+        best_ms = ms / 5;
+        best = cand;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->mf_persist = false;
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_device_error(c, s);
+  c->mf_persist = best == 1;
+  rec.chosen = best;
+  c->tune.push_back(rec);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[rec.key] = best;
+  append_cache_file(path, rec.key, best, best_ms);
 }
 
 void autotune_clear_cache() {

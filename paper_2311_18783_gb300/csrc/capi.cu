@@ -586,7 +586,7 @@ int geneo_export(const geneo_ctx *c, const char *name, void *dst, int64_t cap, i
       for (const auto &r : c->tune) {
         double row[12];
         for (double &q : row) q = std::nan("");
-        row[0] = r.target == "local" ? 0.0 : 1.0;
+        row[0] = r.target == "local" ? 0.0 : r.target == "gradient" ? 1.0 : 2.0;
         row[1] = r.precision;
         row[2] = r.chosen;
         row[3] = r.from_cache ? 1.0 : 0.0;

@@ -329,9 +329,11 @@ __global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tas
 // The steps of the level-by-level solve (permutation in, per level the
 // gather and phases 0 and 1, per level downwards phases 2 and 3,
 // permutation out) run in order, separated by a grid-wide barrier; the CTAs
-// (all resident) stride over each step's items.  A CTA issues the tile loads
-// of its first task of a step before it waits at the barrier that ends the
-// step before, so those latencies overlap the barrier.  Every item computes
+// (all resident) stride over each step's items.  The factor tiles of a CTA's
+// items stream through a ring of shared-memory slots filled by bulk copies
+// ahead of use, across steps and barriers (the factor does not change during
+// a solve), so tile latencies overlap the compute, the reductions and the
+// barriers.  Every item computes
 // exactly what its launch of the level-by-level path computes, in the same
 // order, so both paths give identical results.  Vectors that a step
 // writes are read through L2 (ld.global.cg): a CTA's L1 may still hold a
@@ -402,60 +404,122 @@ __device__ __forceinline__ bool mf_grid_barrier(unsigned *bar, int *err, int &ok
   return ok_sh != 0;
 }
 
-// Shared memory of the single-launch solve beyond MfShared: the task's
-// factor tiles and the mbarrier their bulk copies complete on.
-constexpr size_t kMfPersistSmem = (size_t)kChunk * kTileElems * sizeof(double) + 16;
+// Shared memory of the single-launch solve beyond MfShared: a ring of
+// kRing factor tiles and their mbarriers.
+constexpr int kRing = 6;
+constexpr size_t kMfPersistSmem = (size_t)kRing * kTileElems * sizeof(double) + kRing * 8;
 
 __device__ __forceinline__ void mf_stamp(const MfPersistArgs &p, int st) {
   if (p.stamps && blockIdx.x == 0 && threadIdx.x == 0) p.stamps[st] = clock64();
 }
 
+// Offset (in tiles) of tile q of a task in tile phase `mode` (runtime form
+// of mf_tile_index).
+__device__ __forceinline__ int64_t mf_tile_at(const MfTask &tk, const int64_t *toff, int mode,
+                                              int q) {
+  const int O = tk.I, K = tk.j0 + q;
+  return mode <= 1 ? toff[tk.f] + (int64_t)O * (O + 1) / 2 + K
+                   : toff[tk.f] + (int64_t)K * (K + 1) / 2 + O;
+}
+
+// The tile stream of one CTA: the tiles of its items (it = blockIdx.x +
+// j gridDim.x of every tile step), in the order it consumes them.  Thread 0
+// issues them into the ring ahead of use, across steps and barriers: the
+// factor does not change during a solve.
+struct MfProducer {
+  int st, it, q, nk, mode, nitems;
+  MfTask tk;
+  const MfTask *tasks;
+  long long issued;
+
+  // move to the next tile of the stream from (st, it, q); false at its end
+  __device__ bool settle(const MfPersistArgs &p) {
+    const int k = p.a.k;
+    while (st < p.nsteps) {
+      if (nitems > 0 && it < nitems) {
+        if (q == 0 || nk < 0) {
+          tk = tasks[it / k];
+          nk = tk.j1 - tk.j0;
+        }
+        if (q < nk) return true;
+        it += gridDim.x;
+        q = 0;
+        nk = -1;
+        continue;
+      }
+      ++st;
+      it = blockIdx.x;
+      q = 0;
+      nk = -1;
+      nitems = 0;
+      if (st < p.nsteps) {
+        const MfStep S = p.steps[st];
+        if (S.kind >= kStepTiles && S.kind < kStepPermOut) {
+          mode = S.kind - kStepTiles;
+          nitems = S.ntask * k;
+          tasks = S.tasks;
+        }
+      }
+    }
+    return false;
+  }
+
+  // issue tiles while the ring has room (thread 0)
+  __device__ void fill(const MfPersistArgs &p, long long consumed, double *ring, uint64_t *bars) {
+    while (issued - consumed < kRing && settle(p)) {
+      const int slot = (int)(issued % kRing);
+      const double *T = (mode == 0 || mode == 3) ? p.TY : p.TL;
+      fence_proxy_async();  // generic-proxy reads of the slot's last tile come first
+      mbar_expect_tx(&bars[slot], (uint32_t)(kTileElems * sizeof(double)));
+      bulk_g2s(ring + (size_t)slot * kTileElems, T + mf_tile_at(tk, p.a.toff, mode, q) * kTileElems,
+               (uint32_t)(kTileElems * sizeof(double)), &bars[slot]);
+      ++issued;
+      ++q;
+    }
+  }
+};
+
 template <int kMode>
 __device__ __forceinline__ bool mf_tile_step(const MfStep &S, int st, const MfPersistArgs &p,
-                                             bool sync, double *tiles, uint64_t *mbar,
-                                             uint32_t &parity, MfShared &sh, int &ok_sh) {
+                                             bool sync, double *ring, uint64_t *bars,
+                                             MfProducer &pr, long long &consumed, MfShared &sh,
+                                             int &ok_sh) {
   const int k = p.a.k;
-  const double *T = (kMode == 0 || kMode == 3) ? p.TY : p.TL;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nitems = S.ntask * k;  // at most 2^31 (tasks x 16 columns)
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int ti = it / k, col = it - ti * k;
     const MfTask tk = S.tasks[ti];
     const int nk = tk.j1 - tk.j0;
-    // the tile buffer is free: every thread passed the end of the last item
-    if (threadIdx.x == 0 && nk > 0) {
-      fence_proxy_async();  // the generic-proxy reads of the last item come first
-      mbar_expect_tx(mbar, (uint32_t)(nk * kTileElems * sizeof(double)));
-      for (int q = 0; q < nk; ++q)
-        bulk_g2s(tiles + q * kTileElems, T + mf_tile_index<kMode>(tk, p.a, q) * kTileElems,
-                 (uint32_t)(kTileElems * sizeof(double)), mbar);
-    }
+    if (threadIdx.x == 0) pr.fill(p, consumed, ring, bars);
     if (sync) {
-      const bool ok = mf_grid_barrier(p.bar, p.err, ok_sh);
+      if (!mf_grid_barrier(p.bar, p.err, ok_sh)) return false;
       sync = false;
-      if (!ok) {
-        if (nk > 0) mbar_wait_bounded(mbar, parity);  // let the copies land
-        return false;
-      }
       mf_stamp(p, st);
     }
-    if (nk > 0) {
-      // every thread of the CTA takes the same decision
-      if (!__syncthreads_and(mbar_wait_bounded(mbar, parity))) {
-        if (threadIdx.x == 0) atomicCAS(p.err, kDevOk, kDevTimeout);
-        return false;
-      }
-      parity ^= 1u;
+    bool ok = true;
+    for (int q = 0; q < nk; ++q) {
+      const long long u = consumed + q;
+      ok = ok && mbar_wait_bounded(&bars[(int)(u % kRing)], (uint32_t)((u / kRing) & 1));
     }
+    // every thread of the CTA takes the same decision
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) atomicCAS(p.err, kDevOk, kDevTimeout);
+      return false;
+    }
+    const long long c0 = consumed;
     mf_finish<kMode>(tk, p.a, col,
                      [&](int q, int r) {
                        return *reinterpret_cast<const double2 *>(
-                           tiles + q * kTileElems + (w * 8 + r) * kTile + 2 * l);
+                           ring + (size_t)((c0 + q) % kRing) * kTileElems + (w * 8 + r) * kTile +
+                           2 * l);
                      },
                      sh);
-    __syncthreads();
+    __syncthreads();  // the item's slots are free again
+    consumed += nk;
   }
   if (sync) {
+    if (threadIdx.x == 0) pr.fill(p, consumed, ring, bars);
     if (!mf_grid_barrier(p.bar, p.err, ok_sh)) return false;
     mf_stamp(p, st);
   }
@@ -466,34 +530,46 @@ __global__ void __launch_bounds__(256, 1) k_mf_solve_persistent(MfPersistArgs p)
   __shared__ MfShared sh;
   __shared__ int ok_sh;
   extern __shared__ __align__(128) unsigned char mf_dyn[];
-  double *tiles = reinterpret_cast<double *>(mf_dyn);
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(mf_dyn + (size_t)kChunk * kTileElems * sizeof(double));
-  uint32_t parity = 0;
+  double *ring = reinterpret_cast<double *>(mf_dyn);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(mf_dyn + (size_t)kRing * kTileElems * sizeof(double));
   if (threadIdx.x == 0) {
-    mbar_init(mbar, 1);
+    for (int i = 0; i < kRing; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
+  MfProducer pr;
+  pr.st = -1;
+  pr.it = 0;
+  pr.q = 0;
+  pr.nk = -1;
+  pr.mode = 0;
+  pr.nitems = 0;
+  pr.tasks = nullptr;
+  pr.issued = 0;
+  long long consumed = 0;
   const int k = p.a.k;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = true;
   mf_stamp(p, 0);
-  for (int st = 0; st < p.nsteps; ++st) {
+  for (int st = 0; st < p.nsteps && ok; ++st) {
     const MfStep S = p.steps[st];
     const bool sync = st > 0;
     if (S.kind >= kStepTiles && S.kind < kStepPermOut) {
-      bool ok = true;
       switch (S.kind - kStepTiles) {
-        case 0: ok = mf_tile_step<0>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
-        case 1: ok = mf_tile_step<1>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
-        case 2: ok = mf_tile_step<2>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
-        default: ok = mf_tile_step<3>(S, st, p, sync, tiles, mbar, parity, sh, ok_sh); break;
+        case 0: ok = mf_tile_step<0>(S, st, p, sync, ring, bars, pr, consumed, sh, ok_sh); break;
+        case 1: ok = mf_tile_step<1>(S, st, p, sync, ring, bars, pr, consumed, sh, ok_sh); break;
+        case 2: ok = mf_tile_step<2>(S, st, p, sync, ring, bars, pr, consumed, sh, ok_sh); break;
+        default: ok = mf_tile_step<3>(S, st, p, sync, ring, bars, pr, consumed, sh, ok_sh); break;
       }
-      if (!ok) return;
       continue;
     }
+    if (threadIdx.x == 0) pr.fill(p, consumed, ring, bars);
     if (sync) {
-      if (!mf_grid_barrier(p.bar, p.err, ok_sh)) return;
+      if (!mf_grid_barrier(p.bar, p.err, ok_sh)) {
+        ok = false;
+        break;
+      }
       mf_stamp(p, st);
     }
     if (S.kind == kStepPermIn || S.kind == kStepPermOut) {
@@ -518,7 +594,11 @@ __global__ void __launch_bounds__(256, 1) k_mf_solve_persistent(MfPersistArgs p)
       }
     }
   }
-  mf_stamp(p, p.nsteps);
+  if (ok) mf_stamp(p, p.nsteps);
+  // copies still in flight (a failed wait, or none) land before the CTA leaves
+  if (threadIdx.x == 0)
+    for (long long u = consumed; u < pr.issued; ++u)
+      mbar_wait_bounded(&bars[(int)(u % kRing)], (uint32_t)((u / kRing) & 1));
 }
 
 __global__ void k_perm(const int64_t *__restrict__ idx, const double *__restrict__ src,
@@ -1063,6 +1143,10 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {
   }
   k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, M.xpos.p, y, n0, 0);
   GENEO_CHECK_LAUNCH();
+}
+
+bool mf_single_launch_available(const geneo_ctx *c) {
+  return c->mf && c->mf->persist_ctas > 0;
 }
 
 std::vector<double> mf_step_profile(const geneo_ctx *c) {

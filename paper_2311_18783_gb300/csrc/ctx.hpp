@@ -118,7 +118,7 @@ struct geneo_ctx {
   int local_prec = GENEO_PREC_FP64;  // precision used by the local solves
   bool balanced = false;             // PCG in the balanced (one coarse solve) form
   bool grad32 = false;               // split local solves: S_j^-1 in float32
-  bool mf_persist = true;            // coarse solve as one cooperative launch
+  bool mf_persist = false;           // coarse solve as one cooperative launch
   // warm start of the local eigensolves: edge features [loc.vlen][5]; the
   // locked eigenvectors (first 8 per subdomain, and B times them) when kept
   geneo::DevBuf<float> d_feat;

@@ -809,6 +809,7 @@ void setup_all(geneo_ctx *c) {
     c->crs_x.alloc(c->n0);
     c->crs_y.alloc(c->n0);
     c->crs_x.zero(s);
+    if (c->opt.autotune) autotune_coarse(c);
   } else if (c->n0 > 0) {
     build_z_csr(c);
     c->crs.layout({c->n0});

@@ -45,6 +45,9 @@ void setup_all(geneo_ctx *c);
 // times every candidate SYMV configuration on the context's tile batches and
 // keeps the fastest (autotune.cu)
 void autotune_symv(geneo_ctx *c);
+// times the sparse coarse solve as one launch per level and phase and as one
+// cooperative launch, keeps the faster (c->mf_persist)
+void autotune_coarse(geneo_ctx *c);
 void autotune_clear_cache();
 // Host part only: topology, decomposition, components, local structure and,
 // for a host-only context, the split near-kernel columns.  No CUDA call.
@@ -94,6 +97,7 @@ void mf_setup(geneo_ctx *c, MfSchur *schur = nullptr);
 void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k = 1);
 void mf_reserve(geneo_ctx *c, int k);
 int mf_launches_per_solve(const geneo_ctx *c);
+bool mf_single_launch_available(const geneo_ctx *c);
 // per step of the single-launch coarse solve: kind, level, items, factor bytes,
 // SM cycles of CTA 0 in the last profiled solve
 std::vector<double> mf_step_profile(const geneo_ctx *c);

@@ -53,12 +53,15 @@ def test_autotune_records_and_cache(tmp_path):
     cache = str(tmp_path / "symv_tune.txt")
     s = pkg.Solver.from_workload(w, precision=pkg.PREC_FP32, autotune=1, autotune_cache=cache)
     rows = s.export("autotune").reshape(-1, 12)
-    assert len(rows) == 4  # local float32 and float64, S_j^-1 float64 and float32
+    # local float32 and float64, S_j^-1 float64 and float32, coarse solve shape
+    assert len(rows) == 5
+    assert list(rows[:, 0]) == [0, 0, 1, 1, 2]
     for row in rows:
         prec = int(row[1])
-        ncand = pkg.Solver.symv_config_count(prec)
+        ncand = pkg.Solver.symv_config_count(prec) if row[0] < 2 else 2
         ms = row[4:4 + ncand]
         assert row[3] == 0 and np.all(ms > 0)
+        assert np.all(np.isnan(row[4 + ncand:]))
         assert int(row[2]) == int(np.argmin(ms))
     stages = s.export("setup_stages")
     assert stages[6] > 0 and abs(stages[:7].sum() - stages[7]) <= 0.05 * stages[7] + 0.05
