@@ -280,7 +280,8 @@ def run_block(args):
     t0 = time.perf_counter()
     # gamma = 1e-6 under a 1e6 jump of mu^-1 makes the local matrices
     # numerically singular: invert them with the exact gradient shift
-    s = pkg.Solver.from_workload(w, precision=pkg.PREC_BF16, gradient_shift=1)
+    # balanced form: one coarse solve per iteration, as in the headline
+    s = pkg.Solver.from_workload(w, precision=pkg.PREC_BF16, gradient_shift=1, balanced=1)
     setup_s = time.perf_counter() - t0
     n, k = s.n, w.f_slot.shape[0]
     B = torch.empty((k, n), dtype=torch.float64, device="cuda")

@@ -26,7 +26,8 @@ namespace geneo {
 
 namespace {
 constexpr int kLeafDefault = 256;
-constexpr int kChunk = 4;  // tiles per task of the solve's tile GEMVs
+constexpr int kChunk = 4;     // tiles per task of the solve's tile GEMVs
+constexpr int kColGroup = 4;  // right-hand-side columns one CTA applies a task's tiles to
 
 struct Front {
   std::vector<int32_t> cols;      // pivot columns (coarse column ids)
@@ -312,16 +313,23 @@ __device__ __forceinline__ void mf_finish(const MfTask &tk, MfArgs a, int64_t co
   }
 }
 
-// One launch per (level, phase): blockIdx.x = task * k + column, so the k
-// columns of a task run in adjacent CTAs and its tiles are read from DRAM
-// once and from L2 for the others
+// One launch per (level, phase): blockIdx.x = task * ng + g.  CTA g of a
+// task loads the task's tiles into registers once and applies them to the
+// right-hand-side columns g kColGroup .. (g + 1) kColGroup - 1, one after
+// another (ng = ceil(k / kColGroup) groups; one column per CTA when k = 1)
 template <int kMode>
-__global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tasks, MfArgs a) {
+__global__ void __launch_bounds__(256) k_mf_tiles(const MfTask *__restrict__ tasks, MfArgs a,
+                                                  int ng) {
   __shared__ MfShared sh;
-  const MfTask tk = tasks[blockIdx.x / a.k];
+  const int ti = blockIdx.x / ng, g = blockIdx.x - ti * ng;
+  const MfTask tk = tasks[ti];
   double2 v[kChunk][8];
   mf_load<kMode>(tk, a, a.T, v);
-  mf_finish<kMode>(tk, a, blockIdx.x % a.k, [&](int q, int r) { return v[q][r]; }, sh);
+  const int c1 = min(a.k, (g + 1) * kColGroup);
+  for (int col = g * kColGroup; col < c1; ++col) {
+    mf_finish<kMode>(tk, a, col, [&](int q, int r) { return v[q][r]; }, sh);
+    __syncthreads();  // shared memory is reused by the next column
+  }
 }
 
 // ---- the whole solve in one cooperative launch
@@ -1128,18 +1136,19 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {
   }
   k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, t, M.cpos.p, n0, 1);
   const int nlev = (int)M.levels.size();
+  const int ng = (k + kColGroup - 1) / kColGroup;
   for (int lv = 0; lv < nlev; ++lv) {
     MfLevel &Lv = M.levels[lv];
     k_mf_gather<<<dim3(grid_for(Lv.nrows, 256), k), 256, 0, s>>>(
         Lv.rf.p, Lv.rl.p, Lv.gptr.p, Lv.gidx.p, M.first.p, M.npiv.p, fb.d_voff.p, Lv.nrows, n0,
         fb.vlen, M.cpos.p, M.wbuf.p);
-    if (Lv.ntask[0]) k_mf_tiles<0><<<Lv.ntask[0] * k, 256, 0, s>>>(Lv.task[0].p, ay);
-    if (Lv.ntask[1]) k_mf_tiles<1><<<Lv.ntask[1] * k, 256, 0, s>>>(Lv.task[1].p, al);
+    if (Lv.ntask[0]) k_mf_tiles<0><<<Lv.ntask[0] * ng, 256, 0, s>>>(Lv.task[0].p, ay, ng);
+    if (Lv.ntask[1]) k_mf_tiles<1><<<Lv.ntask[1] * ng, 256, 0, s>>>(Lv.task[1].p, al, ng);
   }
   for (int lv = nlev - 1; lv >= 0; --lv) {
     MfLevel &Lv = M.levels[lv];
-    if (Lv.ntask[2]) k_mf_tiles<2><<<Lv.ntask[2] * k, 256, 0, s>>>(Lv.task[2].p, al);
-    if (Lv.ntask[3]) k_mf_tiles<3><<<Lv.ntask[3] * k, 256, 0, s>>>(Lv.task[3].p, ay);
+    if (Lv.ntask[2]) k_mf_tiles<2><<<Lv.ntask[2] * ng, 256, 0, s>>>(Lv.task[2].p, al, ng);
+    if (Lv.ntask[3]) k_mf_tiles<3><<<Lv.ntask[3] * ng, 256, 0, s>>>(Lv.task[3].p, ay, ng);
   }
   k_perm<<<dim3(grid_for(n0, 256), k), 256, 0, s>>>(M.pos.p, M.xpos.p, y, n0, 0);
   GENEO_CHECK_LAUNCH();

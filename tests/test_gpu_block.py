@@ -45,21 +45,26 @@ def test_block_apply_equals_columns(blk, prec):
         assert torch.equal(Z[j], z)
 
 
+@pytest.mark.parametrize("balanced", [0, 1])
 @pytest.mark.parametrize("graph", [1, 0])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_block_solve_equals_columns(blk, prec, graph):
+def test_block_solve_equals_columns(blk, prec, graph, balanced):
     pkg, w, s, se, B = blk
     sv = s if graph else se
     sv.use_precision(pkg.PREC_FP64 if prec == "fp64" else pkg.PREC_FP32)
-    X = torch.empty_like(B)
-    st, infos = sv.solve_block(B, X, tol=1e-10, maxit=500)
-    assert st == 0
-    assert infos[3]["iters"] == 0 and torch.count_nonzero(X[3]) == 0
-    for j in (0, 1, 2, 4):
-        x = torch.zeros_like(B[j])
-        info = sv.solve(B[j].contiguous(), x, tol=1e-10, maxit=500)
-        assert info["iters"] == infos[j]["iters"] > 2
-        assert torch.equal(X[j], x)
+    sv.use_balanced(bool(balanced))
+    try:
+        X = torch.empty_like(B)
+        st, infos = sv.solve_block(B, X, tol=1e-10, maxit=500)
+        assert st == 0
+        assert infos[3]["iters"] == 0 and torch.count_nonzero(X[3]) == 0
+        for j in (0, 1, 2, 4):
+            x = torch.zeros_like(B[j])
+            info = sv.solve(B[j].contiguous(), x, tol=1e-10, maxit=500)
+            assert info["iters"] == infos[j]["iters"] > 2
+            assert torch.equal(X[j], x)
+    finally:
+        sv.use_balanced(False)
 
 
 def test_block_solve_vs_oracle(blk):
