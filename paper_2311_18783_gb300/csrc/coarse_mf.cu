@@ -370,7 +370,7 @@ struct MfPersistArgs {
   double *y;        // solutions, column order
   double *cpos;
   int64_t n0, vlen;
-  unsigned *bar;    // [0] arrivals, [1] generation; zero at set-up
+  unsigned *bar;    // [0] arrivals, [1] generation; zeroed before every launch
   int *err;
   long long *stamps;  // null, or clock64 of CTA 0 at every step start and at its end
 };
@@ -1121,6 +1121,9 @@ void mf_solve(geneo_ctx *c, const double *t, double *y, cudaStream_t s, int k) {
     MfPersistArgs pa{M.steps.p, M.nsteps, al, M.L.p, M.Y.p, M.pos.p, M.first.p, fb.d_voff.p,
                      M.npiv.p, t, y, M.cpos.p, n0, fb.vlen, M.bar.p, c->d_err.p,
                      c->prof ? M.stamps.p : nullptr};
+    // barrier words start from zero on every launch, also after a launch
+    // that gave up at a barrier
+    GENEO_CUDA(cudaMemsetAsync(M.bar.p, 0, 2 * sizeof(unsigned), s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)M.persist_ctas);
     cfg.blockDim = dim3(256);
