@@ -1322,9 +1322,7 @@ void geneo_eigenvectors(geneo_ctx *c) {
                         g[(size_t)m * ld * ld + i * ld + j];
             }
           std::vector<double> thh((size_t)L.nsub * k), Cm((size_t)L.nsub * ld * ld);
-          for (int m = 0; m < L.nsub; ++m)
-            general_rr(ns, ld, k, H.data() + (size_t)m * ld * ld, Mg.data() + (size_t)m * ld * ld,
-                       thh.data() + (size_t)m * k, Cm.data() + (size_t)m * ld * ld);
+          general_rr_batch(L.nsub, ns, ld, k, H.data(), Mg.data(), thh.data(), Cm.data());
           L.theta.upload(thh, s);
           L.tmat.upload(Cm, s);
         } else {

@@ -3,7 +3,9 @@
 #include "small_eig.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 
 namespace geneo {
 
@@ -104,6 +106,30 @@ void general_rr(int ns, int ld, int kout, const double *H, const double *M, doub
       C[(size_t)i * ld + c] = acc;
     }
   }
+}
+
+void general_rr_batch(int nsub, int ns, int ld, int kout, const double *H, const double *M,
+                      double *theta, double *C, int nthreads) {
+  int nt = nthreads;
+  if (nt <= 0) nt = (int)std::min<unsigned>(64, std::max(1u, std::thread::hardware_concurrency()));
+  nt = std::max(1, std::min(nt, nsub));
+  const size_t blk = (size_t)ld * ld;
+  auto one = [&](int m) {
+    general_rr(ns, ld, kout, H + m * blk, M + m * blk, theta + (size_t)m * kout, C + m * blk);
+  };
+  if (nt == 1) {
+    for (int m = 0; m < nsub; ++m) one(m);
+    return;
+  }
+  // subdomains handed out one at a time (their costs differ with the rank)
+  std::atomic<int> next{0};
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (int m = next++; m < nsub; m = next++) one(m);
+    });
+  for (auto &x : th) x.join();
 }
 
 }  // namespace geneo

@@ -18,4 +18,12 @@ void host_sym_eig(int n, std::vector<double> &a, std::vector<double> &w, std::ve
 void general_rr(int ns, int ld, int kout, const double *H, const double *M, double *theta,
                 double *C);
 
+// general_rr for nsub independent subdomains (H, M: nsub blocks of ld x ld;
+// theta: nsub x kout; C: nsub blocks of ld x ld), spread over host threads
+// (nthreads <= 0: the hardware concurrency, at most 64).  Each subdomain is
+// computed by one thread with the code above, so the results do not depend
+// on the number of threads.
+void general_rr_batch(int nsub, int ns, int ld, int kout, const double *H, const double *M,
+                      double *theta, double *C, int nthreads = 0);
+
 }  // namespace geneo

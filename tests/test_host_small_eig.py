@@ -5,7 +5,9 @@ compiled with g++ and checked against LAPACK through NumPy:
 * general_rr: the Rayleigh-Ritz step in a basis that is not B-orthonormal
   (used by the lobpcg_neumann mode) returns the kout largest eigenvalues of
   the pencil restricted to span S, B-orthonormal Ritz vectors, and a residual
-  orthogonal to span S, also when S has a numerically dependent column."""
+  orthogonal to span S, also when S has a numerically dependent column;
+* general_rr_batch: the same step for many subdomains over host threads
+  equals the one-subdomain calls bit for bit, for any thread count."""
 import ctypes as C
 import os
 import shutil
@@ -33,9 +35,12 @@ def lib(tmp_path_factory):
         '  for (int i = 0; i < n; ++i) w[i] = W[i];\n'
         '  for (size_t i = 0; i < V.size(); ++i) v[i] = V[i];\n}\n'
         'extern "C" void rr(int ns, int ld, int k, const double *H, const double *M,\n'
-        '                   double *th, double *Cm) { geneo::general_rr(ns, ld, k, H, M, th, Cm); }\n')
+        '                   double *th, double *Cm) { geneo::general_rr(ns, ld, k, H, M, th, Cm); }\n'
+        'extern "C" void rr_batch(int nsub, int ns, int ld, int k, const double *H,\n'
+        '                         const double *M, double *th, double *Cm, int nt) {\n'
+        '  geneo::general_rr_batch(nsub, ns, ld, k, H, M, th, Cm, nt); }\n')
     so = d / "small_eig.so"
-    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I" + SRC,
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-I" + SRC,
                     os.path.join(SRC, "small_eig.cpp"), str(shim), "-o", str(so)], check=True)
     return C.CDLL(str(so))
 
@@ -91,3 +96,32 @@ def test_general_rayleigh_ritz(lib):
         assert np.abs(X.T @ B @ X - np.eye(k)).max() <= 1e-9
         R = L @ X - B @ X * th
         assert np.abs(S.T @ R).max() <= 1e-9 * np.abs(S.T @ L @ X).max()
+
+
+def test_general_rr_batch_equals_single_calls(lib):
+    rng = np.random.default_rng(17)
+    nsub, ns, ld, k = 13, 24, 32, 8
+    H = np.zeros((nsub, ld, ld))
+    M = np.zeros((nsub, ld, ld))
+    for m in range(nsub):
+        S = rng.standard_normal((40, ns))
+        if m % 4 == 0:
+            S[:, 5] = S[:, 1] - 2.0 * S[:, 3]  # a dependent direction
+        A = rng.standard_normal((40, 40))
+        Bm = rng.standard_normal((40, 40))
+        H[m, :ns, :ns] = S.T @ (A + A.T) @ S
+        M[m, :ns, :ns] = S.T @ (Bm @ Bm.T + 40 * np.eye(40)) @ S
+    th1 = np.zeros((nsub, k))
+    C1 = np.zeros((nsub, ld, ld))
+    for m in range(nsub):
+        t = np.zeros(k)
+        c = np.zeros((ld, ld))
+        lib.rr(ns, ld, k, H[m].ctypes.data_as(P), M[m].ctypes.data_as(P),
+               t.ctypes.data_as(P), c.ctypes.data_as(P))
+        th1[m], C1[m] = t, c
+    for nt in (1, 3, 8):
+        th = np.zeros((nsub, k))
+        Cb = np.zeros((nsub, ld, ld))
+        lib.rr_batch(nsub, ns, ld, k, H.ctypes.data_as(P), M.ctypes.data_as(P),
+                     th.ctypes.data_as(P), Cb.ctypes.data_as(P), nt)
+        assert np.array_equal(th, th1) and np.array_equal(Cb, C1), nt
